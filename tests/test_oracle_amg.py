@@ -1,0 +1,123 @@
+"""Pins for the oracle V-cycle and PCG (no GPU)."""
+import numpy as np
+import pytest
+
+from oracle.amg import OracleAMG
+from oracle.smoother import SmootherSpec, l1_diag, error_poly
+from paper_2407_09848_gb300 import problems as pr
+
+KINDS = [("l1jacobi", {}), ("cheb4", {}), ("cheb4_opt", {}), ("cheb1_opt", {}),
+         ("cheb1", {"rho": 1.05})]
+
+
+def hier(st, coarse_max):
+    H = pr.build_hierarchy(st, coarse_max=coarse_max)
+    return H.A, H.P
+
+
+def dense_B(amg):
+    n = amg.A[0].shape[0]
+    I = np.eye(n)
+    return np.stack([amg.vcycle(I[:, j]) for j in range(n)], axis=1)
+
+
+def dense_G(A, spec):
+    Ad = A.toarray()
+    Mh = np.sqrt(l1_diag(A))
+    mu, V = np.linalg.eigh(Ad / Mh[:, None] / Mh[None, :])
+    return (V * error_poly(spec, mu)) @ V.T / Mh[:, None] * Mh[None, :]
+
+
+def dense_B_reference(A_list, P_list, spec, level=0):
+    """B_l from Eq. amg written with dense factors:
+    I - B_l A_l = G (I - P_l B_{l+1} P_l^T A_l) G, G = p(M^{-1}A_l)
+    (the post factor p(M^{-T} A) equals G because M is diagonal)."""
+    A = A_list[level].toarray()
+    if level == len(A_list) - 1:
+        return np.linalg.inv(A)
+    P = P_list[level].toarray()
+    Bc = dense_B_reference(A_list, P_list, spec, level + 1)
+    G = dense_G(A_list[level], spec)
+    n = A.shape[0]
+    E = G @ (np.eye(n) - P @ Bc @ P.T @ A) @ G
+    return (np.eye(n) - E) @ np.linalg.inv(A)
+
+
+@pytest.mark.parametrize("kind,kw", KINDS)
+@pytest.mark.parametrize("k", [1, 2, 4])
+def test_vcycle_equals_dense_composition(kind, kw, k):
+    for st, cm in [(pr.poisson(4), 8), (pr.varcoef(4, 1.0, 2.0, seed=1), 8),
+                   (pr.poisson(8), 8), (pr.aniso(6, 1e-2), 30)]:
+        A, Pl = hier(st, cm)
+        spec = SmootherSpec(kind, k, **kw)
+        amg = OracleAMG(A, Pl, spec)
+        B = dense_B(amg)
+        Bref = dense_B_reference(A, Pl, spec)
+        scale = np.abs(Bref).max()
+        assert np.max(np.abs(B - Bref)) <= 1e-12 * scale
+        # symmetric preconditioner
+        assert np.max(np.abs(B - B.T)) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("kind,kw", KINDS)
+def test_vcycle_symmetric_larger(kind, kw):
+    A, Pl = hier(pr.varcoef(16, 1.0, 4.0, seed=2), 64)
+    amg = OracleAMG(A, Pl, SmootherSpec(kind, 3, **kw))
+    rng = np.random.default_rng(0)
+    u, v = rng.standard_normal((2, A[0].shape[0]))
+    lhs, rhs = amg.vcycle(u) @ v, u @ amg.vcycle(v)
+    assert abs(lhs - rhs) <= 1e-13 * abs(lhs)
+
+
+def test_two_level_exact_coarse_special_case():
+    # with two levels the coarse correction is exactly P A_c^{-1} P^T
+    A, Pl = hier(pr.poisson(6), 27)
+    assert len(A) == 2
+    spec = SmootherSpec("cheb4", 2)
+    amg = OracleAMG(A, Pl, spec)
+    Ad, Pd = A[0].toarray(), Pl[0].toarray()
+    G = dense_G(A[0], spec)
+    n = Ad.shape[0]
+    E = G @ (np.eye(n) - Pd @ np.linalg.inv(Pd.T @ Ad @ Pd) @ Pd.T @ Ad) @ G
+    B = dense_B(amg)
+    assert np.allclose(np.eye(n) - B @ Ad, E, atol=1e-12)
+    # the two-level error propagation contracts in the A-norm
+    Ah = np.linalg.cholesky(Ad)
+    assert np.linalg.norm(Ah.T @ E @ np.linalg.inv(Ah.T), 2) < 1.0
+
+
+@pytest.mark.parametrize("kind,kw", KINDS)
+def test_pcg_matches_dense_solve(kind, kw):
+    A, Pl = hier(pr.varcoef(10, 1.0, 3.0, seed=4), 20)
+    amg = OracleAMG(A, Pl, SmootherSpec(kind, 2, **kw))
+    b = pr.rhs_uniform(A[0].shape[0], seed=1)
+    x, it, rel, hist = amg.pcg(b, rtol=1e-10, maxit=200)
+    xd = np.linalg.solve(A[0].toarray(), b)
+    cond = np.linalg.cond(A[0].toarray())
+    assert rel <= 1e-10
+    assert np.linalg.norm(x - xd) <= 1e-10 * cond * np.linalg.norm(xd)
+    assert np.linalg.norm(b - A[0] @ x) <= 1e-9 * np.linalg.norm(b)
+    assert 0 < it < 200
+
+
+def test_pcg_identity_preconditioner_is_cg():
+    # a single-level hierarchy makes the preconditioner the exact inverse:
+    # PCG converges in one iteration
+    A, Pl = hier(pr.poisson(5), 1000)
+    assert len(A) == 1
+    amg = OracleAMG(A, Pl, [])
+    b = pr.rhs_uniform(A[0].shape[0], seed=2)
+    x, it, rel, _ = amg.pcg(b, rtol=1e-12)
+    assert it == 1 and rel < 1e-12
+
+
+def test_pcg_poisson32_opt4_k4_sanity():
+    # the 32^3 configuration; iteration count vs the paper: parity unpinned
+    # (different hierarchy, problem and hardware).  Sanity range only.
+    A, Pl = hier(pr.poisson(32), 512)
+    assert [a.shape[0] for a in A] == [32768, 4096, 512]
+    amg = OracleAMG(A, Pl, SmootherSpec("cheb4_opt", 4))
+    b = pr.rhs_uniform(32768, seed=0)
+    x, it, rel, _ = amg.pcg(b, rtol=1e-8)
+    assert rel <= 1e-8 and 5 <= it <= 20
+    assert np.linalg.norm(b - A[0] @ x) <= 2e-8 * np.linalg.norm(b)

@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Benchmark of the hot path: V-cycle-preconditioned CG to ||r|| <= 1e-8 ||b||.
+
+Workload (default): 3-D Poisson 7-point on a 256^3 grid (16.8 M unknowns,
+Dirichlet), 2x2x2 aggregation down to <= 512 unknowns (6 levels), l1-Jacobi +
+optimised 4th-kind Chebyshev smoother of degree 4 (Eq. polsmootheropt) before
+and after the coarse correction, dense Cholesky on the coarsest level, FP64.
+One step = one full PCG solve from x0 = 0 with the inputs resident on the GPU.
+
+Printed (one JSON line on rank 0): time to solution (ms, lower is better), the
+roofline of the dominant kernel (the fused smoother step on the finest level:
+algorithmic bytes / CUDA-event time against the measured HBM copy peak), the
+end-to-end time through the host-buffer C-ABI call, the oracle CPU baseline on
+a bounded sample, clocks during the timed region and the kernel launch count.
+
+--impl reference times the FP64 CPU oracle instead (the reference of this
+build), each step one PCG iteration of the same solve, scaled by the oracle's
+iteration count to the same metric.
+"""
+import os
+
+# the CPU oracle is timed single-threaded: pin BLAS pools before numpy loads
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import hashlib
+import json
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PCG-AMG time-to-1e-8 and smoother HBM GB/s: plain FP64 vs learned/mixed form"
+GOLDEN_ITERS = os.path.join(ROOT, "tests", "golden", "oracle_pcg_iterations.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_poisson256_traffic.json")
+STEP_SOURCES = [os.path.join(ROOT, "paper_2407_09848_gb300", "csrc", f)
+                for f in ("kernels_smooth.cu", "kernels_common.cuh", "amgps_internal.h")]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--grid", type=int, default=256)
+    ap.add_argument("--kind", default="cheb4_opt")
+    ap.add_argument("--degree", type=int, default=4)
+    ap.add_argument("--prec", default="f64", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return f"poisson{a.grid}^3_{a.kind}_k{a.degree}_{a.prec}"
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def step_source_hash():
+    h = hashlib.sha256()
+    for p in STEP_SOURCES:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def golden_iterations(grid, kind, degree):
+    if not os.path.exists(GOLDEN_ITERS):
+        return None
+    with open(GOLDEN_ITERS) as f:
+        for r in json.load(f)["runs"]:
+            if r["grid"] == grid and r["kind"] == kind and r["degree"] == degree:
+                return int(r["iterations"])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_smi_id(torch, dev):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    try:
+        props = torch.cuda.get_device_properties(dev)
+        bus = getattr(props, "pci_bus_id", None)
+        dom = getattr(props, "pci_domain_id", 0)
+        if bus is not None:
+            out = subprocess.run(["nvidia-smi", "--query-gpu=index,pci.bus_id", "--format=csv,noheader"],
+                                 capture_output=True, text=True, timeout=20).stdout
+            for line in out.splitlines():
+                idx, bid = [x.strip() for x in line.split(",")]
+                parts = bid.split(":")
+                if len(parts) >= 2 and int(parts[-2], 16) == bus and int(parts[0], 16) == dom:
+                    return int(idx)
+    except Exception:
+        pass
+    if vis:
+        return vis.split(",")[dev]
+    return dev
+
+
+def build_problem(a):
+    from paper_2407_09848_gb300 import problems as pr
+    H = pr.build_hierarchy(pr.poisson(a.grid), coarse_max=512, name=f"poisson{a.grid}")
+    b = pr.rhs_uniform(H.levels[0].A.shape[0], seed=0)
+    return H, b
+
+
+def configure(S, H, kind, degree, torch):
+    from paper_2407_09848_gb300 import problems as pr
+    if kind == "cheb1":
+        for l in range(H.n_levels - 1):
+            v0 = torch.from_numpy(pr.vec_uniform(H.levels[l].A.shape[0], seed=0)).cuda()
+            lam = S.estimate_lambda(l, v0, iters=10)
+            S.set_smoother(l, "cheb1", degree, rho=1.1 * lam)
+    else:
+        S.set_smoother(-1, kind, degree)
+
+
+def time_oracle_iteration(H, b, kind, degree):
+    """Seconds of one oracle PCG iteration (V-cycle + SpMV + CG updates)."""
+    from oracle.amg import OracleAMG
+    from oracle.smoother import SmootherSpec, power_lambda
+    from paper_2407_09848_gb300 import problems as pr
+    specs = []
+    for lv in H.levels[:-1]:
+        if kind == "cheb1":
+            lam = power_lambda(lv.A, pr.vec_uniform(lv.A.shape[0], seed=0), iters=10)
+            specs.append(SmootherSpec(kind, degree, rho=1.1 * lam))
+        else:
+            specs.append(SmootherSpec(kind, degree))
+    ora = OracleAMG(H.A, H.P, specs)
+    t = time.perf_counter()
+    ora.pcg(b, rtol=1e-300, maxit=1)
+    return time.perf_counter() - t, ora
+
+
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    H, b = build_problem(a)
+    its = golden_iterations(a.grid, a.kind, a.degree)
+    from oracle.amg import OracleAMG  # noqa: F401  (import cost outside the timing)
+    if its is None:
+        print(json.dumps({"impl": "reference", "unavailable":
+                          f"no stored oracle iteration count for {workload_name(a)}"}))
+        return 0
+    _, ora = time_oracle_iteration(H, b, a.kind, a.degree)
+    times = []
+    for i in range(a.warmup + a.steps):
+        t = time.perf_counter()
+        ora.pcg(b, rtol=1e-300, maxit=1)
+        dt = time.perf_counter() - t
+        if i >= a.warmup:
+            times.append(dt)
+    per_iter = statistics.mean(times)
+    value_ms = per_iter * its * 1e3
+    sample = (f"one PCG iteration (V-cycle + SpMV + updates) of the {workload_name(a)} solve per step, "
+              f"mean of {a.steps}, x {its} oracle iterations")
+    out = {"impl": "reference", "metric": METRIC, "value": value_ms, "unit": "ms",
+           "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": value_ms,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": workload_name(a), "grid": a.grid, "kind": a.kind,
+                      "degree": a.degree, "rtol": a.rtol, "iterations": its},
+           "cpu_baseline": {"value": value_ms, "unit": "ms", "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value_ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def run_ours(a):
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    from paper_2407_09848_gb300 import build as bld
+    bld.build()
+    from paper_2407_09848_gb300.amgps import (PROF_RESTRICT, PROF_SPMV, PROF_STEP, Solver)
+
+    H, b = build_problem(a)
+    n = H.levels[0].A.shape[0]
+    S = Solver(local).load(H.A, H.P, prec=a.prec)
+    configure(S, H, a.kind, a.degree, torch)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    for _ in range(a.warmup):
+        its, rel = S.pcg(bd, x, rtol=a.rtol)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K solves, CUDA events on the caller's stream ----
+    S.profile(True)
+    for c in (PROF_STEP, PROF_RESTRICT, PROF_SPMV, 3):
+        S.profile_read(c, reset=True)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    smi = gpu_smi_id(torch, local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(smi) as clk:
+        ev0.record(stream)
+        for _ in range(a.steps):
+            its, rel = S.pcg(bd, x, rtol=a.rtol)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    total_ms = ev0.elapsed_time(ev1)
+    S.profile(False)
+    n_step, ms_step, by_step = S.profile_read(PROF_STEP, reset=True)
+    n_rr, ms_rr, _ = S.profile_read(PROF_RESTRICT, reset=True)
+    n_sp, ms_sp, _ = S.profile_read(PROF_SPMV, reset=True)
+    launches, _, _ = S.profile_read(3, reset=True)
+    ms_per = total_ms / a.steps
+    if pg:
+        t = torch.tensor([ms_per], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms_per = float(t.item())
+    true_res = float(np.linalg.norm(b - H.levels[0].A @ x.cpu().numpy()) / np.linalg.norm(b))
+
+    # ---- roofline of the fused smoother step on the finest level ----
+    peak, peak_src = measured_peak()
+    achieved = (by_step / 1e9) / (ms_step / 1e3) if ms_step > 0 else None
+    traffic = None
+    if os.path.exists(TRAFFIC_FILE):
+        with open(TRAFFIC_FILE) as f:
+            tr = json.load(f)
+        if tr.get("source_sha256") == step_source_hash() and tr.get("workload") == workload_name(a):
+            traffic = tr.get("dram_bytes_per_launch")
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved else None, "traffic": traffic,
+            "kernel": "k_step (fused SpMV + residual + l1 scaling + recurrence update), level 0",
+            "launches": n_step, "avg_launch_us": 1e3 * ms_step / max(n_step, 1),
+            "bytes_per_launch": by_step / max(n_step, 1), "peak_source": peak_src,
+            "share_of_step_time": ms_step / total_ms if total_ms else None}
+
+    # ---- end to end through the host-buffer C-ABI call ----
+    bh = torch.from_numpy(b.copy()).pin_memory()
+    xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+    S.pcg_host(bh, xh, rtol=a.rtol)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(a.steps):
+        S.pcg_host(bh, xh, rtol=a.rtol)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / a.steps
+
+    # ---- smoother sweep of the 256^3 configuration (one solve each) ----
+    sweep = None
+    if not a.no_sweep and rank == 0:
+        sweep = []
+        for kind in ("cheb1", "cheb4", "cheb4_opt", "cheb1_opt"):
+            for k in range(1, 7):
+                configure(S, H, kind, k, torch)
+                S.pcg(bd, x, rtol=a.rtol, maxit=1000)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                it_k, _ = S.pcg(bd, x, rtol=a.rtol, maxit=1000)
+                torch.cuda.synchronize()
+                sweep.append({"kind": kind, "degree": k, "iterations": it_k,
+                              "ms": round(1e3 * (time.perf_counter() - t0), 3),
+                              "oracle_iterations": golden_iterations(a.grid, kind, k)})
+        configure(S, H, a.kind, a.degree, torch)
+
+    # ---- CPU baseline: the oracle on a bounded sample ----
+    cpu = None
+    if not a.no_cpu and rank == 0:
+        t_iter, _ = time_oracle_iteration(H, b, a.kind, a.degree)
+        cpu = {"value": t_iter * its * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": f"one oracle PCG iteration (V-cycle + SpMV + updates) of the same "
+                         f"{workload_name(a)} solve, {t_iter:.2f} s, x {its} iterations"}
+
+    out = {"metric": METRIC, "value": ms_per, "unit": "ms", "n_gpus": world, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": ms_per, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": a.prec, "data": "synthetic",
+           "config": {"workload": workload_name(a), "grid": a.grid, "n": n,
+                      "levels": H.n_levels, "nnz": int(H.levels[0].A.nnz), "kind": a.kind,
+                      "degree": a.degree, "rtol": a.rtol, "iterations": its, "relres": rel,
+                      "true_relres": true_res,
+                      "oracle_iterations": golden_iterations(a.grid, a.kind, a.degree),
+                      "l2": "inputs larger than L2 (finest matrix 0.94 GB, 129 MB L2)",
+                      "parallelism": "replicas" if world > 1 else "single GPU"},
+           "roofline": roof,
+           "cpu_baseline": cpu,
+           "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 8 * n,
+                   "d2h_bytes_per_step": 8 * n},
+           "gpu_launches": launches,
+           "clocks": clk.summary(),
+           "kernel_ms": {"k_step_level0": ms_step / a.steps, "k_resid_restrict_level0": ms_rr / a.steps,
+                         "k_spmv_dot": ms_sp / a.steps},
+           "sweep": sweep}
+    if rank == 0:
+        print(json.dumps(out))
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,180 @@
+/*
+ * amgps.h -- C ABI of libamgps: polynomial-accelerated l1-Jacobi smoothers
+ * inside a symmetric AMG V-cycle preconditioning CG, on one GB300 (sm_103a).
+ *
+ * The operations follow arXiv 2407.09848 ("Optimal Polynomial Smoothers for
+ * Parallel AMG"):
+ *   - the SPD system A x = b                                  (Sec. 1, Eq. sys1)
+ *   - Galerkin hierarchy A_{l+1} = P_l^T A_l P_l              (Sec. 2)
+ *   - symmetric multiplicative V-cycle                        (Sec. 2, Eq. amg)
+ *   - l1-Jacobi M_i = a_ii + sum_{j != i} |a_ij|              (Sec. 2, Eq. l1smooth)
+ *   - 4th-kind Chebyshev smoother                             (Sec. 2.1, Eq. polsmoother)
+ *   - optimised 4th-kind weights                              (Sec. 2.1, Eq. polsmootheropt)
+ *   - 1st-kind Chebyshev acceleration on [a_k*, 1]            (Sec. 2.2, Algorithm 1;
+ *                                                              a_k* from Eq. optimalparameter)
+ *   - preconditioned CG as the outer solver                   (Sec. 4)
+ *
+ * Conventions (every entry point):
+ *   - No exception crosses this ABI.  Each call returns an amgps_status; the
+ *     text of the last failure is available from amgps_last_error(ctx).
+ *   - Host arrays passed in are borrowed for the duration of the call and
+ *     copied; the library owns every device copy and workspace it makes.
+ *   - Vector arguments named *_dev are device pointers owned by the caller,
+ *     FP64, length n_l of the level they refer to, in the caller's row order
+ *     (the order of the CSR rows given to amgps_hierarchy_load).
+ *   - Work is ordered after prior work on the caller's stream given to
+ *     amgps_create and the caller's stream is ordered after it on return, so
+ *     the calls are stream-asynchronous unless documented otherwise.
+ *   - A context is not thread-safe; use one context per host thread.
+ *   - Device faults are never used for error reporting: invalid input is
+ *     rejected on the host before any launch.
+ */
+#ifndef AMGPS_H
+#define AMGPS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  AMGPS_OK = 0,
+  AMGPS_E_ARG = 1,      /* bad argument: null pointer, malformed CSR, size mismatch, bad kind/degree */
+  AMGPS_E_NOT_SPD = 2,  /* non-positive diagonal, Cholesky pivot <= 0, or p^T A p <= 0 in PCG */
+  AMGPS_E_NOCONV = 3,   /* PCG reached maxit without meeting rtol (x holds the last iterate) */
+  AMGPS_E_NAN = 4,      /* a NaN/Inf appeared in a PCG scalar */
+  AMGPS_E_CUDA = 5,     /* a CUDA runtime call failed (message has cudaGetErrorString) */
+  AMGPS_E_TIMEOUT = 6,  /* reserved: a bounded device wait gave up */
+  AMGPS_E_STATE = 7,    /* call out of order (e.g. smooth before hierarchy_load) */
+  AMGPS_E_NOMEM = 8     /* device or pinned host allocation failed */
+} amgps_status;
+
+/* Smoother kinds (the rows of Table 1, Sec. 4, plus two configurations). */
+typedef enum {
+  AMGPS_L1JACOBI = 0,   /* k sweeps x += M^{-1}(b - A x)                                */
+  AMGPS_CHEB4 = 1,      /* Eq. polsmoother, rho(M^{-1}A) := 1 (or the level's rho)        */
+  AMGPS_CHEB4_OPT = 2,  /* Eq. polsmootheropt with the tabulated optimal beta_{j,k}       */
+  AMGPS_CHEB1 = 3,      /* Algorithm 1 on [a_k*,1] with rho = the level's rho (e.g. 1.1 x
+                           a power-iteration estimate, amgps_estimate_lambda)             */
+  AMGPS_CHEB1_OPT = 4,  /* Algorithm 1 on [a_k*,1] with rho(M^{-1}A) := 1 (Sec. 3)        */
+  AMGPS_WEIGHTS = 5     /* Eq. polsmootheropt with caller-supplied weights (learned)      */
+} amgps_kind;
+
+/* Storage of matrix values on the smoother and transfer path.  F64: all FP64.
+ * F32 / BF16: values rounded to nearest-even at load, V-cycle vectors and
+ * accumulation in FP32; the outer PCG (its SpMV, vectors and dot products) and
+ * the coarsest dense solve stay FP64. */
+typedef enum { AMGPS_F64 = 0, AMGPS_F32 = 1, AMGPS_BF16 = 2 } amgps_prec;
+
+/* Host CSR, borrowed.  rowptr[n_rows+1], col[nnz], val[nnz]; 0-based; columns
+ * need not be sorted; duplicates are not allowed. */
+typedef struct {
+  int64_t n_rows, n_cols, nnz;
+  const int32_t* rowptr;
+  const int32_t* col;
+  const double* val;
+} amgps_csr;
+
+typedef struct amgps_ctx amgps_ctx;
+
+/* Library ABI version (monotone integer). */
+int amgps_version(void);
+
+/* Create a context on CUDA device `device`.  `user_stream` (cudaStream_t,
+ * may be NULL for the legacy default stream) is the stream the caller's work
+ * lives on; the library runs on a stream of its own, ordered against it with
+ * events.  *out is NULL on failure. */
+amgps_status amgps_create(amgps_ctx** out, int device, void* user_stream);
+
+/* Release every device and host resource of the context.  NULL is allowed. */
+amgps_status amgps_destroy(amgps_ctx* ctx);
+
+/* Message of the last failing call on this context ("" if none).  Valid until
+ * the next call on the context.  With ctx == NULL: the last creation error. */
+const char* amgps_last_error(const amgps_ctx* ctx);
+
+/* Load the level hierarchy (Sec. 2): A[0..n_levels-1] square SPD CSR with
+ * n_rows(A[l+1]) == n_cols(P[l]); P[0..n_levels-2] the prolongators, each an
+ * unsmoothed aggregation: every row of P[l] holds exactly one entry equal to
+ * 1 (the aggregate of that fine row); other P are rejected with AMGPS_E_ARG.
+ * The coarsest level (n <= 1024) is solved by a dense FP64 Cholesky
+ * factorisation computed here on the device (AMGPS_E_NOT_SPD if a pivot is
+ * not positive).  Replaces any earlier hierarchy; every level's smoother is
+ * reset to CHEB4_OPT of degree 4.  Synchronous. */
+amgps_status amgps_hierarchy_load(amgps_ctx* ctx, int n_levels, const amgps_csr* A,
+                                  const amgps_csr* P, amgps_prec prec);
+
+/* Rows, nonzeros and stored matrix entries (after padding) of a level. */
+amgps_status amgps_level_info(amgps_ctx* ctx, int level, int64_t* n, int64_t* nnz,
+                              int64_t* stored);
+
+/* Smoother used by amgps_vcycle / amgps_pcg on `level` (-1: every non-coarsest
+ * level).  degree in 1..16.  `weights` (host, `degree` doubles) is read only for
+ * AMGPS_WEIGHTS and copied.  `rho` scales the spectral interval: the smoother
+ * uses rho in place of rho(M^{-1}A) (CHEB1, CHEB4, WEIGHTS, CHEB4_OPT);
+ * rho <= 0 means 1.  Synchronous host bookkeeping only. */
+amgps_status amgps_set_smoother(amgps_ctx* ctx, int level, amgps_kind kind, int degree,
+                                const double* weights, double rho);
+
+/* Power-iteration estimate of the largest eigenvalue of M^{-1}A_l on the
+ * device: v_0 = v0/||v0||, w = M^{-1}A v_{i-1}, lambda_i = ||w||,
+ * v_i = w/lambda_i, i = 1..iters; returns lambda_iters.  v0_dev: n_l FP64.
+ * Synchronous. */
+amgps_status amgps_estimate_lambda(amgps_ctx* ctx, int level, const double* v0_dev,
+                                   int iters, double* lambda_out);
+
+/* One smoother application on `level` (Sec. 2.1-2.2): x <- S(b, x).  `kind`
+ * and `degree` select the recurrence; CHEB4_OPT takes the tabulated weights,
+ * WEIGHTS the weights and rho stored by amgps_set_smoother for this level,
+ * CHEB1 the level's rho.  x_is_zero != 0 means the start vector is zero and
+ * x_dev is write-only.  b_dev, x_dev: n_l FP64 device vectors, must not alias. */
+amgps_status amgps_smooth(amgps_ctx* ctx, int level, amgps_kind kind, int degree,
+                          const double* b_dev, double* x_dev, int x_is_zero);
+
+/* One V-cycle z = B r (Eq. amg) from level 0, with the smoothers set by
+ * amgps_set_smoother.  r_dev, z_dev: n_0 FP64 device vectors, must not alias. */
+amgps_status amgps_vcycle(amgps_ctx* ctx, const double* r_dev, double* z_dev);
+
+/* Preconditioned CG on A_0 x = b with one V-cycle as preconditioner, x_0 = 0,
+ * stopping when ||r_k||_2 <= rtol ||b||_2 (recurrence residual) or after maxit
+ * iterations.  *iters = products with A_0 performed, *relres = final
+ * ||r_k||/||b||.  b_dev, x_dev: n_0 FP64 device vectors.  Synchronous (one
+ * host read of ||r||^2 per iteration).  Returns AMGPS_E_NOCONV at maxit. */
+amgps_status amgps_pcg(amgps_ctx* ctx, const double* b_dev, double* x_dev, double rtol,
+                       int maxit, int* iters, double* relres);
+
+/* amgps_pcg with host vectors: copies b (pinned staging) to the device,
+ * solves, copies x back.  b_host, x_host: n_0 doubles. Synchronous. */
+amgps_status amgps_pcg_host(amgps_ctx* ctx, const double* b_host, double* x_host,
+                            double rtol, int maxit, int* iters, double* relres);
+
+/* Wait for all work of the context.  */
+amgps_status amgps_synchronize(amgps_ctx* ctx);
+
+/* The library's tabulated optimal 4th-kind weights beta_{1..degree} for
+ * Eq. polsmootheropt (degree 1..16), written to beta_out (host). */
+amgps_status amgps_opt4_weights(int degree, double* beta_out);
+
+/* The library's tabulated a_k* of Eq. optimalparameter (degree 1..16). */
+amgps_status amgps_cheb1_astar(int degree, double* a_out);
+
+/* Kernel timing with CUDA events on the library stream.  When enabled, every
+ * launch of the listed kernel classes is bracketed by an event pair; pairs are
+ * harvested at synchronisation points.  Classes: 0 = fused smoother step on
+ * level 0, 1 = residual+restriction on level 0, 2 = PCG SpMV+dot; for these,
+ * *launches, *total_ms (sum of event-timed durations) and *bytes (algorithmic
+ * bytes of the launches: matrix nonzeros and stored indices once, each vector
+ * stream once) are returned.  Class 3 counts every kernel of this library
+ * executed since the last reset (whether or not timing is enabled; a graph
+ * replay counts its kernel nodes); its *total_ms and *bytes are 0.
+ * reset != 0 clears the counters of the class.  Reading is synchronous. */
+amgps_status amgps_profile_enable(amgps_ctx* ctx, int on);
+amgps_status amgps_profile_read(amgps_ctx* ctx, int kernel_class, int reset,
+                                int64_t* launches, double* total_ms, double* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMGPS_H */

@@ -81,7 +81,7 @@ class OracleAMG:
             r = r - alpha * q
             rn = np.linalg.norm(r)
             hist.append(rn / bnorm)
-            if rn <= rtol * bnorm:
+            if rn <= rtol * bnorm or it == maxit:
                 break
             z = self.vcycle(r)
             rz_new = r @ z

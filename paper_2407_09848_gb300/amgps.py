@@ -1,0 +1,243 @@
+"""Python binding of libamgps (include/amgps.h): argument marshalling only.
+
+Every step of the smoother, V-cycle and PCG runs in the library's CUDA
+kernels; this module checks shapes/dtypes, passes raw pointers and turns
+status codes into exceptions.  Device vectors are torch CUDA tensors (FP64,
+contiguous); PyTorch provides memory and the caller's stream, nothing else.
+The library must be built (``paper_2407_09848_gb300.build.build()``); there is
+no fallback path: a missing library raises immediately.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libamgps.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "amgps.h")
+
+KIND = {"l1jacobi": 0, "cheb4": 1, "cheb4_opt": 2, "cheb1": 3, "cheb1_opt": 4, "weights": 5}
+PREC = {"f64": 0, "f32": 1, "bf16": 2}
+STATUS = {0: "AMGPS_OK", 1: "AMGPS_E_ARG", 2: "AMGPS_E_NOT_SPD", 3: "AMGPS_E_NOCONV",
+          4: "AMGPS_E_NAN", 5: "AMGPS_E_CUDA", 6: "AMGPS_E_TIMEOUT", 7: "AMGPS_E_STATE",
+          8: "AMGPS_E_NOMEM"}
+PROF_STEP, PROF_RESTRICT, PROF_SPMV = 0, 1, 2
+
+
+class AmgpsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class CSR(C.Structure):
+    _fields_ = [("n_rows", C.c_int64), ("n_cols", C.c_int64), ("nnz", C.c_int64),
+                ("rowptr", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p)]
+
+
+_lib = None
+
+_SIGS = {
+    "amgps_version": ([], C.c_int),
+    "amgps_create": ([C.POINTER(C.c_void_p), C.c_int, C.c_void_p], C.c_int),
+    "amgps_destroy": ([C.c_void_p], C.c_int),
+    "amgps_last_error": ([C.c_void_p], C.c_char_p),
+    "amgps_hierarchy_load": ([C.c_void_p, C.c_int, C.POINTER(CSR), C.POINTER(CSR), C.c_int], C.c_int),
+    "amgps_level_info": ([C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                          C.POINTER(C.c_int64)], C.c_int),
+    "amgps_set_smoother": ([C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_double], C.c_int),
+    "amgps_estimate_lambda": ([C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_double)], C.c_int),
+    "amgps_smooth": ([C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int], C.c_int),
+    "amgps_vcycle": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "amgps_pcg": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int),
+                   C.POINTER(C.c_double)], C.c_int),
+    "amgps_pcg_host": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int),
+                        C.POINTER(C.c_double)], C.c_int),
+    "amgps_synchronize": ([C.c_void_p], C.c_int),
+    "amgps_opt4_weights": ([C.c_int, C.c_void_p], C.c_int),
+    "amgps_cheb1_astar": ([C.c_int, C.POINTER(C.c_double)], C.c_int),
+    "amgps_profile_enable": ([C.c_void_p, C.c_int], C.c_int),
+    "amgps_profile_read": ([C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                            C.POINTER(C.c_double)], C.c_int),
+}
+
+
+def lib():
+    """Load libamgps.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2407_09848_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def header_symbols():
+    """Names of the entry points declared in include/amgps.h."""
+    with open(HEADER) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"\b(amgps_[a-z0-9_]+)\s*\(", text)))
+
+
+def opt4_weights(k):
+    """The library's tabulated optimal 4th-kind weights (host call, no GPU)."""
+    out = np.zeros(k)
+    st = lib().amgps_opt4_weights(k, out.ctypes.data)
+    if st:
+        raise AmgpsError(st, "bad degree")
+    return out
+
+
+def cheb1_astar(k):
+    a = C.c_double()
+    st = lib().amgps_cheb1_astar(k, C.byref(a))
+    if st:
+        raise AmgpsError(st, "bad degree")
+    return a.value
+
+
+def _csr_struct(A, keep):
+    import scipy.sparse as sp
+    A = sp.csr_matrix(A)
+    rowptr = np.ascontiguousarray(A.indptr, dtype=np.int32)
+    col = np.ascontiguousarray(A.indices, dtype=np.int32)
+    val = np.ascontiguousarray(A.data, dtype=np.float64)
+    keep.extend([rowptr, col, val])
+    return CSR(A.shape[0], A.shape[1], A.nnz, rowptr.ctypes.data, col.ctypes.data, val.ctypes.data)
+
+
+def _dptr(t, n=None, name="vector"):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} has {t.numel()} entries, expected {n}")
+    return C.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One libamgps context on one device."""
+
+    def __init__(self, device=0, stream=None):
+        import torch
+        self._h = C.c_void_p()
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        st = lib().amgps_create(C.byref(self._h), int(device), C.c_void_p(stream))
+        if st:
+            raise AmgpsError(st, lib().amgps_last_error(None).decode())
+        self.device = device
+        self.n_levels = 0
+        self.sizes = []
+
+    def _check(self, st):
+        if st:
+            raise AmgpsError(st, lib().amgps_last_error(self._h).decode())
+
+    def close(self):
+        if self._h:
+            lib().amgps_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, A_list, P_list, prec="f64"):
+        keep = []
+        nl = len(A_list)
+        As = (CSR * nl)(*[_csr_struct(A, keep) for A in A_list])
+        Ps = (CSR * max(nl - 1, 1))(*([_csr_struct(P, keep) for P in P_list] or [CSR()]))
+        self._check(lib().amgps_hierarchy_load(self._h, nl, As, Ps, PREC[prec]))
+        self.n_levels = nl
+        self.sizes = [A.shape[0] for A in A_list]
+        self.prec = prec
+        return self
+
+    def level_info(self, level):
+        n, nnz, stored = C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(lib().amgps_level_info(self._h, level, C.byref(n), C.byref(nnz), C.byref(stored)))
+        return n.value, nnz.value, stored.value
+
+    def set_smoother(self, level, kind, degree, weights=None, rho=0.0):
+        w = None
+        if weights is not None:
+            w = np.ascontiguousarray(weights, dtype=np.float64)
+            if w.size != degree:
+                raise ValueError("weights must have `degree` entries")
+        self._check(lib().amgps_set_smoother(self._h, level, KIND[kind], degree,
+                                             None if w is None else w.ctypes.data, float(rho)))
+
+    def estimate_lambda(self, level, v0, iters=10):
+        lam = C.c_double()
+        self._check(lib().amgps_estimate_lambda(self._h, level, _dptr(v0, self._n(level), "v0"),
+                                                iters, C.byref(lam)))
+        return lam.value
+
+    def _n(self, level):
+        return self.sizes[level] if 0 <= level < len(self.sizes) else None
+
+    def smooth(self, level, kind, degree, b, x, x_is_zero=False):
+        n = self._n(level)
+        self._check(lib().amgps_smooth(self._h, level, KIND[kind], degree, _dptr(b, n, "b"),
+                                       _dptr(x, n, "x"), 1 if x_is_zero else 0))
+
+    def vcycle(self, r, z):
+        n = self._n(0)
+        self._check(lib().amgps_vcycle(self._h, _dptr(r, n, "r"), _dptr(z, n, "z")))
+
+    def pcg(self, b, x, rtol=1e-8, maxit=1000, raise_on_noconv=True):
+        n = self._n(0)
+        it, rel = C.c_int(), C.c_double()
+        st = lib().amgps_pcg(self._h, _dptr(b, n, "b"), _dptr(x, n, "x"), rtol, maxit,
+                             C.byref(it), C.byref(rel))
+        if st == 3 and not raise_on_noconv:
+            return it.value, rel.value
+        self._check(st)
+        return it.value, rel.value
+
+    def pcg_host(self, b, x, rtol=1e-8, maxit=1000):
+        """b, x: host arrays (numpy float64, or pinned CPU torch tensors)."""
+        n = self._n(0)
+        bp, xp = self._host_ptr(b, n), self._host_ptr(x, n)
+        it, rel = C.c_int(), C.c_double()
+        self._check(lib().amgps_pcg_host(self._h, bp, xp, rtol, maxit, C.byref(it), C.byref(rel)))
+        return it.value, rel.value
+
+    @staticmethod
+    def _host_ptr(a, n):
+        try:
+            import torch
+            if isinstance(a, torch.Tensor):
+                if a.is_cuda or a.dtype != torch.float64 or not a.is_contiguous() or a.numel() != n:
+                    raise TypeError("host tensor must be contiguous float64 CPU with n entries")
+                return C.c_void_p(a.data_ptr())
+        except ImportError:
+            pass
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+                and (n is None or a.size == n)):
+            raise TypeError("host array must be contiguous float64 with n entries")
+        return C.c_void_p(a.ctypes.data)
+
+    def synchronize(self):
+        self._check(lib().amgps_synchronize(self._h))
+
+    def profile(self, on=True):
+        self._check(lib().amgps_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self, cls, reset=False):
+        n, ms, by = C.c_int64(), C.c_double(), C.c_double()
+        self._check(lib().amgps_profile_read(self._h, cls, 1 if reset else 0, C.byref(n),
+                                             C.byref(ms), C.byref(by)))
+        return n.value, ms.value, by.value

@@ -1,0 +1,122 @@
+// Internal declarations shared by the libamgps translation units.
+//
+// Device matrix layout (every level): sliced ELLPACK with slices of 32
+// consecutive rows (SELL-32, no row sorting).  Entry k of row (32 s + lane) is
+// stored at val[vbase(s) + 32 k + lane], so a warp that owns a slice reads each
+// k-column of the slice as one coalesced 256-byte (FP64) line.  A slice is
+//   * "uniform" when all its rows fit one shared list of column offsets
+//     (col = row + off[k]); then no per-entry column index is stored and
+//     entries absent from a row hold 0 (their clamped column is a valid
+//     address).  Every level of a 7-point operator with geometric
+//     aggregation is uniform, so the index stream disappears.
+//   * "explicit" otherwise: col[vbase + 32 k + lane] as in plain SELL.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include "amgps.h"
+
+namespace amgps {
+
+constexpr int kSlice = 32;          // rows per slice (one warp)
+constexpr int kBlock = 256;         // threads per block of the row kernels
+constexpr int kWarpsPerBlock = kBlock / 32;
+constexpr int kMaxDegree = 16;
+
+struct SliceDesc {
+  int64_t vbase;  // index of entry (k=0, lane=0) of the slice in val[] / col[]
+  int32_t w;      // stored entries per row
+  int32_t cref;   // >= 0: uniform slice, offsets at off[cref .. cref+w); < 0: explicit
+};
+static_assert(sizeof(SliceDesc) == 16, "slice descriptor is one 16-byte load");
+
+template <class VT>
+struct DevMat {
+  int64_t n = 0;
+  int64_t nslices = 0;
+  const SliceDesc* sd = nullptr;
+  const VT* val = nullptr;
+  const int32_t* col = nullptr;  // null when every slice is uniform
+  const int32_t* off = nullptr;
+};
+
+enum Family { FAM_CHEB4 = 0, FAM_CHEB1 = 1, FAM_JAC = 2 };
+
+// Arguments of one fused smoother step (see kernels_smooth.cu).
+template <class VT, class XT>
+struct StepArgs {
+  DevMat<VT> A;
+  const XT* u = nullptr;     // vector multiplied by A (gathered)
+  const XT* rin = nullptr;   // r_{j-1}, or b on the initial / Jacobi step
+  XT* rout = nullptr;        // r_j (may equal rin); unused when not written
+  const XT* zown = nullptr;  // z_j at the row itself; null: no c1 term
+  XT* zout = nullptr;        // z_{j+1}
+  const XT* xin = nullptr;
+  XT* xout = nullptr;        // may equal xin unless u == xin
+  const XT* dinv = nullptr;  // 1 / M_i (Eq. l1smooth)
+  XT c1 = 0, c2 = 0, beta = 0, rhoinv = 1;
+  int fam = FAM_CHEB4;
+  bool init = false;
+  bool write_r = false;
+};
+
+// Device scalar slots of the Krylov solver.
+enum Scalar {
+  S_PQ = 0, S_RR = 1, S_RZ = 2, S_RZOLD = 3, S_ALPHA = 4, S_BB = 5, S_NRM = 6, S_TMP = 7,
+  S_COUNT = 16
+};
+
+struct RedWork {
+  double* part = nullptr;       // per-block partial sums [grid]
+  unsigned* counter = nullptr;  // arrival counter (reset by the last block)
+  int grid = 0;
+};
+
+// ---- launchers (kernels_smooth.cu) ----
+template <class VT, class XT>
+void launch_step(const StepArgs<VT, XT>& a, cudaStream_t s);
+template <class XT>
+void launch_first(int fam, int64_t n, const XT* b, const XT* dinv, XT* rout, XT* zout, XT* xout,
+                  XT c2, XT beta, XT rhoinv, cudaStream_t s);
+template <class VT, class XT>
+void launch_resid_restrict(const DevMat<VT>& A, const XT* x, const XT* b, const int32_t* cptr,
+                           const int32_t* cidx, int64_t nc, XT* bc, cudaStream_t s);
+template <class XT>
+void launch_prolong(int64_t n, const int32_t* agg, const XT* ec, XT* x, cudaStream_t s);
+template <class VT, class XT>
+void launch_l1diag(const DevMat<VT>& A, XT* dinv, cudaStream_t s);
+template <class A, class B>
+void launch_convert(int64_t n, const A* in, B* out, cudaStream_t s);
+
+// ---- launchers (kernels_krylov.cu) ----
+void launch_spmv_dot(const DevMat<double>& A, const double* p, double* q, const RedWork& w,
+                     double* scal, cudaStream_t s);
+void launch_cg_update(int64_t n, const double* p, const double* q, double* x, double* r,
+                      const RedWork& w, double* scal, cudaStream_t s);
+// out_slot receives a.b; if rz_shift, scal[S_RZOLD] <- scal[S_RZ] first and the dot goes to S_RZ
+void launch_dot(int64_t n, const double* a, const double* b, const RedWork& w, double* scal,
+                int out_slot, bool rz_shift, cudaStream_t s);
+void launch_xpay(int64_t n, const double* z, double* p, const double* scal, cudaStream_t s);
+template <class XT>
+void launch_coarse_gemv(int nc, const double* ainv, const XT* b, XT* x, cudaStream_t s);
+void launch_chol_inverse(int n, double* work, double* ainv, int* status, cudaStream_t s);
+template <class VT, class XT>
+void launch_power_step(const DevMat<VT>& A, const XT* v, const XT* dinv, XT* w, const RedWork& rw,
+                       double* scal, cudaStream_t s);
+template <class XT>
+void launch_scale_by_norm(int64_t n, const XT* w, XT* v, const double* scal, int slot,
+                          cudaStream_t s);
+template <class XT>
+void launch_norm2(int64_t n, const XT* v, const RedWork& rw, double* scal, int slot,
+                  cudaStream_t s);
+
+int reduction_grid(int64_t work_items, int nsm);
+
+// Kernels enqueued through the launchers above (graph captures included; the
+// host driver corrects for captures and adds graph replays).
+int64_t launches_enqueued();
+void count_launch();
+
+}  // namespace amgps

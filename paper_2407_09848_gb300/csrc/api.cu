@@ -1,0 +1,1162 @@
+// libamgps host side: the C ABI of include/amgps.h.
+//
+// Responsibilities: input validation (no device fault is ever used to report
+// bad input), conversion of host CSR into the device SELL-32 layout, the
+// aggregation transfer maps, the coarsest-level factorisation, and the host
+// drivers that sequence the kernels of one smoother application (Sec. 2.1-2.2),
+// one V-cycle (Eq. amg) and the outer PCG (Sec. 4).  The V-cycle below the
+// finest level is captured once into a CUDA graph and replayed, since those
+// levels are launch-bound; the finest level is launched eagerly so that its
+// kernels can be timed with plain CUDA events.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "amgps_internal.h"
+#include "amgps_tables.h"
+
+using namespace amgps;
+
+namespace {
+
+struct Fail {
+  amgps_status st;
+  std::string msg;
+};
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      throw Fail{AMGPS_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};      \
+  } while (0)
+#define REQ(cond, st, msg)          \
+  do {                              \
+    if (!(cond)) throw Fail{st, msg}; \
+  } while (0)
+
+thread_local std::string g_err;
+
+struct Spec {
+  int kind = AMGPS_CHEB4_OPT;
+  int k = 4;
+  double w[kMaxDegree] = {};
+  double rho = 1.0;
+};
+
+// Step coefficients of one smoother application, computed in FP64 on the host.
+struct Coefs {
+  int fam = FAM_CHEB4;
+  int k = 1;
+  double c1[kMaxDegree + 1] = {}, c2[kMaxDegree + 1] = {}, beta[kMaxDegree + 1] = {};
+  double rhoinv = 1.0;
+};
+
+Coefs make_coefs(int kind, int k, const double* w, double rho) {
+  Coefs c;
+  c.k = k;
+  if (rho <= 0.0) rho = 1.0;
+  if (kind == AMGPS_L1JACOBI) {
+    c.fam = FAM_JAC;
+    return c;
+  }
+  if (kind == AMGPS_CHEB1 || kind == AMGPS_CHEB1_OPT) {
+    // Algorithm 1 with theta, delta of Eq. optimal_parameters on [a_k*, 1]
+    c.fam = FAM_CHEB1;
+    const double a = AMGPS_ASTAR[k - 1];
+    const double theta = 0.5 * (1.0 + a), delta = 0.5 * (1.0 - a);
+    const double sigma1 = theta / delta;
+    double rho_prev = 1.0 / sigma1;
+    c.c2[0] = 1.0 / theta;  // d^(0) = r^(0) / theta
+    for (int j = 1; j < k; ++j) {
+      const double rj = 1.0 / (2.0 * sigma1 - rho_prev);
+      c.c1[j] = rj * rho_prev;
+      c.c2[j] = 2.0 * rj / delta;
+      rho_prev = rj;
+    }
+    c.rhoinv = (kind == AMGPS_CHEB1_OPT) ? 1.0 : 1.0 / rho;
+    return c;
+  }
+  // Eq. polsmoother / polsmootheropt: z_j = (2j-3)/(2j+1) z_{j-1} + (8j-4)/(2j+1)/rho M^{-1} r_{j-1}
+  c.fam = FAM_CHEB4;
+  for (int j = 1; j <= k; ++j) {
+    c.c1[j] = double(2 * j - 3) / double(2 * j + 1);
+    c.c2[j] = double(8 * j - 4) / double(2 * j + 1) / rho;
+    if (kind == AMGPS_CHEB4) c.beta[j] = 1.0;
+    else if (kind == AMGPS_CHEB4_OPT) c.beta[j] = AMGPS_OPT4_BETA[k - 1][j - 1];
+    else c.beta[j] = w[j - 1];
+  }
+  return c;
+}
+
+struct Level {
+  int64_t n = 0, nnz = 0, stored = 0, nslices = 0, explicit_entries = 0;
+  SliceDesc* sd = nullptr;
+  void* val = nullptr;
+  int32_t* col = nullptr;
+  int32_t* off = nullptr;
+  // FP64 copy of A_0 for the outer solver when the smoother path is FP32/BF16
+  SliceDesc* sd64 = nullptr;
+  double* val64 = nullptr;
+  int32_t* col64 = nullptr;
+  int32_t* off64 = nullptr;
+  int32_t* agg = nullptr;
+  int32_t* cptr = nullptr;
+  int32_t* cidx = nullptr;
+  int64_t nc = 0;
+  void* dinv = nullptr;   // 1 / M_i
+  void *b = nullptr, *x = nullptr, *r = nullptr, *za = nullptr, *zb = nullptr, *xb = nullptr;
+  double* ainv = nullptr;
+  bool coarsest = false;
+  Spec spec;
+};
+
+struct HostSell {
+  int64_t n = 0, nnz = 0, nslices = 0, stored = 0, explicit_entries = 0;
+  std::vector<SliceDesc> sd;
+  std::vector<double> val;
+  std::vector<int32_t> col;
+  std::vector<int32_t> off;
+  bool any_explicit = false;
+};
+
+void validate_csr(const amgps_csr& A, const char* what, bool square) {
+  std::string w(what);
+  REQ(A.rowptr && A.col && A.val, AMGPS_E_ARG, w + ": null array");
+  REQ(A.n_rows >= 1 && A.n_cols >= 1, AMGPS_E_ARG, w + ": empty matrix");
+  REQ(A.n_rows < (int64_t(1) << 31) && A.n_cols < (int64_t(1) << 31), AMGPS_E_ARG,
+      w + ": dimension exceeds int32");
+  REQ(!square || A.n_rows == A.n_cols, AMGPS_E_ARG, w + ": not square");
+  REQ(A.rowptr[0] == 0 && A.rowptr[A.n_rows] == A.nnz, AMGPS_E_ARG, w + ": bad rowptr ends");
+  for (int64_t i = 0; i < A.n_rows; ++i)
+    REQ(A.rowptr[i + 1] >= A.rowptr[i], AMGPS_E_ARG, w + ": rowptr not monotone");
+  for (int64_t e = 0; e < A.nnz; ++e) {
+    REQ(A.col[e] >= 0 && A.col[e] < A.n_cols, AMGPS_E_ARG, w + ": column index out of range");
+    REQ(std::isfinite(A.val[e]), AMGPS_E_ARG, w + ": non-finite value");
+  }
+}
+
+HostSell build_sell(const amgps_csr& A) {
+  HostSell h;
+  const int64_t n = A.n_rows;
+  h.n = n;
+  h.nnz = A.nnz;
+  h.nslices = (n + kSlice - 1) / kSlice;
+  h.sd.resize(h.nslices);
+  std::map<std::vector<int32_t>, int32_t> pats;
+  std::vector<int32_t> prev;
+  int32_t prev_ref = -1;
+  std::vector<int64_t> offs;
+  int64_t vbase = 0;
+  for (int64_t s = 0; s < h.nslices; ++s) {
+    const int64_t r0 = s * kSlice, r1 = std::min(n, r0 + kSlice);
+    int maxlen = 0;
+    for (int64_t r = r0; r < r1; ++r) maxlen = std::max(maxlen, A.rowptr[r + 1] - A.rowptr[r]);
+    // fast path: every offset of the slice already in the previous pattern
+    bool reuse = prev_ref >= 0 && (int64_t)prev.size() <= maxlen + 1;
+    for (int64_t r = r0; r < r1 && reuse; ++r)
+      for (int e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e) {
+        const int32_t o = (int32_t)((int64_t)A.col[e] - r);
+        if (!std::binary_search(prev.begin(), prev.end(), o)) {
+          reuse = false;
+          break;
+        }
+      }
+    if (reuse) {
+      h.sd[s] = SliceDesc{vbase, (int32_t)prev.size(), prev_ref};
+      vbase += (int64_t)prev.size() * kSlice;
+      continue;
+    }
+    offs.clear();
+    for (int64_t r = r0; r < r1; ++r)
+      for (int e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e) offs.push_back((int64_t)A.col[e] - r);
+    std::sort(offs.begin(), offs.end());
+    offs.erase(std::unique(offs.begin(), offs.end()), offs.end());
+    const bool uniform = (int64_t)offs.size() <= maxlen + 1 && offs.size() <= 64;
+    if (uniform) {
+      std::vector<int32_t> p(offs.begin(), offs.end());
+      auto it = pats.find(p);
+      int32_t ref;
+      if (it == pats.end()) {
+        ref = (int32_t)h.off.size();
+        h.off.insert(h.off.end(), p.begin(), p.end());
+        pats.emplace(p, ref);
+      } else {
+        ref = it->second;
+      }
+      prev = p;
+      prev_ref = ref;
+      h.sd[s] = SliceDesc{vbase, (int32_t)p.size(), ref};
+      vbase += (int64_t)p.size() * kSlice;
+    } else {
+      h.sd[s] = SliceDesc{vbase, (int32_t)maxlen, -1};
+      vbase += (int64_t)maxlen * kSlice;
+      h.any_explicit = true;
+      h.explicit_entries += (int64_t)maxlen * kSlice;
+    }
+  }
+  h.stored = vbase;
+  h.val.assign(vbase, 0.0);
+  if (h.any_explicit) h.col.assign(vbase, 0);
+  std::vector<std::pair<int32_t, double>> rowbuf;
+  for (int64_t s = 0; s < h.nslices; ++s) {
+    const SliceDesc d = h.sd[s];
+    const int64_t r0 = s * kSlice, r1 = std::min(n, r0 + kSlice);
+    for (int64_t r = r0; r < r1; ++r) {
+      const int lane = (int)(r - r0);
+      if (d.cref >= 0) {
+        uint64_t filled = 0;
+        for (int e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e) {
+          const int32_t o = (int32_t)((int64_t)A.col[e] - r);
+          const int32_t* p = h.off.data() + d.cref;
+          const int k = (int)(std::lower_bound(p, p + d.w, o) - p);
+          REQ(!(filled >> k & 1u), AMGPS_E_ARG, "duplicate entry in CSR row");
+          filled |= uint64_t(1) << k;
+          h.val[d.vbase + (int64_t)k * kSlice + lane] = A.val[e];
+        }
+      } else {
+        rowbuf.clear();
+        for (int e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e) rowbuf.emplace_back(A.col[e], A.val[e]);
+        std::sort(rowbuf.begin(), rowbuf.end());
+        for (size_t k = 0; k < rowbuf.size(); ++k) {
+          REQ(k == 0 || rowbuf[k].first != rowbuf[k - 1].first, AMGPS_E_ARG,
+              "duplicate entry in CSR row");
+          h.val[d.vbase + (int64_t)k * kSlice + lane] = rowbuf[k].second;
+          h.col[d.vbase + (int64_t)k * kSlice + lane] = rowbuf[k].first;
+        }
+        for (int k = (int)rowbuf.size(); k < d.w; ++k)
+          h.col[d.vbase + (int64_t)k * kSlice + lane] = (int32_t)r;
+      }
+    }
+  }
+  return h;
+}
+
+// FP64 -> BF16 round-to-nearest-even taken directly from the double (no
+// intermediate FP32 rounding): compare against the neighbouring BF16 values.
+uint16_t dbl_to_bf16(double x) {
+  float f = (float)x;
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  uint32_t base = u & 0xFFFF0000u;
+  auto val = [](uint32_t bits) {
+    float g;
+    std::memcpy(&g, &bits, 4);
+    return (double)g;
+  };
+  uint32_t best = base;
+  double bestd = std::fabs(val(base) - x);
+  for (int d = -1; d <= 1; d += 2) {
+    const uint32_t cand = base + (uint32_t)(d * 0x10000);
+    const double cd = std::fabs(val(cand) - x);
+    if (std::isfinite(val(cand)) &&
+        (cd < bestd || (cd == bestd && ((cand >> 16) & 1u) == 0 && ((best >> 16) & 1u) == 1))) {
+      best = cand;
+      bestd = cd;
+    }
+  }
+  return (uint16_t)(best >> 16);
+}
+
+}  // namespace
+
+struct amgps_ctx {
+  int device = 0;
+  int nsm = 0;
+  cudaStream_t ustream = nullptr, stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_sync = nullptr;
+  std::string err;
+  bool loaded = false;
+  amgps_prec prec = AMGPS_F64;
+  std::vector<Level> lv;
+  std::vector<void*> allocs;
+  double *pr = nullptr, *pp = nullptr, *pq = nullptr, *pz = nullptr;
+  double *stage_b = nullptr, *stage_x = nullptr;
+  double* h_stage = nullptr;
+  size_t h_stage_n = 0;
+  double* dscal = nullptr;
+  double* hscal = nullptr;
+  double* part = nullptr;
+  unsigned* counters = nullptr;
+  int red_grid = 0;
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_ok = false;
+  int64_t graph_kernels = 0;   // kernel nodes in gexec
+  int64_t launch_adjust = 0;   // captured (not run) launches removed, replays added
+  int64_t launch_base = 0;     // reset point of the launch counter
+  bool prof = false;
+  struct Pair {
+    cudaEvent_t a, b;
+    int cls;
+    double bytes;
+  };
+  std::vector<Pair> pending;
+  std::vector<cudaEvent_t> pool;
+  int64_t prof_launches[3] = {};
+  double prof_ms[3] = {};
+  double prof_bytes[3] = {};
+};
+
+namespace {
+
+template <class F>
+amgps_status guard(amgps_ctx* c, F&& f) {
+  try {
+    f();
+    if (c) c->err.clear();
+    return AMGPS_OK;
+  } catch (const Fail& e) {
+    if (c) c->err = e.msg;
+    else g_err = e.msg;
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    if (c) c->err = "host allocation failed";
+    else g_err = "host allocation failed";
+    return AMGPS_E_NOMEM;
+  } catch (...) {
+    if (c) c->err = "unexpected C++ exception";
+    else g_err = "unexpected C++ exception";
+    return AMGPS_E_ARG;
+  }
+}
+
+void* dalloc(amgps_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Fail{AMGPS_E_NOMEM, std::string("cudaMalloc of ") + std::to_string(bytes) +
+                                  " bytes failed: " + cudaGetErrorString(e)};
+  }
+  c->allocs.push_back(p);
+  return p;
+}
+
+template <class T>
+T* dupload(amgps_ctx* c, const T* h, size_t count) {
+  T* d = (T*)dalloc(c, count * sizeof(T));
+  if (count) CK(cudaMemcpy(d, h, count * sizeof(T), cudaMemcpyHostToDevice));
+  return d;
+}
+
+void free_hierarchy(amgps_ctx* c) {
+  if (c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  c->graph_ok = false;
+  if (!c->allocs.empty()) cudaStreamSynchronize(c->stream);
+  for (void* p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+  c->lv.clear();
+  c->loaded = false;
+  c->pr = c->pp = c->pq = c->pz = c->stage_b = c->stage_x = nullptr;
+}
+
+void enter(amgps_ctx* c) {
+  CK(cudaSetDevice(c->device));
+  CK(cudaEventRecord(c->ev_in, c->ustream));
+  CK(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
+}
+
+void leave(amgps_ctx* c) {
+  CK(cudaEventRecord(c->ev_out, c->stream));
+  CK(cudaStreamWaitEvent(c->ustream, c->ev_out, 0));
+}
+
+void check_launch() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    throw Fail{AMGPS_E_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e)};
+}
+
+RedWork redwork(amgps_ctx* c, int slot, int64_t work) {
+  RedWork w;
+  w.part = c->part;
+  w.counter = c->counters + slot;
+  w.grid = reduction_grid(work, c->nsm);
+  return w;
+}
+
+// ---- profiling: event pairs around selected launches, harvested on sync ----
+cudaEvent_t take_event(amgps_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  CK(cudaEventCreate(&e));
+  return e;
+}
+
+void harvest(amgps_ctx* c) {
+  for (auto& p : c->pending) {
+    float ms = 0.f;
+    CK(cudaEventSynchronize(p.b));
+    CK(cudaEventElapsedTime(&ms, p.a, p.b));
+    c->prof_launches[p.cls] += 1;
+    c->prof_ms[p.cls] += ms;
+    c->prof_bytes[p.cls] += p.bytes;
+    c->pool.push_back(p.a);
+    c->pool.push_back(p.b);
+  }
+  c->pending.clear();
+}
+
+struct ProfScope {
+  amgps_ctx* c;
+  bool on;
+  cudaEvent_t a{}, b{};
+  int cls;
+  double bytes;
+  ProfScope(amgps_ctx* c_, bool want, int cls_, double bytes_) : c(c_), on(want && c_->prof),
+                                                                  cls(cls_), bytes(bytes_) {
+    if (on) {
+      a = take_event(c);
+      b = take_event(c);
+      CK(cudaEventRecord(a, c->stream));
+    }
+  }
+  void done() {
+    if (on) {
+      CK(cudaEventRecord(b, c->stream));
+      c->pending.push_back({a, b, cls, bytes});
+      on = false;
+    }
+  }
+};
+
+template <class VT>
+DevMat<VT> devmat(const Level& L) {
+  DevMat<VT> m;
+  m.n = L.n;
+  m.nslices = L.nslices;
+  m.sd = L.sd;
+  m.val = (const VT*)L.val;
+  m.col = L.col;
+  m.off = L.off;
+  return m;
+}
+
+DevMat<double> devmat64(const Level& L, amgps_prec prec) {
+  if (prec == AMGPS_F64) return devmat<double>(L);
+  DevMat<double> m;
+  m.n = L.n;
+  m.nslices = L.nslices;
+  m.sd = L.sd64;
+  m.val = L.val64;
+  m.col = L.col64;
+  m.off = L.off64;
+  return m;
+}
+
+// Algorithmic bytes of one fused step: A's nonzeros and stored indices once,
+// each live vector stream once.
+template <class VT, class XT>
+double step_bytes(const Level& L, int nvec) {
+  return (double)L.nnz * sizeof(VT) + (double)L.explicit_entries * 4.0 +
+         (double)L.n * sizeof(XT) * nvec;
+}
+
+// ---------------------------------------------------------------------------
+// Engine: the kernel sequences, templated on matrix value type VT and vector
+// type XT (FP64/FP64, FP32/FP32, BF16/FP32).
+// ---------------------------------------------------------------------------
+template <class VT, class XT>
+struct Engine {
+  // One smoother application on level l: x <- S(b, x) (x = 0 when xzero).
+  static void smooth(amgps_ctx* c, int l, const Coefs& cf, const XT* b, XT* x, bool xzero) {
+    Level& L = c->lv[l];
+    cudaStream_t s = c->stream;
+    const DevMat<VT> A = devmat<VT>(L);
+    const XT* md = (const XT*)L.dinv;
+    XT* r = (XT*)L.r;
+    XT* zc = (XT*)L.za;
+    XT* zn = (XT*)L.zb;
+    XT* xb = (XT*)L.xb;
+    const int k = cf.k;
+    const bool profl = (l == 0);
+    if (cf.fam == FAM_JAC) {
+      XT* cur = x;
+      XT* oth = xb;
+      int j0 = 0;
+      if (xzero) {
+        launch_first<XT>(FAM_JAC, L.n, b, md, nullptr, nullptr, cur, XT(0), XT(0), XT(1), s);
+        j0 = 1;
+      }
+      for (int j = j0; j < k; ++j) {
+        StepArgs<VT, XT> a;
+        a.A = A;
+        a.u = cur;
+        a.rin = b;
+        a.xin = cur;
+        a.xout = oth;
+        a.dinv = md;
+        a.fam = FAM_JAC;
+        a.init = true;
+        ProfScope ps(c, profl, 0, step_bytes<VT, XT>(L, 4));
+        launch_step<VT, XT>(a, s);
+        ps.done();
+        std::swap(cur, oth);
+      }
+      if (cur != x) CK(cudaMemcpyAsync(x, cur, L.n * sizeof(XT), cudaMemcpyDeviceToDevice, s));
+      check_launch();
+      return;
+    }
+    const XT* rin_next;
+    XT* xcur = x;
+    if (xzero) {
+      const double c2 = (cf.fam == FAM_CHEB4) ? cf.c2[1] : cf.c2[0];
+      launch_first<XT>(cf.fam, L.n, b, md, r, zc, x, XT(c2), XT(cf.beta[1]), XT(cf.rhoinv), s);
+      rin_next = (cf.fam == FAM_CHEB4) ? b : r;
+    } else {
+      StepArgs<VT, XT> a;
+      a.A = A;
+      a.u = x;
+      a.rin = b;
+      a.rout = r;
+      a.write_r = k > 1;
+      a.zout = zc;
+      a.xin = x;
+      a.xout = xb;
+      a.dinv = md;
+      a.c2 = XT(cf.fam == FAM_CHEB4 ? cf.c2[1] : cf.c2[0]);
+      a.beta = XT(cf.beta[1]);
+      a.rhoinv = XT(cf.rhoinv);
+      a.fam = cf.fam;
+      a.init = true;
+      ProfScope ps(c, profl, 0, step_bytes<VT, XT>(L, a.write_r ? 6 : 5));
+      launch_step<VT, XT>(a, s);
+      ps.done();
+      xcur = xb;
+      rin_next = r;
+    }
+    for (int j = 1; j < k; ++j) {
+      StepArgs<VT, XT> a;
+      a.A = A;
+      a.u = zc;
+      a.rin = rin_next;
+      a.rout = r;
+      a.write_r = (j < k - 1);
+      a.zown = zc;
+      a.zout = zn;
+      a.xin = xcur;
+      a.xout = x;
+      a.dinv = md;
+      if (cf.fam == FAM_CHEB4) {
+        a.c1 = XT(cf.c1[j + 1]);
+        a.c2 = XT(cf.c2[j + 1]);
+        a.beta = XT(cf.beta[j + 1]);
+      } else {
+        a.c1 = XT(cf.c1[j]);
+        a.c2 = XT(cf.c2[j]);
+      }
+      a.rhoinv = XT(cf.rhoinv);
+      a.fam = cf.fam;
+      a.init = false;
+      ProfScope ps(c, profl, 0, step_bytes<VT, XT>(L, a.write_r ? 7 : 6));
+      launch_step<VT, XT>(a, s);
+      ps.done();
+      xcur = x;
+      rin_next = r;
+      std::swap(zc, zn);
+    }
+    if (xcur != x) CK(cudaMemcpyAsync(x, xcur, L.n * sizeof(XT), cudaMemcpyDeviceToDevice, s));
+    check_launch();
+  }
+
+  static void vcycle_level(amgps_ctx* c, int l, const XT* b, XT* x) {
+    Level& L = c->lv[l];
+    cudaStream_t s = c->stream;
+    if (L.coarsest) {
+      launch_coarse_gemv<XT>((int)L.n, L.ainv, b, x, s);
+      check_launch();
+      return;
+    }
+    const Coefs cf = make_coefs(L.spec.kind, L.spec.k, L.spec.w, L.spec.rho);
+    smooth(c, l, cf, b, x, true);
+    Level& C = c->lv[l + 1];
+    {
+      ProfScope ps(c, l == 0, 1,
+                   (double)L.nnz * sizeof(VT) + (double)L.explicit_entries * 4.0 +
+                       (double)L.n * sizeof(XT) * 2 + (double)L.n * 4 + (double)C.n * 12);
+      launch_resid_restrict<VT, XT>(devmat<VT>(L), x, b, L.cptr, L.cidx, L.nc, (XT*)C.b, s);
+      ps.done();
+    }
+    if (l + 1 == 1 && c->graph_ok && !capturing(c)) {
+      CK(cudaGraphLaunch(c->gexec, s));
+      c->launch_adjust += c->graph_kernels;
+    } else {
+      vcycle_level(c, l + 1, (const XT*)C.b, (XT*)C.x);
+    }
+    launch_prolong<XT>(L.n, L.agg, (const XT*)C.x, x, s);
+    smooth(c, l, cf, b, x, false);
+    check_launch();
+  }
+
+  static bool capturing(amgps_ctx* c) {
+    cudaStreamCaptureStatus st;
+    CK(cudaStreamIsCapturing(c->stream, &st));
+    return st != cudaStreamCaptureStatusNone;
+  }
+
+  // Capture levels >= 1 of the V-cycle into a graph (fixed internal buffers).
+  static void build_graph(amgps_ctx* c) {
+    if (c->graph_ok || c->lv.size() < 2) return;
+    if (c->gexec) {
+      CK(cudaGraphExecDestroy(c->gexec));
+      c->gexec = nullptr;
+    }
+    cudaGraph_t g;
+    const int64_t before = launches_enqueued();
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    try {
+      vcycle_level(c, 1, (const XT*)c->lv[1].b, (XT*)c->lv[1].x);
+    } catch (...) {
+      cudaGraph_t junk;
+      cudaStreamEndCapture(c->stream, &junk);
+      if (junk) cudaGraphDestroy(junk);
+      cudaGetLastError();
+      throw;
+    }
+    CK(cudaStreamEndCapture(c->stream, &g));
+    c->graph_kernels = launches_enqueued() - before;
+    c->launch_adjust -= c->graph_kernels;
+    cudaError_t e = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    c->graph_ok = true;
+  }
+
+  // z = B r on level 0 with FP64 vectors at the boundary.
+  static void vcycle(amgps_ctx* c, const double* r, double* z) {
+    build_graph(c);
+    Level& L = c->lv[0];
+    if constexpr (std::is_same<XT, double>::value) {
+      vcycle_level(c, 0, r, z);
+    } else {
+      launch_convert<double, XT>(L.n, r, (XT*)L.b, c->stream);
+      vcycle_level(c, 0, (const XT*)L.b, (XT*)L.x);
+      launch_convert<XT, double>(L.n, (const XT*)L.x, z, c->stream);
+    }
+    check_launch();
+  }
+
+  static void smooth_public(amgps_ctx* c, int l, const Coefs& cf, const double* b, double* x,
+                            bool xzero) {
+    if constexpr (std::is_same<XT, double>::value) {
+      smooth(c, l, cf, b, x, xzero);
+    } else {
+      Level& L = c->lv[l];
+      // the level's own rhs / solution buffers serve as FP32 staging here
+      launch_convert<double, XT>(L.n, b, (XT*)L.b, c->stream);
+      if (!xzero) launch_convert<double, XT>(L.n, x, (XT*)L.x, c->stream);
+      smooth(c, l, cf, (const XT*)L.b, (XT*)L.x, xzero);
+      launch_convert<XT, double>(L.n, (const XT*)L.x, x, c->stream);
+      check_launch();
+    }
+  }
+
+  static double lambda(amgps_ctx* c, int l, const double* v0, int iters) {
+    Level& L = c->lv[l];
+    cudaStream_t s = c->stream;
+    XT* v = (XT*)L.za;
+    XT* w = (XT*)L.zb;
+    launch_convert<double, XT>(L.n, v0, w, s);
+    RedWork rw = redwork(c, 3, L.n);
+    launch_norm2<XT>(L.n, w, rw, c->dscal, S_NRM, s);
+    launch_scale_by_norm<XT>(L.n, w, v, c->dscal, S_NRM, s);
+    const DevMat<VT> A = devmat<VT>(L);
+    RedWork rs = redwork(c, 4, L.n);
+    for (int i = 0; i < iters; ++i) {
+      launch_power_step<VT, XT>(A, v, (const XT*)L.dinv, w, rs, c->dscal, s);
+      if (i + 1 < iters) launch_scale_by_norm<XT>(L.n, w, v, c->dscal, S_NRM, s);
+    }
+    check_launch();
+    CK(cudaMemcpyAsync(c->hscal, c->dscal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return std::sqrt(c->hscal[S_NRM]);
+  }
+};
+
+// Type dispatch on the context's precision.
+template <class F>
+void with_engine(amgps_ctx* c, F&& f) {
+  switch (c->prec) {
+    case AMGPS_F64:
+      f(Engine<double, double>{});
+      break;
+    case AMGPS_F32:
+      f(Engine<float, float>{});
+      break;
+    default:
+      f(Engine<__nv_bfloat16, float>{});
+  }
+}
+
+void need_loaded(amgps_ctx* c) {
+  REQ(c != nullptr, AMGPS_E_ARG, "null context");
+  REQ(c->loaded, AMGPS_E_STATE, "no hierarchy loaded");
+}
+
+void check_kind_degree(int kind, int degree) {
+  REQ(kind >= AMGPS_L1JACOBI && kind <= AMGPS_WEIGHTS, AMGPS_E_ARG, "unknown smoother kind");
+  REQ(degree >= 1 && degree <= kMaxDegree, AMGPS_E_ARG, "degree must be in 1..16");
+}
+
+// Outer PCG (Sec. 4; standard Hestenes-Stiefel form, one V-cycle per iteration).
+void pcg_impl(amgps_ctx* c, const double* b, double* x, double rtol, int maxit, int* iters,
+              double* relres, bool* converged) {
+  Level& L = c->lv[0];
+  cudaStream_t s = c->stream;
+  const int64_t n = L.n;
+  const DevMat<double> A = devmat64(L, c->prec);
+  RedWork rw_dot = redwork(c, 0, n), rw_spmv = redwork(c, 1, n), rw_upd = redwork(c, 2, n);
+  rw_spmv.grid = reduction_grid(L.nslices * kSlice, c->nsm);
+  CK(cudaMemcpyAsync(c->pr, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  launch_dot(n, b, b, rw_dot, c->dscal, S_BB, false, s);
+  with_engine(c, [&](auto eng) { decltype(eng)::vcycle(c, c->pr, c->pz); });
+  launch_dot(n, c->pr, c->pz, rw_dot, c->dscal, S_RZ, true, s);
+  CK(cudaMemcpyAsync(c->pp, c->pz, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(c->hscal, c->dscal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  harvest(c);
+  const double bnorm = std::sqrt(c->hscal[S_BB]);
+  *converged = false;
+  *iters = 0;
+  *relres = 0.0;
+  if (bnorm == 0.0) {
+    *converged = true;
+    return;
+  }
+  REQ(std::isfinite(bnorm), AMGPS_E_NAN, "right-hand side is not finite");
+  int it = 0;
+  double rel = 1.0;
+  for (it = 1; it <= maxit; ++it) {
+    {
+      ProfScope ps(c, true, 2, (double)L.nnz * 8 + (double)L.explicit_entries * 4.0 + n * 8.0 * 2);
+      launch_spmv_dot(A, c->pp, c->pq, rw_spmv, c->dscal, s);
+      ps.done();
+    }
+    launch_cg_update(n, c->pp, c->pq, x, c->pr, rw_upd, c->dscal, s);
+    check_launch();
+    CK(cudaMemcpyAsync(c->hscal, c->dscal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(c->ev_sync, s));
+    CK(cudaEventSynchronize(c->ev_sync));
+    harvest(c);
+    const double pq = c->hscal[S_PQ], rr = c->hscal[S_RR];
+    REQ(std::isfinite(pq) && std::isfinite(rr), AMGPS_E_NAN, "NaN/Inf in PCG scalars");
+    REQ(pq > 0.0, AMGPS_E_NOT_SPD, "p^T A p <= 0 in PCG");
+    rel = std::sqrt(rr) / bnorm;
+    if (rel <= rtol) break;
+    if (it == maxit) break;
+    with_engine(c, [&](auto eng) { decltype(eng)::vcycle(c, c->pr, c->pz); });
+    launch_dot(n, c->pr, c->pz, rw_dot, c->dscal, S_RZ, true, s);
+    launch_xpay(n, c->pz, c->pp, c->dscal, s);
+    check_launch();
+  }
+  *iters = std::min(it, maxit);
+  *relres = rel;
+  *converged = rel <= rtol;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int amgps_version(void) { return 1; }
+
+const char* amgps_last_error(const amgps_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_err.c_str();
+}
+
+amgps_status amgps_create(amgps_ctx** out, int device, void* user_stream) {
+  if (!out) {
+    g_err = "null output pointer";
+    return AMGPS_E_ARG;
+  }
+  *out = nullptr;
+  amgps_ctx* c = nullptr;
+  amgps_status st = guard(nullptr, [&] {
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    REQ(device >= 0 && device < ndev, AMGPS_E_ARG, "device index out of range");
+    CK(cudaSetDevice(device));
+    std::unique_ptr<amgps_ctx> u(new amgps_ctx());
+    u->device = device;
+    CK(cudaDeviceGetAttribute(&u->nsm, cudaDevAttrMultiProcessorCount, device));
+    u->ustream = (cudaStream_t)user_stream;
+    CK(cudaStreamCreateWithFlags(&u->stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&u->ev_in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&u->ev_out, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&u->ev_sync, cudaEventDisableTiming | cudaEventBlockingSync));
+    CK(cudaMalloc(&u->dscal, S_COUNT * sizeof(double)));
+    CK(cudaMemset(u->dscal, 0, S_COUNT * sizeof(double)));
+    CK(cudaMallocHost(&u->hscal, S_COUNT * sizeof(double)));
+    const int maxgrid = u->nsm * 4;
+    CK(cudaMalloc(&u->part, (size_t)maxgrid * sizeof(double)));
+    CK(cudaMalloc(&u->counters, 8 * sizeof(unsigned)));
+    CK(cudaMemset(u->counters, 0, 8 * sizeof(unsigned)));
+    c = u.release();
+  });
+  if (st == AMGPS_OK) *out = c;
+  return st;
+}
+
+amgps_status amgps_destroy(amgps_ctx* c) {
+  if (!c) return AMGPS_OK;
+  cudaSetDevice(c->device);
+  free_hierarchy(c);
+  for (auto& p : c->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : c->pool) cudaEventDestroy(e);
+  if (c->h_stage) cudaFreeHost(c->h_stage);
+  if (c->hscal) cudaFreeHost(c->hscal);
+  if (c->dscal) cudaFree(c->dscal);
+  if (c->part) cudaFree(c->part);
+  if (c->counters) cudaFree(c->counters);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  if (c->ev_sync) cudaEventDestroy(c->ev_sync);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return AMGPS_OK;
+}
+
+amgps_status amgps_hierarchy_load(amgps_ctx* c, int n_levels, const amgps_csr* A,
+                                  const amgps_csr* P, amgps_prec prec) {
+  return guard(c, [&] {
+    REQ(c, AMGPS_E_ARG, "null context");
+    REQ(A && n_levels >= 1 && n_levels <= 32, AMGPS_E_ARG, "bad level count or null A");
+    REQ(n_levels == 1 || P, AMGPS_E_ARG, "null P");
+    REQ(prec == AMGPS_F64 || prec == AMGPS_F32 || prec == AMGPS_BF16, AMGPS_E_ARG,
+        "unknown precision");
+    // validate everything before touching the device
+    for (int l = 0; l < n_levels; ++l) {
+      validate_csr(A[l], "A", true);
+      // SPD needs a positive diagonal; M_i = sum |a_ij| then bounds rho(M^{-1}A) <= 1
+      for (int64_t i = 0; i < A[l].n_rows; ++i) {
+        bool found = false;
+        for (int e = A[l].rowptr[i]; e < A[l].rowptr[i + 1]; ++e)
+          if (A[l].col[e] == i) {
+            REQ(A[l].val[e] > 0.0, AMGPS_E_NOT_SPD, "non-positive diagonal entry");
+            found = true;
+          }
+        REQ(found, AMGPS_E_NOT_SPD, "missing diagonal entry");
+      }
+    }
+    for (int l = 0; l + 1 < n_levels; ++l) {
+      validate_csr(P[l], "P", false);
+      REQ(P[l].n_rows == A[l].n_rows && P[l].n_cols == A[l + 1].n_rows, AMGPS_E_ARG,
+          "P dimensions do not match A_l / A_{l+1}");
+      for (int64_t i = 0; i < P[l].n_rows; ++i) {
+        REQ(P[l].rowptr[i + 1] - P[l].rowptr[i] == 1, AMGPS_E_ARG,
+            "P is not an unsmoothed aggregation (one entry per row)");
+        REQ(P[l].val[P[l].rowptr[i]] == 1.0, AMGPS_E_ARG, "P entries must equal 1");
+      }
+    }
+    REQ(A[n_levels - 1].n_rows <= 1024, AMGPS_E_ARG, "coarsest level larger than 1024 rows");
+    enter(c);
+    CK(cudaStreamSynchronize(c->stream));
+    free_hierarchy(c);
+    c->prec = prec;
+    c->lv.resize(n_levels);
+    const size_t xs = (prec == AMGPS_F64) ? sizeof(double) : sizeof(float);
+    for (int l = 0; l < n_levels; ++l) {
+      Level& L = c->lv[l];
+      L.n = A[l].n_rows;
+      L.nnz = A[l].nnz;
+      L.coarsest = (l == n_levels - 1);
+      L.b = dalloc(c, L.n * xs);
+      L.x = dalloc(c, L.n * xs);
+      if (L.coarsest) {
+        std::vector<double> dense((size_t)L.n * L.n, 0.0);
+        for (int64_t i = 0; i < L.n; ++i)
+          for (int e = A[l].rowptr[i]; e < A[l].rowptr[i + 1]; ++e)
+            dense[(size_t)i * L.n + A[l].col[e]] = A[l].val[e];
+        double* work = dupload(c, dense.data(), dense.size());
+        L.ainv = (double*)dalloc(c, dense.size() * sizeof(double));
+        int* dstat = (int*)dalloc(c, sizeof(int));
+        CK(cudaMemsetAsync(dstat, 0, sizeof(int), c->stream));
+        launch_chol_inverse((int)L.n, work, L.ainv, dstat, c->stream);
+        check_launch();
+        int hstat = 0;
+        CK(cudaMemcpyAsync(&hstat, dstat, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        REQ(hstat == 0, AMGPS_E_NOT_SPD, "coarsest matrix: Cholesky pivot not positive");
+        // a single-level hierarchy also needs the SELL form of A_0 for the PCG SpMV
+        if (l > 0) continue;
+      }
+      HostSell h = build_sell(A[l]);
+      L.nslices = h.nslices;
+      L.stored = h.stored;
+      L.explicit_entries = h.explicit_entries;
+      L.sd = dupload(c, h.sd.data(), h.sd.size());
+      if (h.off.empty()) h.off.push_back(0);  // every slice explicit: keep a valid pointer
+      L.off = dupload(c, h.off.data(), h.off.size());
+      L.col = h.any_explicit ? dupload(c, h.col.data(), h.col.size()) : nullptr;
+      if (prec == AMGPS_F64) {
+        L.val = dupload(c, h.val.data(), h.val.size());
+      } else if (prec == AMGPS_F32) {
+        std::vector<float> f(h.val.size());
+        for (size_t i = 0; i < f.size(); ++i) f[i] = (float)h.val[i];
+        L.val = dupload(c, f.data(), f.size());
+      } else {
+        std::vector<uint16_t> f(h.val.size());
+        for (size_t i = 0; i < f.size(); ++i) f[i] = dbl_to_bf16(h.val[i]);
+        L.val = dupload(c, f.data(), f.size());
+      }
+      if (l == 0 && prec != AMGPS_F64) {
+        L.sd64 = L.sd;
+        L.off64 = L.off;
+        L.col64 = L.col;
+        L.val64 = dupload(c, h.val.data(), h.val.size());
+      }
+      if (L.coarsest) continue;  // single-level hierarchy: SELL for the PCG SpMV only
+      L.dinv = dalloc(c, L.n * xs);
+      L.r = dalloc(c, L.n * xs);
+      L.za = dalloc(c, L.n * xs);
+      L.zb = dalloc(c, L.n * xs);
+      L.xb = dalloc(c, L.n * xs);
+      if (prec == AMGPS_F64) launch_l1diag<double, double>(devmat<double>(L), (double*)L.dinv, c->stream);
+      else if (prec == AMGPS_F32) launch_l1diag<float, float>(devmat<float>(L), (float*)L.dinv, c->stream);
+      else launch_l1diag<__nv_bfloat16, float>(devmat<__nv_bfloat16>(L), (float*)L.dinv, c->stream);
+      check_launch();
+      // aggregation maps: agg[i] and the children lists of every coarse row
+      const amgps_csr& Pl = P[l];
+      const int64_t nc = Pl.n_cols;
+      std::vector<int32_t> agg(L.n), cptr(nc + 1, 0), cidx(L.n);
+      for (int64_t i = 0; i < L.n; ++i) {
+        agg[i] = Pl.col[Pl.rowptr[i]];
+        cptr[agg[i] + 1]++;
+      }
+      for (int64_t I = 0; I < nc; ++I) {
+        REQ(cptr[I + 1] > 0, AMGPS_E_ARG, "P has an empty aggregate (zero column)");
+        cptr[I + 1] += cptr[I];
+      }
+      std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
+      for (int64_t i = 0; i < L.n; ++i) cidx[fill[agg[i]]++] = (int32_t)i;
+      L.nc = nc;
+      L.agg = dupload(c, agg.data(), agg.size());
+      L.cptr = dupload(c, cptr.data(), cptr.size());
+      L.cidx = dupload(c, cidx.data(), cidx.size());
+      L.spec = Spec{};
+    }
+    const int64_t n0 = c->lv[0].n;
+    c->pr = (double*)dalloc(c, n0 * sizeof(double));
+    c->pp = (double*)dalloc(c, n0 * sizeof(double));
+    c->pq = (double*)dalloc(c, n0 * sizeof(double));
+    c->pz = (double*)dalloc(c, n0 * sizeof(double));
+    c->stage_b = (double*)dalloc(c, n0 * sizeof(double));
+    c->stage_x = (double*)dalloc(c, n0 * sizeof(double));
+    CK(cudaStreamSynchronize(c->stream));
+    c->loaded = true;
+    leave(c);
+  });
+}
+
+amgps_status amgps_level_info(amgps_ctx* c, int level, int64_t* n, int64_t* nnz, int64_t* stored) {
+  return guard(c, [&] {
+    need_loaded(c);
+    REQ(level >= 0 && level < (int)c->lv.size(), AMGPS_E_ARG, "level out of range");
+    if (n) *n = c->lv[level].n;
+    if (nnz) *nnz = c->lv[level].nnz;
+    if (stored) *stored = c->lv[level].stored;
+  });
+}
+
+amgps_status amgps_set_smoother(amgps_ctx* c, int level, amgps_kind kind, int degree,
+                                const double* weights, double rho) {
+  return guard(c, [&] {
+    need_loaded(c);
+    check_kind_degree(kind, degree);
+    const int nl = (int)c->lv.size();
+    REQ(level == -1 || (level >= 0 && level < nl - 1), AMGPS_E_ARG,
+        "level must be -1 or a non-coarsest level");
+    REQ(kind != AMGPS_WEIGHTS || weights, AMGPS_E_ARG, "AMGPS_WEIGHTS needs weights");
+    if (weights)
+      for (int j = 0; j < degree; ++j)
+        REQ(std::isfinite(weights[j]), AMGPS_E_ARG, "non-finite weight");
+    REQ(std::isfinite(rho), AMGPS_E_ARG, "non-finite rho");
+    for (int l = 0; l < nl - 1; ++l) {
+      if (level != -1 && level != l) continue;
+      Spec& s = c->lv[l].spec;
+      s.kind = kind;
+      s.k = degree;
+      s.rho = rho > 0.0 ? rho : 1.0;
+      std::fill(s.w, s.w + kMaxDegree, 0.0);
+      if (weights) std::copy(weights, weights + degree, s.w);
+    }
+    c->graph_ok = false;
+  });
+}
+
+amgps_status amgps_estimate_lambda(amgps_ctx* c, int level, const double* v0, int iters,
+                                   double* lambda_out) {
+  return guard(c, [&] {
+    need_loaded(c);
+    REQ(level >= 0 && level < (int)c->lv.size() - 1, AMGPS_E_ARG, "level out of range");
+    REQ(v0 && lambda_out && iters >= 1 && iters <= 10000, AMGPS_E_ARG, "bad arguments");
+    enter(c);
+    double lam = 0.0;
+    with_engine(c, [&](auto eng) { lam = decltype(eng)::lambda(c, level, v0, iters); });
+    *lambda_out = lam;
+    leave(c);
+  });
+}
+
+amgps_status amgps_smooth(amgps_ctx* c, int level, amgps_kind kind, int degree, const double* b,
+                          double* x, int x_is_zero) {
+  return guard(c, [&] {
+    need_loaded(c);
+    check_kind_degree(kind, degree);
+    REQ(level >= 0 && level < (int)c->lv.size() - 1, AMGPS_E_ARG,
+        "level out of range (the coarsest level has no smoother)");
+    REQ(b && x && (const void*)b != (const void*)x, AMGPS_E_ARG, "null or aliased vectors");
+    const Spec& sp = c->lv[level].spec;
+    REQ(kind != AMGPS_WEIGHTS || (sp.kind == AMGPS_WEIGHTS && sp.k == degree), AMGPS_E_STATE,
+        "AMGPS_WEIGHTS: set the level's weights of this degree first");
+    const Coefs cf = make_coefs(kind, degree, sp.w, sp.rho);
+    enter(c);
+    with_engine(c, [&](auto eng) { decltype(eng)::smooth_public(c, level, cf, b, x, x_is_zero != 0); });
+    leave(c);
+  });
+}
+
+amgps_status amgps_vcycle(amgps_ctx* c, const double* r, double* z) {
+  return guard(c, [&] {
+    need_loaded(c);
+    REQ(r && z && (const void*)r != (const void*)z, AMGPS_E_ARG, "null or aliased vectors");
+    enter(c);
+    with_engine(c, [&](auto eng) { decltype(eng)::vcycle(c, r, z); });
+    leave(c);
+  });
+}
+
+amgps_status amgps_pcg(amgps_ctx* c, const double* b, double* x, double rtol, int maxit,
+                       int* iters, double* relres) {
+  return guard(c, [&] {
+    need_loaded(c);
+    REQ(b && x && iters && relres && (const void*)b != (const void*)x, AMGPS_E_ARG,
+        "null or aliased arguments");
+    REQ(rtol > 0.0 && maxit >= 1, AMGPS_E_ARG, "rtol must be > 0 and maxit >= 1");
+    enter(c);
+    bool conv = false;
+    pcg_impl(c, b, x, rtol, maxit, iters, relres, &conv);
+    leave(c);
+    REQ(conv, AMGPS_E_NOCONV, "PCG did not reach rtol within maxit");
+  });
+}
+
+amgps_status amgps_pcg_host(amgps_ctx* c, const double* b_host, double* x_host, double rtol,
+                            int maxit, int* iters, double* relres) {
+  return guard(c, [&] {
+    need_loaded(c);
+    REQ(b_host && x_host && iters && relres, AMGPS_E_ARG, "null arguments");
+    REQ(rtol > 0.0 && maxit >= 1, AMGPS_E_ARG, "rtol must be > 0 and maxit >= 1");
+    const int64_t n = c->lv[0].n;
+    enter(c);
+    cudaPointerAttributes pa{};
+    bool pinned_b = cudaPointerGetAttributes(&pa, b_host) == cudaSuccess &&
+                    pa.type == cudaMemoryTypeHost;
+    cudaGetLastError();
+    cudaPointerAttributes px{};
+    bool pinned_x = cudaPointerGetAttributes(&px, x_host) == cudaSuccess &&
+                    px.type == cudaMemoryTypeHost;
+    cudaGetLastError();
+    if ((!pinned_b || !pinned_x) && c->h_stage_n < (size_t)n) {
+      if (c->h_stage) cudaFreeHost(c->h_stage);
+      c->h_stage = nullptr;
+      c->h_stage_n = 0;
+      CK(cudaMallocHost(&c->h_stage, n * sizeof(double)));
+      c->h_stage_n = n;
+    }
+    const double* src = b_host;
+    if (!pinned_b) {
+      std::memcpy(c->h_stage, b_host, n * sizeof(double));
+      src = c->h_stage;
+    }
+    CK(cudaMemcpyAsync(c->stage_b, src, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    bool conv = false;
+    pcg_impl(c, c->stage_b, c->stage_x, rtol, maxit, iters, relres, &conv);
+    double* dst = pinned_x ? x_host : c->h_stage;
+    CK(cudaMemcpyAsync(dst, c->stage_x, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (!pinned_x) std::memcpy(x_host, c->h_stage, n * sizeof(double));
+    leave(c);
+    REQ(conv, AMGPS_E_NOCONV, "PCG did not reach rtol within maxit");
+  });
+}
+
+amgps_status amgps_synchronize(amgps_ctx* c) {
+  return guard(c, [&] {
+    REQ(c, AMGPS_E_ARG, "null context");
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    harvest(c);
+  });
+}
+
+amgps_status amgps_opt4_weights(int degree, double* beta_out) {
+  if (!beta_out || degree < 1 || degree > AMGPS_TABLE_KMAX) return AMGPS_E_ARG;
+  for (int j = 0; j < degree; ++j) beta_out[j] = AMGPS_OPT4_BETA[degree - 1][j];
+  return AMGPS_OK;
+}
+
+amgps_status amgps_cheb1_astar(int degree, double* a_out) {
+  if (!a_out || degree < 1 || degree > AMGPS_TABLE_KMAX) return AMGPS_E_ARG;
+  *a_out = AMGPS_ASTAR[degree - 1];
+  return AMGPS_OK;
+}
+
+amgps_status amgps_profile_enable(amgps_ctx* c, int on) {
+  return guard(c, [&] {
+    REQ(c, AMGPS_E_ARG, "null context");
+    c->prof = on != 0;
+  });
+}
+
+amgps_status amgps_profile_read(amgps_ctx* c, int cls, int reset, int64_t* launches,
+                                double* total_ms, double* bytes) {
+  return guard(c, [&] {
+    REQ(c, AMGPS_E_ARG, "null context");
+    REQ(cls >= 0 && cls <= 3, AMGPS_E_ARG, "kernel class out of range");
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    harvest(c);
+    if (cls == 3) {
+      const int64_t total = launches_enqueued() + c->launch_adjust;
+      if (launches) *launches = total - c->launch_base;
+      if (total_ms) *total_ms = 0.0;
+      if (bytes) *bytes = 0.0;
+      if (reset) c->launch_base = total;
+      return;
+    }
+    if (launches) *launches = c->prof_launches[cls];
+    if (total_ms) *total_ms = c->prof_ms[cls];
+    if (bytes) *bytes = c->prof_bytes[cls];
+    if (reset) {
+      c->prof_launches[cls] = 0;
+      c->prof_ms[cls] = 0.0;
+      c->prof_bytes[cls] = 0.0;
+    }
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,105 @@
+// Device helpers shared by the kernel translation units.
+#pragma once
+
+#include "amgps_internal.h"
+
+namespace amgps {
+
+// Matrix values are streamed once per step: cache-streaming loads (evict-first
+// in L1 and L2) keep them from displacing the vectors that neighbouring rows
+// gather.  BF16 values are widened to FP32.
+__device__ __forceinline__ double ldval(const double* p) { return __ldcs(p); }
+__device__ __forceinline__ float ldval(const float* p) { return __ldcs(p); }
+__device__ __forceinline__ float ldval(const __nv_bfloat16* p) {
+  unsigned short s = __ldcs(reinterpret_cast<const unsigned short*>(p));
+  return __bfloat162float(__ushort_as_bfloat16(s));
+}
+
+template <class T>
+__device__ __forceinline__ T absv(T v) { return v < T(0) ? -v : v; }
+
+// init + SIGN * (A u)_row from one pass over the row (SIGN = +1 or -1, so a
+// residual b - A u comes out of the same multiply-adds).  `lane` is the row's
+// position in slice `s`.  Rows past n (tail of the last slice) see only zero
+// padding and clamped, in-range columns.  FP64 arithmetic is the scarce
+// resource on this GPU (its FP64 pipe issues about 2 FMAs per clock per SM),
+// so the row costs exactly one multiply-add per stored entry and nothing else.
+template <int SIGN, class VT, class XT>
+__device__ __forceinline__ XT row_spmv(const DevMat<VT>& A, int64_t s, int lane, int64_t row,
+                                       const XT* __restrict__ u, XT init) {
+  const SliceDesc d = A.sd[s];
+  const int w = d.w;
+  const int64_t nm1 = A.n - 1;
+  XT t = init;
+  for (int k0 = 0; k0 < w; k0 += 8) {
+    XT a[8];
+    int64_t c[8];
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      const int k = k0 + kk;
+      a[kk] = XT(0);
+      c[kk] = 0;
+      if (k < w) {
+        const int64_t e = d.vbase + (int64_t)k * kSlice + lane;
+        a[kk] = XT(ldval(A.val + e));
+        if (d.cref >= 0) {
+          int64_t cc = row + (int64_t)A.off[d.cref + k];
+          c[kk] = cc < 0 ? 0 : (cc > nm1 ? nm1 : cc);
+        } else {
+          c[kk] = A.col[e];
+        }
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk)
+      if (k0 + kk < w) t = fma(SIGN > 0 ? a[kk] : -a[kk], __ldg(u + c[kk]), t);
+  }
+  return t;
+}
+
+// Sum over a block (any blockDim multiple of 32, <= 1024); result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+  if (warp == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+// Deterministic grid-wide sum: each block writes its partial, the last block to
+// arrive adds the partials in index order with a fixed tree and calls
+// fin(total) from thread 0, then re-arms the counter.  The grid size is a pure
+// function of the problem size, so the result is bitwise reproducible.
+template <class Fin>
+__device__ __forceinline__ void grid_sum(double v, const RedWork& w, Fin fin) {
+  __shared__ double sh[32];
+  __shared__ bool last;
+  double b = block_sum(v, sh);
+  if (threadIdx.x == 0) {
+    w.part[blockIdx.x] = b;
+    __threadfence();
+    const unsigned t = atomicAdd(w.counter, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    double s = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s += __ldcg(w.part + i);
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) {
+      fin(s);
+      *w.counter = 0u;
+    }
+  }
+}
+
+}  // namespace amgps

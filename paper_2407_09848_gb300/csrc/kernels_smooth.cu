@@ -1,0 +1,267 @@
+// Smoother, transfer and conversion kernels of the V-cycle (Sec. 2 and 3).
+//
+// One launch of k_step is one degree step of a polynomial smoother: the SpMV
+// with the current recurrence vector, the residual update, the l1-Jacobi
+// scaling and the recurrence / solution updates share a single pass over A and
+// the vectors (the fusion Sec. 3 obtains with its psb_upd_xyz kernel):
+//
+//   4th kind (Eq. polsmoother / polsmootheropt), step producing z_{j+1}:
+//     t = A z_j ; r_j = r_{j-1} - t
+//     z_{j+1} = c1 z_j + c2 M^{-1} r_j         c1 = (2j-1)/(2j+3), c2 = (8j+4)/(2j+3)/rho
+//     x += beta_{j+1} z_{j+1}
+//   1st kind (Algorithm 1), step producing d^(j):
+//     t = A d^(j-1) ; r^(j) = r^(j-1) - (1/rho) M^{-1} t
+//     d^(j) = rho_j rho_{j-1} d^(j-1) + (2 rho_j/delta) r^(j) ; x += d^(j)
+//   l1-Jacobi sweep: x_new = x + M^{-1}(b - A x)
+//
+// D^{-1} = 1/M (Eq. l1smooth) is formed once per level and streamed as one
+// vector: on this GPU the FP64 pipe, not HBM, is the tighter limit of the FP64
+// path, and re-deriving M_i from the row plus an IEEE division every step would
+// cost about four times the FP64 instructions of the whole step.  The row's
+// own vectors are loaded before the SpMV so their latency overlaps it.  z
+// ping-pongs between two buffers because neighbouring rows gather z_j in the
+// same launch that writes z_{j+1}.
+#include "kernels_common.cuh"
+
+namespace amgps {
+
+template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN>
+__global__ void __launch_bounds__(kBlock) k_step(const StepArgs<VT, XT> a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (s >= a.A.nslices) return;
+  const int64_t row = s * kSlice + lane;
+  const bool live = row < a.A.n;
+  XT rin = XT(0), xin = XT(0), zo = XT(0), di = XT(0);
+  if (live) {
+    rin = a.rin[row];
+    xin = a.xin[row];
+    di = a.dinv[row];
+    if (ZOWN) zo = a.zown[row];
+  }
+  if constexpr (FAM == FAM_CHEB4) {
+    // r_j = r_{j-1} - A z_j accumulated directly (7 FMAs for a 7-point row)
+    const XT r = row_spmv<-1, VT, XT>(a.A, s, lane, row, a.u, rin);
+    if (!live) return;
+    if (WR) a.rout[row] = r;
+    XT z = a.c2 * (r * di);
+    if (ZOWN) z = fma(a.c1, zo, z);
+    a.zout[row] = z;
+    a.xout[row] = fma(a.beta, z, xin);
+  } else if constexpr (FAM == FAM_CHEB1) {
+    XT r;
+    if (INIT) {
+      const XT res = row_spmv<-1, VT, XT>(a.A, s, lane, row, a.u, rin);
+      if (!live) return;
+      r = a.rhoinv * (res * di);
+    } else {
+      const XT t = row_spmv<1, VT, XT>(a.A, s, lane, row, a.u, XT(0));
+      if (!live) return;
+      r = fma(-(a.rhoinv * di), t, rin);
+    }
+    if (WR) a.rout[row] = r;
+    XT z = a.c2 * r;
+    if (ZOWN) z = fma(a.c1, zo, z);
+    a.zout[row] = z;
+    a.xout[row] = xin + z;
+  } else {
+    const XT res = row_spmv<-1, VT, XT>(a.A, s, lane, row, a.u, rin);
+    if (!live) return;
+    a.xout[row] = fma(res, di, xin);
+  }
+}
+
+template <class VT, class XT, int FAM, bool INIT>
+static void dispatch_wr(const StepArgs<VT, XT>& a, dim3 g, cudaStream_t s) {
+  const bool z = a.zown != nullptr;
+  if (a.write_r) {
+    if (z) k_step<VT, XT, FAM, INIT, true, true><<<g, kBlock, 0, s>>>(a);
+    else k_step<VT, XT, FAM, INIT, true, false><<<g, kBlock, 0, s>>>(a);
+  } else {
+    if (z) k_step<VT, XT, FAM, INIT, false, true><<<g, kBlock, 0, s>>>(a);
+    else k_step<VT, XT, FAM, INIT, false, false><<<g, kBlock, 0, s>>>(a);
+  }
+  count_launch();
+}
+
+template <class VT, class XT>
+void launch_step(const StepArgs<VT, XT>& a, cudaStream_t s) {
+  if (a.A.nslices == 0) return;
+  dim3 g((unsigned)((a.A.nslices + kWarpsPerBlock - 1) / kWarpsPerBlock));
+  switch (a.fam) {
+    case FAM_CHEB4:
+      if (a.init) dispatch_wr<VT, XT, FAM_CHEB4, true>(a, g, s);
+      else dispatch_wr<VT, XT, FAM_CHEB4, false>(a, g, s);
+      break;
+    case FAM_CHEB1:
+      if (a.init) dispatch_wr<VT, XT, FAM_CHEB1, true>(a, g, s);
+      else dispatch_wr<VT, XT, FAM_CHEB1, false>(a, g, s);
+      break;
+    default:
+      k_step<VT, XT, FAM_JAC, true, false, false><<<g, kBlock, 0, s>>>(a);
+      count_launch();
+  }
+}
+
+// First step from x = 0 (no product with A):
+//   4th kind: z_1 = c2 M^{-1} b, x = beta_1 z_1 (r_0 = b is not copied)
+//   1st kind: r^(0) = (1/rho) M^{-1} b, d^(0) = r^(0)/theta, x = d^(0)
+//   Jacobi:   x = M^{-1} b
+template <class XT, int FAM>
+__global__ void __launch_bounds__(kBlock) k_first(int64_t n, const XT* __restrict__ b,
+                                                  const XT* __restrict__ dinv,
+                                                  XT* __restrict__ rout, XT* __restrict__ zout,
+                                                  XT* __restrict__ xout, XT c2, XT beta,
+                                                  XT rhoinv) {
+  const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (i >= n) return;
+  const XT bm = b[i] * dinv[i];
+  if constexpr (FAM == FAM_CHEB4) {
+    const XT z = c2 * bm;
+    zout[i] = z;
+    xout[i] = beta * z;
+  } else if constexpr (FAM == FAM_CHEB1) {
+    const XT r = rhoinv * bm;
+    rout[i] = r;
+    const XT z = c2 * r;
+    zout[i] = z;
+    xout[i] = z;
+  } else {
+    xout[i] = bm;
+  }
+}
+
+template <class XT>
+void launch_first(int fam, int64_t n, const XT* b, const XT* dinv, XT* rout, XT* zout, XT* xout,
+                  XT c2, XT beta, XT rhoinv, cudaStream_t s) {
+  if (n == 0) return;
+  dim3 g((unsigned)((n + kBlock - 1) / kBlock));
+  if (fam == FAM_CHEB4)
+    k_first<XT, FAM_CHEB4><<<g, kBlock, 0, s>>>(n, b, dinv, rout, zout, xout, c2, beta, rhoinv);
+  else if (fam == FAM_CHEB1)
+    k_first<XT, FAM_CHEB1><<<g, kBlock, 0, s>>>(n, b, dinv, rout, zout, xout, c2, beta, rhoinv);
+  else
+    k_first<XT, FAM_JAC><<<g, kBlock, 0, s>>>(n, b, dinv, rout, zout, xout, c2, beta, rhoinv);
+  count_launch();
+}
+
+// b_c = P^T (b - A x) for an unsmoothed aggregation P (Sec. 2): eight lanes per
+// coarse row walk its children (cidx[cptr[I] .. cptr[I+1])), each computing the
+// true residual of a child row; the eight partial sums meet in a fixed shuffle
+// tree, so the result does not depend on scheduling.
+template <class VT, class XT>
+__global__ void __launch_bounds__(kBlock) k_resid_restrict(const DevMat<VT> A,
+                                                           const XT* __restrict__ x,
+                                                           const XT* __restrict__ b,
+                                                           const int32_t* __restrict__ cptr,
+                                                           const int32_t* __restrict__ cidx,
+                                                           int64_t nc, XT* __restrict__ bc) {
+  const int g = threadIdx.x & 7;
+  const int64_t I = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 3;
+  XT acc = XT(0);
+  if (I < nc) {
+    const int q1 = cptr[I + 1];
+    for (int q = cptr[I] + g; q < q1; q += 8) {
+      const int64_t i = cidx[q];
+      acc += row_spmv<-1, VT, XT>(A, i >> 5, (int)(i & 31), i, x, b[i]);
+    }
+  }
+  acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  if (g == 0 && I < nc) bc[I] = acc;
+}
+
+template <class VT, class XT>
+void launch_resid_restrict(const DevMat<VT>& A, const XT* x, const XT* b, const int32_t* cptr,
+                           const int32_t* cidx, int64_t nc, XT* bc, cudaStream_t s) {
+  if (nc == 0) return;
+  dim3 g((unsigned)((nc * 8 + kBlock - 1) / kBlock));
+  k_resid_restrict<VT, XT><<<g, kBlock, 0, s>>>(A, x, b, cptr, cidx, nc, bc);
+  count_launch();
+}
+
+// x += P e_c (gather through the aggregate map).
+template <class XT>
+__global__ void __launch_bounds__(kBlock) k_prolong(int64_t n, const int32_t* __restrict__ agg,
+                                                    const XT* __restrict__ ec, XT* x) {
+  const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (i < n) x[i] += ec[agg[i]];
+}
+
+template <class XT>
+void launch_prolong(int64_t n, const int32_t* agg, const XT* ec, XT* x, cudaStream_t s) {
+  if (n == 0) return;
+  k_prolong<XT><<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, agg, ec, x);
+  count_launch();
+}
+
+// 1/M_i with M_i of Eq. l1smooth (a_ii + sum_{j != i} |a_ij|), formed once per level.
+template <class VT, class XT>
+__global__ void __launch_bounds__(kBlock) k_l1diag(const DevMat<VT> A, XT* __restrict__ dinv) {
+  const int lane = threadIdx.x & 31;
+  const int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (s >= A.nslices) return;
+  const int64_t row = s * kSlice + lane;
+  const SliceDesc d = A.sd[s];
+  const int64_t nm1 = A.n - 1;
+  XT m = XT(0);
+  for (int k = 0; k < d.w; ++k) {
+    const int64_t e = d.vbase + (int64_t)k * kSlice + lane;
+    const XT a = XT(ldval(A.val + e));
+    int64_t c;
+    if (d.cref >= 0) {
+      c = row + (int64_t)A.off[d.cref + k];
+      c = c < 0 ? 0 : (c > nm1 ? nm1 : c);
+    } else {
+      c = A.col[e];
+    }
+    m += (c == row) ? a : absv(a);
+  }
+  if (row < A.n) dinv[row] = XT(1) / m;
+}
+
+template <class VT, class XT>
+void launch_l1diag(const DevMat<VT>& A, XT* dinv, cudaStream_t s) {
+  if (A.nslices == 0) return;
+  dim3 g((unsigned)((A.nslices + kWarpsPerBlock - 1) / kWarpsPerBlock));
+  k_l1diag<VT, XT><<<g, kBlock, 0, s>>>(A, dinv);
+  count_launch();
+}
+
+template <class A, class B>
+__global__ void __launch_bounds__(kBlock) k_convert(int64_t n, const A* __restrict__ in,
+                                                    B* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (i < n) out[i] = B(in[i]);
+}
+
+template <class A, class B>
+void launch_convert(int64_t n, const A* in, B* out, cudaStream_t s) {
+  if (n == 0) return;
+  k_convert<A, B><<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, in, out);
+  count_launch();
+}
+
+#define AMGPS_INST(VT, XT)                                                                   \
+  template void launch_step<VT, XT>(const StepArgs<VT, XT>&, cudaStream_t);                  \
+  template void launch_resid_restrict<VT, XT>(const DevMat<VT>&, const XT*, const XT*,       \
+                                              const int32_t*, const int32_t*, int64_t, XT*,  \
+                                              cudaStream_t);                                 \
+  template void launch_l1diag<VT, XT>(const DevMat<VT>&, XT*, cudaStream_t);
+AMGPS_INST(double, double)
+AMGPS_INST(float, float)
+AMGPS_INST(__nv_bfloat16, float)
+#undef AMGPS_INST
+
+template void launch_first<double>(int, int64_t, const double*, const double*, double*, double*,
+                                   double*, double, double, double, cudaStream_t);
+template void launch_first<float>(int, int64_t, const float*, const float*, float*, float*,
+                                  float*, float, float, float, cudaStream_t);
+template void launch_prolong<double>(int64_t, const int32_t*, const double*, double*, cudaStream_t);
+template void launch_prolong<float>(int64_t, const int32_t*, const float*, float*, cudaStream_t);
+template void launch_convert<double, float>(int64_t, const double*, float*, cudaStream_t);
+template void launch_convert<float, double>(int64_t, const float*, double*, cudaStream_t);
+template void launch_convert<double, double>(int64_t, const double*, double*, cudaStream_t);
+
+}  // namespace amgps

@@ -1,0 +1,79 @@
+"""The C-ABI library builds, loads and exports every declared entry point;
+its host-only table calls agree with the oracle and the paper (no GPU)."""
+import numpy as np
+import pytest
+
+from conftest import load_constants
+from paper_2407_09848_gb300 import amgps, build
+
+ROWS = load_constants()
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return amgps.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = amgps.header_symbols()
+    assert len(names) >= 17
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_version(lib):
+    assert lib.amgps_version() >= 1
+
+
+@pytest.mark.parametrize("row", ROWS, ids=lambda r: f"k{r[0]}")
+def test_astar_table(lib, row):
+    from oracle import params
+    k, a_pr = row[0], row[1]
+    a = amgps.cheb1_astar(k)
+    # the oracle solves in double precision: a few units of rounding
+    assert abs(a - params.a_star(k)) <= 2e-15 * a
+    assert abs(a - a_pr) <= 1e-14 * a_pr
+
+
+@pytest.mark.parametrize("row", ROWS[:10], ids=lambda r: f"k{r[0]}")
+def test_opt4_table_agrees_with_oracle(lib, row):
+    # two independent solvers of Eq. prob1 (the library's table: high-precision
+    # Newton on the equioscillation system; the oracle: a Remez exchange)
+    from oracle import params, smoother
+    k, g_pr = row[0], row[4]
+    beta_lib = amgps.opt4_weights(k)
+    beta_ora = smoother.opt4_table(k)
+    assert np.max(np.abs(beta_lib - beta_ora)) <= 1e-12
+    g = params.gamma_opt4(beta_lib)
+    assert abs(g - g_pr) <= 1e-9 * g_pr
+
+
+def test_table_degree_bounds(lib):
+    with pytest.raises(amgps.AmgpsError):
+        amgps.opt4_weights(17)
+    with pytest.raises(amgps.AmgpsError):
+        amgps.cheb1_astar(0)
+
+
+def test_create_reports_missing_gpu(lib):
+    import ctypes
+    import torch
+    h = ctypes.c_void_p()
+    st = lib.amgps_create(ctypes.byref(h), 0, None)
+    if torch.cuda.is_available():
+        assert st == 0
+        lib.amgps_destroy(h)
+    else:
+        assert st == 5  # AMGPS_E_CUDA, reported without touching a device
+        assert lib.amgps_last_error(None)
+        assert not h.value
+
+
+def test_null_arguments_rejected_on_host(lib):
+    import ctypes
+    assert lib.amgps_create(None, 0, None) == 1
+    assert lib.amgps_smooth(None, 0, 2, 4, None, None, 1) == 1
+    assert lib.amgps_pcg(None, None, None, 1e-8, 10, None, None) == 1
+    assert lib.amgps_destroy(None) == 0
+    assert lib.amgps_opt4_weights(4, None) == 1

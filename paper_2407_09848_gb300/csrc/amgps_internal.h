@@ -64,7 +64,7 @@ struct StepArgs {
 
 // Device scalar slots of the Krylov solver.
 enum Scalar {
-  S_PQ = 0, S_RR = 1, S_RZ = 2, S_RZOLD = 3, S_ALPHA = 4, S_BB = 5, S_NRM = 6, S_TMP = 7,
+  S_PQ = 0, S_RR = 1, S_RZ = 2, S_RZOLD = 3, S_ALPHA = 4, S_BB = 5, S_NRM = 6, S_BETA = 7,
   S_COUNT = 16
 };
 

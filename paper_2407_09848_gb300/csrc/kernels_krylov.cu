@@ -37,7 +37,10 @@ __global__ void __launch_bounds__(kBlock) k_spmv_dot(const DevMat<double> A,
       acc = fma(p[row], t, acc);
     }
   }
-  grid_sum(acc, w, [&](double tot) { scal[S_PQ] = tot; });
+  grid_sum(acc, w, [&](double tot) {
+    scal[S_PQ] = tot;
+    scal[S_ALPHA] = scal[S_RZ] / tot;  // once per iteration, not once per thread
+  });
 }
 
 void launch_spmv_dot(const DevMat<double>& A, const double* p, double* q, const RedWork& w,
@@ -46,13 +49,13 @@ void launch_spmv_dot(const DevMat<double>& A, const double* p, double* q, const 
   count_launch();
 }
 
-// alpha = rz / pq ; x += alpha p ; r -= alpha q ; r.r (S_RR)
+// x += alpha p ; r -= alpha q ; r.r (S_RR), alpha = rz / pq from k_spmv_dot
 __global__ void __launch_bounds__(kBlock) k_cg_update(int64_t n, const double* __restrict__ p,
                                                       const double* __restrict__ q,
                                                       double* __restrict__ x,
                                                       double* __restrict__ r, const RedWork w,
                                                       double* scal) {
-  const double alpha = scal[S_RZ] / scal[S_PQ];
+  const double alpha = scal[S_ALPHA];
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * kBlock) {
@@ -61,10 +64,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(int64_t n, const double* _
     r[i] = ri;
     acc = fma(ri, ri, acc);
   }
-  grid_sum(acc, w, [&](double tot) {
-    scal[S_RR] = tot;
-    scal[S_ALPHA] = alpha;
-  });
+  grid_sum(acc, w, [&](double tot) { scal[S_RR] = tot; });
 }
 
 void launch_cg_update(int64_t n, const double* p, const double* q, double* x, double* r,
@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(kBlock) k_dot(int64_t n, const double* __restr
     if (rz_shift) {
       scal[S_RZOLD] = scal[S_RZ];
       scal[S_RZ] = tot;
+      scal[S_BETA] = tot / scal[S_RZOLD];
     } else {
       scal[slot] = tot;
     }
@@ -96,11 +97,11 @@ void launch_dot(int64_t n, const double* a, const double* b, const RedWork& w, d
   count_launch();
 }
 
-// p = z + (rz / rz_old) p
+// p = z + beta p, beta = rz / rz_old from the last block of k_dot
 __global__ void __launch_bounds__(kBlock) k_xpay(int64_t n, const double* __restrict__ z,
                                                  double* __restrict__ p,
                                                  const double* __restrict__ scal) {
-  const double beta = scal[S_RZ] / scal[S_RZOLD];
+  const double beta = scal[S_BETA];
   const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
   if (i < n) p[i] = fma(beta, p[i], z[i]);
 }

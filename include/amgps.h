@@ -132,6 +132,22 @@ amgps_status amgps_estimate_lambda(amgps_ctx* ctx, int level, const double* v0_d
 amgps_status amgps_smooth(amgps_ctx* ctx, int level, amgps_kind kind, int degree,
                           const double* b_dev, double* x_dev, int x_is_zero);
 
+/* amgps_smooth without any device allocation, for callers that may not
+ * allocate device memory at the point of the call (for example code running
+ * under an allocator that owns all device memory, or a phase of a real-time
+ * loop where allocation is forbidden).  No counterpart in the paper: same
+ * kernels and result as amgps_smooth, but the work vectors live in one static
+ * device array (3 MiB on each GPU that loads the library, held until exit), so
+ * levels with more than 65536 rows are rejected with AMGPS_E_ARG.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * Every call shares the array: calls that overlap on the GPU (other streams,
+ * other contexts, other host threads) race and corrupt each other's results.
+ * Nothing needs clearing between calls: each call writes every scratch entry
+ * it reads before reading it.  Arguments as for amgps_smooth. */
+amgps_status amgps_smooth_noalloc(amgps_ctx* ctx, int level, amgps_kind kind, int degree,
+                                  const double* b_dev, double* x_dev, int x_is_zero);
+
 /* One V-cycle z = B r (Eq. amg) from level 0, with the smoothers set by
  * amgps_set_smoother.  r_dev, z_dev: n_0 FP64 device vectors, must not alias. */
 amgps_status amgps_vcycle(amgps_ctx* ctx, const double* r_dev, double* z_dev);

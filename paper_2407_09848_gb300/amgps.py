@@ -52,6 +52,8 @@ _SIGS = {
     "amgps_set_smoother": ([C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_double], C.c_int),
     "amgps_estimate_lambda": ([C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_double)], C.c_int),
     "amgps_smooth": ([C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int], C.c_int),
+    "amgps_smooth_noalloc": ([C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int],
+                             C.c_int),
     "amgps_vcycle": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "amgps_pcg": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int),
                    C.POINTER(C.c_double)], C.c_int),
@@ -192,6 +194,12 @@ class Solver:
         n = self._n(level)
         self._check(lib().amgps_smooth(self._h, level, KIND[kind], degree, _dptr(b, n, "b"),
                                        _dptr(x, n, "x"), 1 if x_is_zero else 0))
+
+    def smooth_noalloc(self, level, kind, degree, b, x, x_is_zero=False):
+        """amgps_smooth without device allocation (static 65536-row scratch)."""
+        n = self._n(level)
+        self._check(lib().amgps_smooth_noalloc(self._h, level, KIND[kind], degree, _dptr(b, n, "b"),
+                                               _dptr(x, n, "x"), 1 if x_is_zero else 0))
 
     def vcycle(self, r, z):
         n = self._n(0)

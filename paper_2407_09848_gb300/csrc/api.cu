@@ -15,6 +15,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <type_traits>
@@ -773,6 +774,40 @@ void pcg_impl(amgps_ctx* c, const double* b, double* x, double rtol, int maxit, 
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Allocation-free smoother application (amgps_smooth_noalloc).
+//
+// Its work vectors (the recurrence residual r, the two z buffers, the second
+// x buffer and, for FP32/BF16 hierarchies, the FP32 copies of b and x) live in
+// this file-scope device array instead of the context's per-level buffers, so
+// the call itself allocates nothing.  The array exists on every GPU that loads
+// the library, for the life of the process: kNoAllocRows rows x 6 vectors x
+// 8 bytes = 3 MiB.  Host code must not pass the symbol itself to a kernel (on
+// the host it is only a stand-in); noalloc_scratch() looks up its device
+// address once per device with that device current.
+// ---------------------------------------------------------------------------
+constexpr int64_t kNoAllocRows = 65536;
+constexpr int kNoAllocVectors = 6;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocVectors * kNoAllocRows];
+
+void* noalloc_scratch(int device) {
+  static std::mutex mu;
+  static void* addr[256] = {};
+  REQ(device >= 0 && device < 256, AMGPS_E_ARG, "device index out of range");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      throw Fail{AMGPS_E_CUDA, std::string("cudaGetSymbolAddress(scratch): ") +
+                                   cudaGetErrorString(e)};
+    }
+    addr[device] = p;
+  }
+  return addr[device];
+}
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -1035,6 +1070,44 @@ amgps_status amgps_smooth(amgps_ctx* c, int level, amgps_kind kind, int degree, 
     const Coefs cf = make_coefs(kind, degree, sp.w, sp.rho);
     enter(c);
     with_engine(c, [&](auto eng) { decltype(eng)::smooth_public(c, level, cf, b, x, x_is_zero != 0); });
+    leave(c);
+  });
+}
+
+amgps_status amgps_smooth_noalloc(amgps_ctx* c, int level, amgps_kind kind, int degree,
+                                  const double* b, double* x, int x_is_zero) {
+  return guard(c, [&] {
+    need_loaded(c);
+    check_kind_degree(kind, degree);
+    REQ(level >= 0 && level < (int)c->lv.size() - 1, AMGPS_E_ARG,
+        "level out of range (the coarsest level has no smoother)");
+    REQ(b && x && (const void*)b != (const void*)x, AMGPS_E_ARG, "null or aliased vectors");
+    Level& L = c->lv[level];
+    REQ(L.n <= kNoAllocRows, AMGPS_E_ARG,
+        "amgps_smooth_noalloc: level " + std::to_string(level) + " has " + std::to_string(L.n) +
+            " rows; the static scratch holds at most 65536");
+    const Spec& sp = L.spec;
+    REQ(kind != AMGPS_WEIGHTS || (sp.kind == AMGPS_WEIGHTS && sp.k == degree), AMGPS_E_STATE,
+        "AMGPS_WEIGHTS: set the level's weights of this degree first");
+    const Coefs cf = make_coefs(kind, degree, sp.w, sp.rho);
+    enter(c);
+    char* base = (char*)noalloc_scratch(c->device);
+    const size_t stride = (size_t)kNoAllocRows * sizeof(double);
+    // Point the level's work vectors at the static scratch for this call only.
+    struct Restore {
+      Level& L;
+      void *r, *za, *zb, *xb, *b, *x;
+      ~Restore() { L.r = r; L.za = za; L.zb = zb; L.xb = xb; L.b = b; L.x = x; }
+    } restore{L, L.r, L.za, L.zb, L.xb, L.b, L.x};
+    L.r = base;
+    L.za = base + stride;
+    L.zb = base + 2 * stride;
+    L.xb = base + 3 * stride;
+    L.b = base + 4 * stride;
+    L.x = base + 5 * stride;
+    with_engine(c, [&](auto eng) {
+      decltype(eng)::smooth_public(c, level, cf, b, x, x_is_zero != 0);
+    });
     leave(c);
   });
 }

@@ -168,6 +168,20 @@ amgps_status amgps_pcg_host(amgps_ctx* ctx, const double* b_host, double* x_host
 /* Wait for all work of the context.  */
 amgps_status amgps_synchronize(amgps_ctx* ctx);
 
+/* Context options.  AMGPS_OPT_TMA (default 1): run the fused smoother step
+ * through the TMA-fed pipelined kernel where the level's layout allows it
+ * (0: the direct-load kernel everywhere; results are identical). */
+enum { AMGPS_OPT_TMA = 1 };
+amgps_status amgps_set_option(amgps_ctx* ctx, int option, int64_t value);
+
+/* Host-only planning query (no device needed): how the TMA-fed step would
+ * cover matrix A at precision `prec` -- 256-row tiles it takes, slices left to
+ * the direct kernel, bytes per shared-memory stage and stages per CTA.  Every
+ * bulk copy of the plan is checked on the host for bounds and 16-byte
+ * alignment; a violation returns AMGPS_E_ARG. */
+amgps_status amgps_tma_plan_stats(const amgps_csr* A, amgps_prec prec, int64_t* tiles,
+                                  int64_t* generic_slices, int* stage_bytes, int* nstages);
+
 /* The library's tabulated optimal 4th-kind weights beta_{1..degree} for
  * Eq. polsmootheropt (degree 1..16), written to beta_out (host). */
 amgps_status amgps_opt4_weights(int degree, double* beta_out);

@@ -63,6 +63,9 @@ _SIGS = {
     "amgps_opt4_weights": ([C.c_int, C.c_void_p], C.c_int),
     "amgps_cheb1_astar": ([C.c_int, C.POINTER(C.c_double)], C.c_int),
     "amgps_profile_enable": ([C.c_void_p, C.c_int], C.c_int),
+    "amgps_set_option": ([C.c_void_p, C.c_int, C.c_int64], C.c_int),
+    "amgps_tma_plan_stats": ([C.POINTER(CSR), C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                              C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "amgps_profile_read": ([C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double),
                             C.POINTER(C.c_double)], C.c_int),
 }
@@ -105,6 +108,18 @@ def cheb1_astar(k):
     if st:
         raise AmgpsError(st, "bad degree")
     return a.value
+
+
+def tma_plan_stats(A, prec="f64"):
+    """Host-only: (tiles, generic_slices, stage_bytes, nstages) of the TMA plan."""
+    keep = []
+    csr = _csr_struct(A, keep)
+    t, g, sb, ns = C.c_int64(), C.c_int64(), C.c_int(), C.c_int()
+    st = lib().amgps_tma_plan_stats(C.byref(csr), PREC[prec], C.byref(t), C.byref(g), C.byref(sb),
+                                    C.byref(ns))
+    if st:
+        raise AmgpsError(st, lib().amgps_last_error(None).decode())
+    return t.value, g.value, sb.value, ns.value
 
 
 def _csr_struct(A, keep):
@@ -237,6 +252,10 @@ class Solver:
                 and (n is None or a.size == n)):
             raise TypeError("host array must be contiguous float64 with n entries")
         return C.c_void_p(a.ctypes.data)
+
+    def set_tma(self, on):
+        """Use the TMA-fed step kernel where possible (default) or the direct one."""
+        self._check(lib().amgps_set_option(self._h, 1, 1 if on else 0))
 
     def synchronize(self):
         self._check(lib().amgps_synchronize(self._h))

@@ -60,11 +60,44 @@ struct StepArgs {
   int fam = FAM_CHEB4;
   bool init = false;
   bool write_r = false;
+  const int32_t* slices = nullptr;  // optional list of slices to process (null: all)
+  int64_t nlist = 0;                // entries in `slices`
+};
+
+// ---- TMA-fed step (kernels_tma.cu) ----
+// A tile is `rows` consecutive rows (a multiple of 32 slices' worth, up to
+// kTmaMaxRows) of one uniform pattern.  For each tile the producer warp copies
+// into shared memory, with cp.async.bulk: the tile's values, its rows of r_in,
+// x_in and 1/M, and for each group of nearby column offsets the contiguous
+// window of the multiplied vector that the group reads.  Consumer warps then
+// work from shared memory only.  Fewer, larger copies keep the TMA unit
+// streaming: tiles are 512 rows for FP64 and 1024 rows for FP32/BF16 vectors.
+constexpr int kTmaMaxRows = 1024;
+constexpr int kTmaConsumers = 16;
+constexpr int kTmaMaxW = 8;
+constexpr int kTmaMaxGroups = 4;
+constexpr int kTmaMaxStages = 8;
+
+struct TmaTile {
+  int64_t r0;     // first row of the tile
+  int64_t vbase;  // val[] index of the tile's first entry
+};
+
+struct TmaPlan {
+  int rows = 0;                     // rows per tile
+  int w = 0, ngroups = 0;
+  int g_start[kTmaMaxGroups] = {};  // window start, elements relative to the tile's first row
+  int g_elems[kTmaMaxGroups] = {};  // elements copied (multiple of 16 bytes)
+  int g_smem[kTmaMaxGroups] = {};   // element offset of the window in the stage's window area
+  int d[kTmaMaxW] = {};             // window-area index of row (tile start + offset_k)
+  int d0 = 0;                       // same for offset 0 (the row itself)
+  int vals_bytes = 0, vec_bytes = 0, win_bytes = 0, stage_bytes = 0, nstages = 0;
 };
 
 // Device scalar slots of the Krylov solver.
 enum Scalar {
   S_PQ = 0, S_RR = 1, S_RZ = 2, S_RZOLD = 3, S_ALPHA = 4, S_BB = 5, S_NRM = 6, S_BETA = 7,
+  S_ERR = 8,  // set non-zero by a kernel whose bounded wait gave up
   S_COUNT = 16
 };
 
@@ -77,6 +110,11 @@ struct RedWork {
 // ---- launchers (kernels_smooth.cu) ----
 template <class VT, class XT>
 void launch_step(const StepArgs<VT, XT>& a, cudaStream_t s);
+// Returns false (nothing launched) when the kernel cannot take these arguments
+// (a pointer not 16-byte aligned); the caller then uses launch_step.
+template <class VT, class XT>
+bool launch_step_tma(const StepArgs<VT, XT>& a, const TmaPlan& p, const TmaTile* tiles,
+                     int ntiles, int grid, double* err_slot, cudaStream_t s);
 template <class XT>
 void launch_first(int fam, int64_t n, const XT* b, const XT* dinv, XT* rout, XT* zout, XT* xout,
                   XT c2, XT beta, XT rhoinv, cudaStream_t s);
@@ -113,6 +151,7 @@ void launch_norm2(int64_t n, const XT* v, const RedWork& rw, double* scal, int s
                   cudaStream_t s);
 
 int reduction_grid(int64_t work_items, int nsm);
+void tma_configure(int max_dynamic_smem);
 
 // Kernels enqueued through the launchers above (graph captures included; the
 // host driver corrects for captures and adds graph replays).

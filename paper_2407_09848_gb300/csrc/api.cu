@@ -118,6 +118,13 @@ struct Level {
   double* ainv = nullptr;
   bool coarsest = false;
   Spec spec;
+  // TMA-fed step: eligible tiles, the other slices, and the stage layout
+  TmaPlan plan;
+  TmaTile* tma_tiles = nullptr;
+  int ntma = 0;
+  int tma_grid = 0;
+  int32_t* gen_slices = nullptr;
+  int64_t ngen = 0;
 };
 
 struct HostSell {
@@ -267,6 +274,135 @@ uint16_t dbl_to_bf16(double x) {
   return (uint16_t)(best >> 16);
 }
 
+// Dynamic shared memory per CTA of the TMA-fed step: two CTAs fit one SM
+// (2 x (115200 B + 1 KB driver reserve + static) <= 228 KB).
+constexpr int kTmaSmemBudget = 115200;
+
+struct HostPlan {
+  TmaPlan p;
+  std::vector<TmaTile> tiles;
+  std::vector<int32_t> gen;  // slices the TMA kernel does not cover
+};
+
+int64_t floor_to(int64_t x, int64_t a) { return x >= 0 ? x / a * a : -((-x + a - 1) / a) * a; }
+int64_t ceil_to(int64_t x, int64_t a) { return -floor_to(-x, a); }
+
+// Which tiles the TMA-fed step can take, and the shared-memory stage layout for
+// them.  A tile qualifies when all its slices share the level's most
+// frequent uniform pattern (width <= kTmaMaxW) and every window it copies lies
+// inside [0, n).  Every copy range and alignment is re-checked here on the host,
+// so the kernel never sees an out-of-bounds or misaligned bulk copy.
+HostPlan build_tma_plan(const HostSell& h, size_t vsize, size_t xsize, int smem_budget) {
+  HostPlan hp;
+  const int64_t n = h.n;
+  const int rows = xsize == 8 ? 512 : kTmaMaxRows;  // FP64 vectors: two 512-row stages per CTA
+  const int64_t ntf = n / rows;
+  const int spt = rows / kSlice;
+  hp.p.rows = rows;
+  auto candidate = [&](int64_t t, int32_t& cref, int& w) {
+    const SliceDesc d0 = h.sd[t * spt];
+    if (d0.cref < 0 || d0.w < 1 || d0.w > kTmaMaxW) return false;
+    for (int i = 1; i < spt; ++i) {
+      const SliceDesc d = h.sd[t * spt + i];
+      if (d.cref != d0.cref || d.w != d0.w || d.vbase != d0.vbase + (int64_t)i * d0.w * kSlice)
+        return false;
+    }
+    cref = d0.cref;
+    w = d0.w;
+    return true;
+  };
+  std::map<int32_t, int64_t> freq;
+  std::map<int32_t, int> width;
+  for (int64_t t = 0; t < ntf; ++t) {
+    int32_t cref;
+    int w;
+    if (candidate(t, cref, w)) {
+      freq[cref]++;
+      width[cref] = w;
+    }
+  }
+  std::vector<char> covered(h.nslices, 0);
+  auto finish = [&]() {
+    for (int64_t s = 0; s < h.nslices; ++s)
+      if (!covered[s]) hp.gen.push_back((int32_t)s);
+    return hp;
+  };
+  if (freq.empty()) return finish();
+  int32_t dom = freq.begin()->first;
+  for (auto& kv : freq)
+    if (kv.second > freq[dom]) dom = kv.first;
+  TmaPlan& P = hp.p;
+  P.w = width[dom];
+  const int32_t* off = h.off.data() + dom;
+  const int64_t A = 16 / (int64_t)xsize;
+  // groups of offsets whose tile-height windows overlap or touch
+  int gk[kTmaMaxW];
+  int64_t glo[kTmaMaxW], ghi[kTmaMaxW];
+  int ng = 0;
+  for (int k = 0; k < P.w; ++k) {
+    if (ng > 0 && off[k] - ghi[ng - 1] <= rows) {
+      ghi[ng - 1] = off[k];
+    } else {
+      glo[ng] = ghi[ng] = off[k];
+      ++ng;
+    }
+    gk[k] = ng - 1;
+  }
+  if (ng > kTmaMaxGroups) return finish();
+  P.ngroups = ng;
+  int64_t acc = 0;
+  for (int g = 0; g < ng; ++g) {
+    const int64_t st = floor_to(glo[g], A), en = ceil_to(ghi[g] + rows, A);
+    P.g_start[g] = (int)st;
+    P.g_elems[g] = (int)(en - st);
+    P.g_smem[g] = (int)acc;
+    acc += en - st;
+  }
+  bool has0 = false;
+  for (int k = 0; k < P.w; ++k) {
+    P.d[k] = P.g_smem[gk[k]] + (int)(off[k] - P.g_start[gk[k]]);
+    if (off[k] == 0) {
+      P.d0 = P.d[k];
+      has0 = true;
+    }
+  }
+  if (!has0) return finish();
+  P.vals_bytes = (int)(P.w * rows * vsize);
+  P.vec_bytes = (int)(rows * xsize);
+  P.win_bytes = (int)(acc * (int64_t)xsize);
+  P.stage_bytes = (int)ceil_to(P.vals_bytes + 3 * P.vec_bytes + P.win_bytes, 128);
+  P.nstages = std::min<int>(kTmaMaxStages, (smem_budget - 2 * kTmaMaxStages * 8) / P.stage_bytes);
+  if (P.nstages < 2) {
+    P.nstages = 0;
+    return finish();
+  }
+  for (int64_t t = 0; t < ntf; ++t) {
+    int32_t cref;
+    int w;
+    if (!candidate(t, cref, w) || cref != dom) continue;
+    const int64_t r0 = t * rows;
+    bool ok = true;
+    for (int g = 0; g < ng; ++g)
+      ok = ok && r0 + P.g_start[g] >= 0 && r0 + P.g_start[g] + P.g_elems[g] <= n;
+    if (!ok) continue;
+    const int64_t vb = h.sd[t * spt].vbase;
+    // host-side proof of every bulk copy of this tile: in bounds and 16-byte aligned
+    REQ(vb >= 0 && vb + (int64_t)P.w * rows <= h.stored && (vb * (int64_t)vsize) % 16 == 0,
+        AMGPS_E_ARG, "TMA plan: value copy out of range or misaligned");
+    REQ(r0 + rows <= n && (r0 * (int64_t)xsize) % 16 == 0, AMGPS_E_ARG,
+        "TMA plan: vector copy out of range or misaligned");
+    for (int g = 0; g < ng; ++g)
+      REQ(((r0 + P.g_start[g]) * (int64_t)xsize) % 16 == 0 &&
+              ((int64_t)P.g_elems[g] * (int64_t)xsize) % 16 == 0,
+          AMGPS_E_ARG, "TMA plan: window copy misaligned");
+    for (int k = 0; k < P.w; ++k)
+      REQ(P.d[k] >= 0 && P.d[k] + rows <= acc, AMGPS_E_ARG, "TMA plan: window index out of range");
+    hp.tiles.push_back(TmaTile{r0, vb});
+    for (int i = 0; i < spt; ++i) covered[t * spt + i] = 1;
+  }
+  return finish();
+}
+
 }  // namespace
 
 struct amgps_ctx {
@@ -291,6 +427,7 @@ struct amgps_ctx {
   cudaGraphExec_t gexec = nullptr;
   bool graph_ok = false;
   int64_t graph_kernels = 0;   // kernel nodes in gexec
+  bool use_tma = true;         // TMA-fed step kernels (option AMGPS_OPT_TMA)
   int64_t launch_adjust = 0;   // captured (not run) launches removed, replays added
   int64_t launch_base = 0;     // reset point of the launch counter
   bool prof = false;
@@ -475,6 +612,21 @@ double step_bytes(const Level& L, int nvec) {
 // ---------------------------------------------------------------------------
 template <class VT, class XT>
 struct Engine {
+  // One fused step on level L: the TMA-fed kernel over its tiles plus the
+  // direct kernel over the remaining slices, or the direct kernel alone.
+  static void run_step(amgps_ctx* c, const Level& L, StepArgs<VT, XT> a, cudaStream_t s) {
+    if (c->use_tma && L.ntma > 0 &&
+        launch_step_tma<VT, XT>(a, L.plan, L.tma_tiles, L.ntma, L.tma_grid, c->dscal + S_ERR, s)) {
+      if (L.ngen > 0) {
+        a.slices = L.gen_slices;
+        a.nlist = L.ngen;
+        launch_step<VT, XT>(a, s);
+      }
+    } else {
+      launch_step<VT, XT>(a, s);
+    }
+  }
+
   // One smoother application on level l: x <- S(b, x) (x = 0 when xzero).
   static void smooth(amgps_ctx* c, int l, const Coefs& cf, const XT* b, XT* x, bool xzero) {
     Level& L = c->lv[l];
@@ -506,7 +658,7 @@ struct Engine {
         a.fam = FAM_JAC;
         a.init = true;
         ProfScope ps(c, profl, 0, step_bytes<VT, XT>(L, 4));
-        launch_step<VT, XT>(a, s);
+        run_step(c, L, a, s);
         ps.done();
         std::swap(cur, oth);
       }
@@ -537,7 +689,7 @@ struct Engine {
       a.fam = cf.fam;
       a.init = true;
       ProfScope ps(c, profl, 0, step_bytes<VT, XT>(L, a.write_r ? 6 : 5));
-      launch_step<VT, XT>(a, s);
+      run_step(c, L, a, s);
       ps.done();
       xcur = xb;
       rin_next = r;
@@ -566,7 +718,7 @@ struct Engine {
       a.fam = cf.fam;
       a.init = false;
       ProfScope ps(c, profl, 0, step_bytes<VT, XT>(L, a.write_r ? 7 : 6));
-      launch_step<VT, XT>(a, s);
+      run_step(c, L, a, s);
       ps.done();
       xcur = x;
       rin_next = r;
@@ -756,6 +908,10 @@ void pcg_impl(amgps_ctx* c, const double* b, double* x, double rtol, int maxit, 
     CK(cudaEventRecord(c->ev_sync, s));
     CK(cudaEventSynchronize(c->ev_sync));
     harvest(c);
+    if (c->hscal[S_ERR] != 0.0) {
+      CK(cudaMemsetAsync(c->dscal + S_ERR, 0, sizeof(double), s));
+      throw Fail{AMGPS_E_TIMEOUT, "a bounded wait inside a pipelined kernel gave up"};
+    }
     const double pq = c->hscal[S_PQ], rr = c->hscal[S_RR];
     REQ(std::isfinite(pq) && std::isfinite(rr), AMGPS_E_NAN, "NaN/Inf in PCG scalars");
     REQ(pq > 0.0, AMGPS_E_NOT_SPD, "p^T A p <= 0 in PCG");
@@ -910,6 +1066,8 @@ amgps_status amgps_hierarchy_load(amgps_ctx* c, int n_levels, const amgps_csr* A
     enter(c);
     CK(cudaStreamSynchronize(c->stream));
     free_hierarchy(c);
+    tma_configure(kTmaSmemBudget + 2 * kTmaMaxStages * 8);
+    check_launch();
     c->prec = prec;
     c->lv.resize(n_levels);
     const size_t xs = (prec == AMGPS_F64) ? sizeof(double) : sizeof(float);
@@ -956,6 +1114,18 @@ amgps_status amgps_hierarchy_load(amgps_ctx* c, int n_levels, const amgps_csr* A
         std::vector<uint16_t> f(h.val.size());
         for (size_t i = 0; i < f.size(); ++i) f[i] = dbl_to_bf16(h.val[i]);
         L.val = dupload(c, f.data(), f.size());
+      }
+      {
+        const size_t vsz = prec == AMGPS_F64 ? 8 : (prec == AMGPS_F32 ? 4 : 2);
+        HostPlan hp = build_tma_plan(h, vsz, xs, kTmaSmemBudget);
+        L.plan = hp.p;
+        L.ntma = (int)hp.tiles.size();
+        L.ngen = (int64_t)hp.gen.size();
+        if (L.ntma > 0) {
+          L.tma_tiles = dupload(c, hp.tiles.data(), hp.tiles.size());
+          L.tma_grid = std::min<int>(L.ntma, 2 * c->nsm);
+        }
+        if (L.ngen > 0) L.gen_slices = dupload(c, hp.gen.data(), hp.gen.size());
       }
       if (l == 0 && prec != AMGPS_F64) {
         L.sd64 = L.sd;
@@ -1181,8 +1351,41 @@ amgps_status amgps_synchronize(amgps_ctx* c) {
   return guard(c, [&] {
     REQ(c, AMGPS_E_ARG, "null context");
     CK(cudaSetDevice(c->device));
+    CK(cudaMemcpyAsync(c->hscal + S_ERR, c->dscal + S_ERR, sizeof(double), cudaMemcpyDeviceToHost,
+                       c->stream));
     CK(cudaStreamSynchronize(c->stream));
     harvest(c);
+    if (c->hscal[S_ERR] != 0.0) {
+      CK(cudaMemset(c->dscal + S_ERR, 0, sizeof(double)));
+      throw Fail{AMGPS_E_TIMEOUT, "a bounded wait inside a pipelined kernel gave up"};
+    }
+  });
+}
+
+amgps_status amgps_set_option(amgps_ctx* c, int option, int64_t value) {
+  return guard(c, [&] {
+    REQ(c, AMGPS_E_ARG, "null context");
+    REQ(option == AMGPS_OPT_TMA, AMGPS_E_ARG, "unknown option");
+    c->use_tma = value != 0;
+    c->graph_ok = false;
+  });
+}
+
+amgps_status amgps_tma_plan_stats(const amgps_csr* A, amgps_prec prec, int64_t* tiles,
+                                  int64_t* generic_slices, int* stage_bytes, int* nstages) {
+  return guard(nullptr, [&] {
+    REQ(A, AMGPS_E_ARG, "null matrix");
+    REQ(prec == AMGPS_F64 || prec == AMGPS_F32 || prec == AMGPS_BF16, AMGPS_E_ARG,
+        "unknown precision");
+    validate_csr(*A, "A", true);
+    HostSell h = build_sell(*A);
+    const size_t vsz = prec == AMGPS_F64 ? 8 : (prec == AMGPS_F32 ? 4 : 2);
+    const size_t xsz = prec == AMGPS_F64 ? 8 : 4;
+    HostPlan hp = build_tma_plan(h, vsz, xsz, kTmaSmemBudget);
+    if (tiles) *tiles = (int64_t)hp.tiles.size();
+    if (generic_slices) *generic_slices = (int64_t)hp.gen.size();
+    if (stage_bytes) *stage_bytes = hp.p.stage_bytes;
+    if (nstages) *nstages = hp.p.nstages;
   });
 }
 

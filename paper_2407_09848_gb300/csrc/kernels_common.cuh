@@ -57,6 +57,42 @@ __device__ __forceinline__ XT row_spmv(const DevMat<VT>& A, int64_t s, int lane,
   return t;
 }
 
+// The SpMV of one smoother step is accumulated as init + SIGN * (A u):
+// r_j = r_{j-1} - A z_j directly for the 4th kind, the 1st-kind initial step
+// and Jacobi (init = r_in, SIGN = -1); the plain product t = A d for the
+// other 1st-kind steps (init = 0, SIGN = +1).
+template <int FAM, bool INIT>
+struct StepForm {
+  static constexpr bool kResidual = !(FAM == FAM_CHEB1 && !INIT);
+  static constexpr int kSign = kResidual ? -1 : 1;
+};
+
+// Epilogue of one smoother step for one row, given the accumulated SpMV and
+// the row's own vector entries (see kernels_smooth.cu for the recurrences).
+template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN>
+__device__ __forceinline__ void step_finish(const StepArgs<VT, XT>& a, int64_t row, XT acc, XT rin,
+                                            XT xin, XT di, XT zo) {
+  if constexpr (FAM == FAM_CHEB4) {
+    const XT r = acc;
+    if (WR) a.rout[row] = r;
+    XT z = a.c2 * (r * di);
+    if (ZOWN) z = fma(a.c1, zo, z);
+    a.zout[row] = z;
+    a.xout[row] = fma(a.beta, z, xin);
+  } else if constexpr (FAM == FAM_CHEB1) {
+    XT r;
+    if (INIT) r = a.rhoinv * (acc * di);
+    else r = fma(-(a.rhoinv * di), acc, rin);
+    if (WR) a.rout[row] = r;
+    XT z = a.c2 * r;
+    if (ZOWN) z = fma(a.c1, zo, z);
+    a.zout[row] = z;
+    a.xout[row] = xin + z;
+  } else {
+    a.xout[row] = fma(acc, di, xin);
+  }
+}
+
 // Sum over a block (any blockDim multiple of 32, <= 1024); result valid in thread 0.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
 #pragma unroll

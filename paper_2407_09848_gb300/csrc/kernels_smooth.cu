@@ -28,8 +28,13 @@ namespace amgps {
 template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN>
 __global__ void __launch_bounds__(kBlock) k_step(const StepArgs<VT, XT> a) {
   const int lane = threadIdx.x & 31;
-  const int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  if (s >= a.A.nslices) return;
+  int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (a.slices) {
+    if (s >= a.nlist) return;
+    s = a.slices[s];
+  } else if (s >= a.A.nslices) {
+    return;
+  }
   const int64_t row = s * kSlice + lane;
   const bool live = row < a.A.n;
   XT rin = XT(0), xin = XT(0), zo = XT(0), di = XT(0);
@@ -39,36 +44,10 @@ __global__ void __launch_bounds__(kBlock) k_step(const StepArgs<VT, XT> a) {
     di = a.dinv[row];
     if (ZOWN) zo = a.zown[row];
   }
-  if constexpr (FAM == FAM_CHEB4) {
-    // r_j = r_{j-1} - A z_j accumulated directly (7 FMAs for a 7-point row)
-    const XT r = row_spmv<-1, VT, XT>(a.A, s, lane, row, a.u, rin);
-    if (!live) return;
-    if (WR) a.rout[row] = r;
-    XT z = a.c2 * (r * di);
-    if (ZOWN) z = fma(a.c1, zo, z);
-    a.zout[row] = z;
-    a.xout[row] = fma(a.beta, z, xin);
-  } else if constexpr (FAM == FAM_CHEB1) {
-    XT r;
-    if (INIT) {
-      const XT res = row_spmv<-1, VT, XT>(a.A, s, lane, row, a.u, rin);
-      if (!live) return;
-      r = a.rhoinv * (res * di);
-    } else {
-      const XT t = row_spmv<1, VT, XT>(a.A, s, lane, row, a.u, XT(0));
-      if (!live) return;
-      r = fma(-(a.rhoinv * di), t, rin);
-    }
-    if (WR) a.rout[row] = r;
-    XT z = a.c2 * r;
-    if (ZOWN) z = fma(a.c1, zo, z);
-    a.zout[row] = z;
-    a.xout[row] = xin + z;
-  } else {
-    const XT res = row_spmv<-1, VT, XT>(a.A, s, lane, row, a.u, rin);
-    if (!live) return;
-    a.xout[row] = fma(res, di, xin);
-  }
+  using F = StepForm<FAM, INIT>;
+  const XT acc = row_spmv<F::kSign, VT, XT>(a.A, s, lane, row, a.u, F::kResidual ? rin : XT(0));
+  if (!live) return;
+  step_finish<VT, XT, FAM, INIT, WR, ZOWN>(a, row, acc, rin, xin, di, zo);
 }
 
 template <class VT, class XT, int FAM, bool INIT>
@@ -86,8 +65,9 @@ static void dispatch_wr(const StepArgs<VT, XT>& a, dim3 g, cudaStream_t s) {
 
 template <class VT, class XT>
 void launch_step(const StepArgs<VT, XT>& a, cudaStream_t s) {
-  if (a.A.nslices == 0) return;
-  dim3 g((unsigned)((a.A.nslices + kWarpsPerBlock - 1) / kWarpsPerBlock));
+  const int64_t work = a.slices ? a.nlist : a.A.nslices;
+  if (work == 0) return;
+  dim3 g((unsigned)((work + kWarpsPerBlock - 1) / kWarpsPerBlock));
   switch (a.fam) {
     case FAM_CHEB4:
       if (a.init) dispatch_wr<VT, XT, FAM_CHEB4, true>(a, g, s);

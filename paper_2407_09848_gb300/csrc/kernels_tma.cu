@@ -1,0 +1,277 @@
+// TMA-fed fused smoother step: the k_step recurrences (Sec. 2.1, 2.2) with
+// every global read staged by the Tensor Memory Accelerator.
+//
+// A persistent grid walks a list of 256-row tiles round-robin, so the tiles in
+// flight at any moment form one contiguous band and the vector windows that
+// neighbouring tiles share are read from HBM once and then from L2.  Warp 0 of
+// each CTA is the producer: one lane issues cp.async.bulk copies of a tile's
+// values, of its rows of r_in, x_in and 1/M, and of the contiguous windows of
+// the multiplied vector u (one per group of nearby column offsets) into a
+// shared-memory stage, completing on that stage's "full" mbarrier.  Warps
+// 1..8 are consumers, one 32-row slice each: they wait on "full", evaluate
+// the row from shared memory, store r/z/x to global memory, and arrive on the
+// stage's "empty" mbarrier so the producer may refill it.  The arithmetic and
+// its order are those of k_step, so both paths give the same bits.
+//
+// Every wait is bounded (kWaitSpins polls).  A wait that gives up sets the
+// solver's error slot and makes all warps leave their loops; the producer
+// still waits (bounded) for the copies it issued before it exits.
+#include "kernels_common.cuh"
+
+namespace amgps {
+namespace {
+
+constexpr uint32_t kWaitSpins = 1u << 21;
+constexpr int kBarrierBytes = 2 * kTmaMaxStages * 8;  // full[] and empty[] (128 B)
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(su32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// true when the phase of `parity` has completed; false after kWaitSpins polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kWaitSpins; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(su32(dst)),
+      "l"(src), "r"(bytes), "r"(su32(bar))
+      : "memory");
+}
+
+template <class XT>
+__device__ __forceinline__ XT widen(double v) { return XT(v); }
+template <class XT>
+__device__ __forceinline__ XT widen(float v) { return XT(v); }
+template <class XT>
+__device__ __forceinline__ XT widen(__nv_bfloat16 v) { return XT(__bfloat162float(v)); }
+
+template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN>
+__global__ void __launch_bounds__((kTmaConsumers + 1) * 32, 1)
+    k_step_tma(const StepArgs<VT, XT> a, const TmaPlan p, const TmaTile* __restrict__ tiles,
+               int ntiles, double* err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ volatile int abort_flag;
+  __shared__ long long stage_r0[kTmaMaxStages];  // first row of the tile held by each stage
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* empty = full + kTmaMaxStages;
+  unsigned char* stages = smem + kBarrierBytes;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ns = p.nstages;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < ns; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kTmaConsumers);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == 0) {
+    // The whole warp fetches the descriptors of this CTA's next 32 tiles in one
+    // load; lane 0 then issues their copies without a global round trip per tile.
+    int it = 0;
+    for (int j0 = blockIdx.x; j0 < ntiles; j0 += 32 * gridDim.x) {
+      if (__shfl_sync(0xffffffffu, (int)abort_flag, 0)) break;  // warp-uniform exit
+      const int jl = j0 + lane * gridDim.x;
+      TmaTile mine{0, 0};
+      if (jl < ntiles) mine = tiles[jl];
+      const int cnt = min(32, (ntiles - j0 + (int)gridDim.x - 1) / (int)gridDim.x);
+      for (int q = 0; q < cnt; ++q) {
+        const long long rq = __shfl_sync(0xffffffffu, (long long)mine.r0, q);
+        const long long vq = __shfl_sync(0xffffffffu, (long long)mine.vbase, q);
+        if (lane == 0) {
+          const int st = it % ns;
+          const uint32_t ph = (uint32_t)(it / ns) & 1u;
+          if (abort_flag || !mbar_wait(&empty[st], ph ^ 1u)) {
+            abort_flag = 1;
+          } else {
+            unsigned char* base = stages + (size_t)st * p.stage_bytes;
+            const int64_t r0 = rq;
+            stage_r0[st] = rq;
+            mbar_expect_tx(&full[st], (uint32_t)(p.vals_bytes + 3 * p.vec_bytes + p.win_bytes));
+            bulk_g2s(base, a.A.val + vq, (uint32_t)p.vals_bytes, &full[st]);
+            XT* sv = reinterpret_cast<XT*>(base + p.vals_bytes);
+            bulk_g2s(sv, a.rin + r0, (uint32_t)p.vec_bytes, &full[st]);
+            bulk_g2s(sv + p.rows, a.xin + r0, (uint32_t)p.vec_bytes, &full[st]);
+            bulk_g2s(sv + 2 * p.rows, a.dinv + r0, (uint32_t)p.vec_bytes, &full[st]);
+            XT* sw = sv + 3 * p.rows;
+            for (int g = 0; g < p.ngroups; ++g)
+              bulk_g2s(sw + p.g_smem[g], a.u + r0 + p.g_start[g],
+                       (uint32_t)(p.g_elems[g] * (int)sizeof(XT)), &full[st]);
+          }
+        }
+        ++it;
+        if (__shfl_sync(0xffffffffu, (int)abort_flag, 0)) break;
+      }
+    }
+    if (lane == 0) {
+      // the last fill of each stage must have landed before this CTA exits
+      const int first = it > ns ? it - ns : 0;
+      for (int q = first; q < it; ++q)
+        if (!mbar_wait(&full[q % ns], (uint32_t)(q / ns) & 1u)) abort_flag = 1;
+      if (abort_flag) *err = 1.0;
+    }
+    return;
+  }
+
+  const int c = warp - 1;
+  const int spt = p.rows / kSlice;  // slices per tile
+  using F = StepForm<FAM, INIT>;
+  int it = 0;
+  for (int j = blockIdx.x; j < ntiles; j += gridDim.x, ++it) {
+    const int st = it % ns;
+    const uint32_t ph = (uint32_t)(it / ns) & 1u;
+    if (abort_flag || !mbar_wait(&full[st], ph)) {
+      abort_flag = 1;
+      break;
+    }
+    const unsigned char* base = stages + (size_t)st * p.stage_bytes;
+    const XT* sv = reinterpret_cast<const XT*>(base + p.vals_bytes);
+    const XT* sw = sv + 3 * p.rows;
+    const int64_t r0 = stage_r0[st];
+    for (int cs = c; cs < spt; cs += kTmaConsumers) {
+      const int it_row = cs * kSlice + lane;  // row inside the tile
+      const VT* svals = reinterpret_cast<const VT*>(base) + (size_t)cs * p.w * kSlice + lane;
+      const XT rin = sv[it_row], xin = sv[p.rows + it_row], di = sv[2 * p.rows + it_row];
+      const XT zo = ZOWN ? sw[p.d0 + it_row] : XT(0);
+      XT acc = F::kResidual ? rin : XT(0);
+#pragma unroll
+      for (int k = 0; k < kTmaMaxW; ++k) {
+        if (k < p.w) {
+          const XT av = widen<XT>(svals[k * kSlice]);
+          acc = fma(F::kSign > 0 ? av : -av, sw[p.d[k] + it_row], acc);
+        }
+      }
+      step_finish<VT, XT, FAM, INIT, WR, ZOWN>(a, r0 + it_row, acc, rin, xin, di, zo);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);
+  }
+  if (abort_flag && lane == 0) *err = 1.0;
+}
+
+template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN>
+void launch_inst(const StepArgs<VT, XT>& a, const TmaPlan& p, const TmaTile* tiles, int ntiles,
+                 int grid, double* err, cudaStream_t s) {
+  const int smem = kBarrierBytes + p.nstages * p.stage_bytes;
+  k_step_tma<VT, XT, FAM, INIT, WR, ZOWN>
+      <<<grid, (kTmaConsumers + 1) * 32, smem, s>>>(a, p, tiles, ntiles, err);
+  count_launch();
+}
+
+template <class VT, class XT, int FAM, bool INIT>
+void launch_wr(const StepArgs<VT, XT>& a, const TmaPlan& p, const TmaTile* tiles, int ntiles,
+               int grid, double* err, cudaStream_t s) {
+  const bool z = a.zown != nullptr;
+  if (a.write_r) {
+    if (z) launch_inst<VT, XT, FAM, INIT, true, true>(a, p, tiles, ntiles, grid, err, s);
+    else launch_inst<VT, XT, FAM, INIT, true, false>(a, p, tiles, ntiles, grid, err, s);
+  } else {
+    if (z) launch_inst<VT, XT, FAM, INIT, false, true>(a, p, tiles, ntiles, grid, err, s);
+    else launch_inst<VT, XT, FAM, INIT, false, false>(a, p, tiles, ntiles, grid, err, s);
+  }
+}
+
+template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN>
+void set_smem_attr(int bytes) {
+  cudaFuncSetAttribute(k_step_tma<VT, XT, FAM, INIT, WR, ZOWN>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <class VT, class XT>
+void configure_all(int bytes) {
+  set_smem_attr<VT, XT, FAM_CHEB4, true, true, true>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB4, true, true, false>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB4, true, false, true>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB4, true, false, false>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB4, false, true, true>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB4, false, true, false>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB4, false, false, true>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB4, false, false, false>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB1, true, true, true>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB1, true, true, false>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB1, true, false, true>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB1, true, false, false>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB1, false, true, true>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB1, false, true, false>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB1, false, false, true>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB1, false, false, false>(bytes);
+  set_smem_attr<VT, XT, FAM_JAC, true, false, false>(bytes);
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+void tma_configure(int max_dynamic_smem) {
+  configure_all<double, double>(max_dynamic_smem);
+  configure_all<float, float>(max_dynamic_smem);
+  configure_all<__nv_bfloat16, float>(max_dynamic_smem);
+}
+
+template <class VT, class XT>
+bool launch_step_tma(const StepArgs<VT, XT>& a, const TmaPlan& p, const TmaTile* tiles,
+                     int ntiles, int grid, double* err, cudaStream_t s) {
+  if (ntiles <= 0 || p.nstages < 2) return false;
+  if (!aligned16(a.A.val) || !aligned16(a.u) || !aligned16(a.rin) || !aligned16(a.xin) ||
+      !aligned16(a.dinv))
+    return false;
+  if (a.zown && a.zown != a.u) return false;  // z_j at the row is read from u's window
+  switch (a.fam) {
+    case FAM_CHEB4:
+      if (a.init) launch_wr<VT, XT, FAM_CHEB4, true>(a, p, tiles, ntiles, grid, err, s);
+      else launch_wr<VT, XT, FAM_CHEB4, false>(a, p, tiles, ntiles, grid, err, s);
+      break;
+    case FAM_CHEB1:
+      if (a.init) launch_wr<VT, XT, FAM_CHEB1, true>(a, p, tiles, ntiles, grid, err, s);
+      else launch_wr<VT, XT, FAM_CHEB1, false>(a, p, tiles, ntiles, grid, err, s);
+      break;
+    default:
+      launch_inst<VT, XT, FAM_JAC, true, false, false>(a, p, tiles, ntiles, grid, err, s);
+  }
+  return true;
+}
+
+template bool launch_step_tma<double, double>(const StepArgs<double, double>&, const TmaPlan&,
+                                              const TmaTile*, int, int, double*, cudaStream_t);
+template bool launch_step_tma<float, float>(const StepArgs<float, float>&, const TmaPlan&,
+                                            const TmaTile*, int, int, double*, cudaStream_t);
+template bool launch_step_tma<__nv_bfloat16, float>(const StepArgs<__nv_bfloat16, float>&,
+                                                    const TmaPlan&, const TmaTile*, int, int,
+                                                    double*, cudaStream_t);
+
+}  // namespace amgps

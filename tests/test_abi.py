@@ -77,3 +77,35 @@ def test_null_arguments_rejected_on_host(lib):
     assert lib.amgps_pcg(None, None, None, 1e-8, 10, None, None) == 1
     assert lib.amgps_destroy(None) == 0
     assert lib.amgps_opt4_weights(4, None) == 1
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+def test_tma_plan_covers_and_checks_copies(lib, prec):
+    # host-only: the plan proves every bulk copy in bounds / aligned (else E_ARG)
+    from paper_2407_09848_gb300 import problems as pr
+    for st in (pr.poisson(16), pr.poisson(33, 17, 9), pr.varcoef(24, 1.0, 4.0, seed=1),
+               pr.poisson(64)):
+        H = pr.build_hierarchy(st)
+        for lv in H.levels[:-1]:
+            n = lv.A.shape[0]
+            tiles, gen, stage, nst = amgps.tma_plan_stats(lv.A, prec)
+            nslices = (n + 31) // 32
+            per = (512 if prec == "f64" else 1024) // 32
+            assert tiles * per + gen == nslices
+            if tiles:
+                assert 2 <= nst <= 8 and nst * stage + 128 <= 115200 and stage % 128 == 0
+    # 64^3: (almost) every tile whose +-4096-row windows stay inside the vector
+    # qualifies; the exceptions are tiles where the slice pattern changes
+    H = pr.build_hierarchy(pr.poisson(64))
+    tiles, gen, _, _ = amgps.tma_plan_stats(H.levels[0].A, prec)
+    rows = 512 if prec == "f64" else 1024
+    per = rows // 32
+    assert tiles * per + gen == 8192 and tiles >= (262144 - 2 * 4096) // rows - 64 // per - 2
+
+
+def test_tma_plan_rejects_bad_csr(lib):
+    import scipy.sparse as sp
+    A = sp.csr_matrix(np.array([[2.0, -1.0], [-1.0, 2.0]]))
+    A.indices[0] = 5  # column out of range
+    with pytest.raises(amgps.AmgpsError):
+        amgps.tma_plan_stats(A, "f64")

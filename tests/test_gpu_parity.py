@@ -316,3 +316,44 @@ def test_profile_counts(poisson32):
     assert n_step == 7 * it and ms > 0 and by > 0
     n_sp, ms_sp, _ = S.profile_read(2, reset=True)
     assert n_sp == it and ms_sp > 0
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+def test_tma_step_equals_direct_step(torch_cuda, prec):
+    # the TMA-fed kernel evaluates the same arithmetic in the same order as the
+    # direct-load kernel: results must agree bit for bit
+    from paper_2407_09848_gb300.amgps import Solver
+    torch = torch_cuda
+    H = pr.build_hierarchy(pr.varcoef(48, 1.0, 4.0, seed=3, ny=40, nz=36), coarse_max=512)
+    S = Solver().load(H.A, H.P, prec=prec)
+    rng = np.random.default_rng(12)
+    for level in (0, 1):
+        n = H.levels[level].A.shape[0]
+        b = to_dev(torch, rng.uniform(-1, 1, n))
+        x0 = to_dev(torch, rng.uniform(-1, 1, n))
+        for kind, k in [("cheb4_opt", 4), ("cheb4", 2), ("cheb1_opt", 3), ("l1jacobi", 3),
+                        ("cheb1", 2), ("weights", 3)]:
+            if kind == "weights" and level != 0:
+                continue
+            if kind == "cheb1":
+                S.set_smoother(level, "cheb1", k, rho=1.05)
+            if kind == "weights":
+                S.set_smoother(level, "weights", 3, weights=[1.1, 0.9, 1.3])
+            for zero in (True, False):
+                outs = []
+                for tma in (True, False):
+                    S.set_tma(tma)
+                    x = x0.clone()
+                    S.smooth(level, kind, k, b, x, x_is_zero=zero)
+                    outs.append(x)
+                S.synchronize()
+                assert torch.equal(outs[0], outs[1]), (prec, level, kind, k, zero)
+    S.set_tma(True)
+    z1 = torch.empty(H.levels[0].A.shape[0], dtype=torch.float64, device="cuda")
+    z2 = torch.empty_like(z1)
+    r = to_dev(torch, rng.uniform(-1, 1, H.levels[0].A.shape[0]))
+    S.vcycle(r, z1)
+    S.set_tma(False)
+    S.vcycle(r, z2)
+    S.synchronize()
+    assert torch.equal(z1, z2)

@@ -42,7 +42,9 @@ struct DevMat {
   const int32_t* off = nullptr;
 };
 
-enum Family { FAM_CHEB4 = 0, FAM_CHEB1 = 1, FAM_JAC = 2 };
+// FAM_RES is not a smoother: it writes the true residual b - A x (rin = b,
+// u = x, result in zout) for the restriction of Eq. amg.
+enum Family { FAM_CHEB4 = 0, FAM_CHEB1 = 1, FAM_JAC = 2, FAM_RES = 3 };
 
 // Arguments of one fused smoother step (see kernels_smooth.cu).
 template <class VT, class XT>
@@ -118,9 +120,10 @@ bool launch_step_tma(const StepArgs<VT, XT>& a, const TmaPlan& p, const TmaTile*
 template <class XT>
 void launch_first(int fam, int64_t n, const XT* b, const XT* dinv, XT* rout, XT* zout, XT* xout,
                   XT c2, XT beta, XT rhoinv, cudaStream_t s);
-template <class VT, class XT>
-void launch_resid_restrict(const DevMat<VT>& A, const XT* x, const XT* b, const int32_t* cptr,
-                           const int32_t* cidx, int64_t nc, XT* bc, cudaStream_t s);
+// b_c[I] = sum of res over the children of coarse row I (children lists)
+template <class XT>
+void launch_aggregate(const int32_t* cptr, const int32_t* cidx, int64_t nc, const XT* res, XT* bc,
+                      cudaStream_t s);
 template <class XT>
 void launch_prolong(int64_t n, const int32_t* agg, const XT* ec, XT* x, cudaStream_t s);
 template <class VT, class XT>

@@ -740,10 +740,20 @@ struct Engine {
     smooth(c, l, cf, b, x, true);
     Level& C = c->lv[l + 1];
     {
+      // b_{l+1} = P^T (b - A x): the true residual (into the level's r buffer,
+      // free between the smoothers), then the children sums of each aggregate
       ProfScope ps(c, l == 0, 1,
                    (double)L.nnz * sizeof(VT) + (double)L.explicit_entries * 4.0 +
-                       (double)L.n * sizeof(XT) * 2 + (double)L.n * 4 + (double)C.n * 12);
-      launch_resid_restrict<VT, XT>(devmat<VT>(L), x, b, L.cptr, L.cidx, L.nc, (XT*)C.b, s);
+                       (double)L.n * sizeof(XT) * 4 + (double)L.n * 4 + (double)C.n * 12);
+      StepArgs<VT, XT> a;
+      a.A = devmat<VT>(L);
+      a.u = x;
+      a.rin = b;
+      a.zout = (XT*)L.r;
+      a.fam = FAM_RES;
+      a.init = true;
+      run_step(c, L, a, s);
+      launch_aggregate<XT>(L.cptr, L.cidx, L.nc, (const XT*)L.r, (XT*)C.b, s);
       ps.done();
     }
     if (l + 1 == 1 && c->graph_ok && !capturing(c)) {

@@ -88,8 +88,10 @@ __device__ __forceinline__ void step_finish(const StepArgs<VT, XT>& a, int64_t r
     if (ZOWN) z = fma(a.c1, zo, z);
     a.zout[row] = z;
     a.xout[row] = xin + z;
-  } else {
+  } else if constexpr (FAM == FAM_JAC) {
     a.xout[row] = fma(acc, di, xin);
+  } else {
+    a.zout[row] = acc;  // FAM_RES: the true residual b - A x
   }
 }
 

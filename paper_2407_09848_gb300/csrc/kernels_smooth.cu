@@ -40,8 +40,10 @@ __global__ void __launch_bounds__(kBlock) k_step(const StepArgs<VT, XT> a) {
   XT rin = XT(0), xin = XT(0), zo = XT(0), di = XT(0);
   if (live) {
     rin = a.rin[row];
-    xin = a.xin[row];
-    di = a.dinv[row];
+    if (FAM != FAM_RES) {
+      xin = a.xin[row];
+      di = a.dinv[row];
+    }
     if (ZOWN) zo = a.zown[row];
   }
   using F = StepForm<FAM, INIT>;
@@ -76,6 +78,10 @@ void launch_step(const StepArgs<VT, XT>& a, cudaStream_t s) {
     case FAM_CHEB1:
       if (a.init) dispatch_wr<VT, XT, FAM_CHEB1, true>(a, g, s);
       else dispatch_wr<VT, XT, FAM_CHEB1, false>(a, g, s);
+      break;
+    case FAM_RES:
+      k_step<VT, XT, FAM_RES, true, false, false><<<g, kBlock, 0, s>>>(a);
+      count_launch();
       break;
     default:
       k_step<VT, XT, FAM_JAC, true, false, false><<<g, kBlock, 0, s>>>(a);
@@ -125,39 +131,28 @@ void launch_first(int fam, int64_t n, const XT* b, const XT* dinv, XT* rout, XT*
   count_launch();
 }
 
-// b_c = P^T (b - A x) for an unsmoothed aggregation P (Sec. 2): eight lanes per
-// coarse row walk its children (cidx[cptr[I] .. cptr[I+1])), each computing the
-// true residual of a child row; the eight partial sums meet in a fixed shuffle
-// tree, so the result does not depend on scheduling.
-template <class VT, class XT>
-__global__ void __launch_bounds__(kBlock) k_resid_restrict(const DevMat<VT> A,
-                                                           const XT* __restrict__ x,
-                                                           const XT* __restrict__ b,
-                                                           const int32_t* __restrict__ cptr,
-                                                           const int32_t* __restrict__ cidx,
-                                                           int64_t nc, XT* __restrict__ bc) {
-  const int g = threadIdx.x & 7;
-  const int64_t I = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 3;
+// b_c = P^T res for an unsmoothed aggregation P (Sec. 2): one thread per coarse
+// row adds the residuals of its children (cidx[cptr[I] .. cptr[I+1])) in list
+// order, so the sum does not depend on scheduling.  The residual itself comes
+// from the FAM_RES step (pipelined and coalesced like the smoother steps).
+template <class XT>
+__global__ void __launch_bounds__(kBlock) k_aggregate(const int32_t* __restrict__ cptr,
+                                                      const int32_t* __restrict__ cidx, int64_t nc,
+                                                      const XT* __restrict__ res,
+                                                      XT* __restrict__ bc) {
+  const int64_t I = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (I >= nc) return;
   XT acc = XT(0);
-  if (I < nc) {
-    const int q1 = cptr[I + 1];
-    for (int q = cptr[I] + g; q < q1; q += 8) {
-      const int64_t i = cidx[q];
-      acc += row_spmv<-1, VT, XT>(A, i >> 5, (int)(i & 31), i, x, b[i]);
-    }
-  }
-  acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-  if (g == 0 && I < nc) bc[I] = acc;
+  const int q1 = cptr[I + 1];
+  for (int q = cptr[I]; q < q1; ++q) acc += res[cidx[q]];
+  bc[I] = acc;
 }
 
-template <class VT, class XT>
-void launch_resid_restrict(const DevMat<VT>& A, const XT* x, const XT* b, const int32_t* cptr,
-                           const int32_t* cidx, int64_t nc, XT* bc, cudaStream_t s) {
+template <class XT>
+void launch_aggregate(const int32_t* cptr, const int32_t* cidx, int64_t nc, const XT* res, XT* bc,
+                      cudaStream_t s) {
   if (nc == 0) return;
-  dim3 g((unsigned)((nc * 8 + kBlock - 1) / kBlock));
-  k_resid_restrict<VT, XT><<<g, kBlock, 0, s>>>(A, x, b, cptr, cidx, nc, bc);
+  k_aggregate<XT><<<(unsigned)((nc + kBlock - 1) / kBlock), kBlock, 0, s>>>(cptr, cidx, nc, res, bc);
   count_launch();
 }
 
@@ -225,9 +220,6 @@ void launch_convert(int64_t n, const A* in, B* out, cudaStream_t s) {
 
 #define AMGPS_INST(VT, XT)                                                                   \
   template void launch_step<VT, XT>(const StepArgs<VT, XT>&, cudaStream_t);                  \
-  template void launch_resid_restrict<VT, XT>(const DevMat<VT>&, const XT*, const XT*,       \
-                                              const int32_t*, const int32_t*, int64_t, XT*,  \
-                                              cudaStream_t);                                 \
   template void launch_l1diag<VT, XT>(const DevMat<VT>&, XT*, cudaStream_t);
 AMGPS_INST(double, double)
 AMGPS_INST(float, float)
@@ -238,6 +230,10 @@ template void launch_first<double>(int, int64_t, const double*, const double*, d
                                    double*, double, double, double, cudaStream_t);
 template void launch_first<float>(int, int64_t, const float*, const float*, float*, float*,
                                   float*, float, float, float, cudaStream_t);
+template void launch_aggregate<double>(const int32_t*, const int32_t*, int64_t, const double*,
+                                       double*, cudaStream_t);
+template void launch_aggregate<float>(const int32_t*, const int32_t*, int64_t, const float*, float*,
+                                      cudaStream_t);
 template void launch_prolong<double>(int64_t, const int32_t*, const double*, double*, cudaStream_t);
 template void launch_prolong<float>(int64_t, const int32_t*, const float*, float*, cudaStream_t);
 template void launch_convert<double, float>(int64_t, const double*, float*, cudaStream_t);

@@ -122,12 +122,15 @@ __global__ void __launch_bounds__((kTmaConsumers + 1) * 32, 1)
             unsigned char* base = stages + (size_t)st * p.stage_bytes;
             const int64_t r0 = rq;
             stage_r0[st] = rq;
-            mbar_expect_tx(&full[st], (uint32_t)(p.vals_bytes + 3 * p.vec_bytes + p.win_bytes));
+            constexpr int nvec = FAM == FAM_RES ? 1 : 3;  // the residual needs no x_in, 1/M
+            mbar_expect_tx(&full[st], (uint32_t)(p.vals_bytes + nvec * p.vec_bytes + p.win_bytes));
             bulk_g2s(base, a.A.val + vq, (uint32_t)p.vals_bytes, &full[st]);
             XT* sv = reinterpret_cast<XT*>(base + p.vals_bytes);
             bulk_g2s(sv, a.rin + r0, (uint32_t)p.vec_bytes, &full[st]);
-            bulk_g2s(sv + p.rows, a.xin + r0, (uint32_t)p.vec_bytes, &full[st]);
-            bulk_g2s(sv + 2 * p.rows, a.dinv + r0, (uint32_t)p.vec_bytes, &full[st]);
+            if (FAM != FAM_RES) {
+              bulk_g2s(sv + p.rows, a.xin + r0, (uint32_t)p.vec_bytes, &full[st]);
+              bulk_g2s(sv + 2 * p.rows, a.dinv + r0, (uint32_t)p.vec_bytes, &full[st]);
+            }
             XT* sw = sv + 3 * p.rows;
             for (int g = 0; g < p.ngroups; ++g)
               bulk_g2s(sw + p.g_smem[g], a.u + r0 + p.g_start[g],
@@ -166,7 +169,9 @@ __global__ void __launch_bounds__((kTmaConsumers + 1) * 32, 1)
     for (int cs = c; cs < spt; cs += kTmaConsumers) {
       const int it_row = cs * kSlice + lane;  // row inside the tile
       const VT* svals = reinterpret_cast<const VT*>(base) + (size_t)cs * p.w * kSlice + lane;
-      const XT rin = sv[it_row], xin = sv[p.rows + it_row], di = sv[2 * p.rows + it_row];
+      const XT rin = sv[it_row];
+      const XT xin = FAM == FAM_RES ? XT(0) : sv[p.rows + it_row];
+      const XT di = FAM == FAM_RES ? XT(0) : sv[2 * p.rows + it_row];
       const XT zo = ZOWN ? sw[p.d0 + it_row] : XT(0);
       XT acc = F::kResidual ? rin : XT(0);
 #pragma unroll
@@ -231,6 +236,7 @@ void configure_all(int bytes) {
   set_smem_attr<VT, XT, FAM_CHEB1, false, false, true>(bytes);
   set_smem_attr<VT, XT, FAM_CHEB1, false, false, false>(bytes);
   set_smem_attr<VT, XT, FAM_JAC, true, false, false>(bytes);
+  set_smem_attr<VT, XT, FAM_RES, true, false, false>(bytes);
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -247,9 +253,8 @@ template <class VT, class XT>
 bool launch_step_tma(const StepArgs<VT, XT>& a, const TmaPlan& p, const TmaTile* tiles,
                      int ntiles, int grid, double* err, cudaStream_t s) {
   if (ntiles <= 0 || p.nstages < 2) return false;
-  if (!aligned16(a.A.val) || !aligned16(a.u) || !aligned16(a.rin) || !aligned16(a.xin) ||
-      !aligned16(a.dinv))
-    return false;
+  if (!aligned16(a.A.val) || !aligned16(a.u) || !aligned16(a.rin)) return false;
+  if (a.fam != FAM_RES && (!aligned16(a.xin) || !aligned16(a.dinv))) return false;
   if (a.zown && a.zown != a.u) return false;  // z_j at the row is read from u's window
   switch (a.fam) {
     case FAM_CHEB4:
@@ -259,6 +264,9 @@ bool launch_step_tma(const StepArgs<VT, XT>& a, const TmaPlan& p, const TmaTile*
     case FAM_CHEB1:
       if (a.init) launch_wr<VT, XT, FAM_CHEB1, true>(a, p, tiles, ntiles, grid, err, s);
       else launch_wr<VT, XT, FAM_CHEB1, false>(a, p, tiles, ntiles, grid, err, s);
+      break;
+    case FAM_RES:
+      launch_inst<VT, XT, FAM_RES, true, false, false>(a, p, tiles, ntiles, grid, err, s);
       break;
     default:
       launch_inst<VT, XT, FAM_JAC, true, false, false>(a, p, tiles, ntiles, grid, err, s);

@@ -132,6 +132,31 @@ amgps_status amgps_estimate_lambda(amgps_ctx* ctx, int level, const double* v0_d
 amgps_status amgps_smooth(amgps_ctx* ctx, int level, amgps_kind kind, int degree,
                           const double* b_dev, double* x_dev, int x_is_zero);
 
+/* Reverse mode of one smoother application x = S(b, x0) on `level` (FP64
+ * hierarchies).  No passage of the paper defines it; it serves the learned
+ * weights.  Given gx = dL/dx returns gb = dL/db and gx0 = dL/dx0 (device,
+ * nullable) and, for the 4th-kind family (CHEB4, CHEB4_OPT, WEIGHTS),
+ * gweights[j] = dL/dbeta_{j+1} (host, `degree` doubles, nullable; zeros for
+ * other kinds).  x0_dev NULL means a zero start.  The smoother operator
+ * Q = q(M^{-1}A) M^{-1} is symmetric, so gb is one more smoother application
+ * (to gx, from zero) and gx0 = gx - A gb; the weight gradients are
+ * <gx, z_j> with the z recurrence recomputed from (b, x0), so no recurrence
+ * vector is stored.  The first backward call allocates the reverse-mode
+ * buffers of every level.  Synchronous when gweights is requested. */
+amgps_status amgps_smooth_backward(amgps_ctx* ctx, int level, amgps_kind kind, int degree,
+                                   const double* b_dev, const double* x0_dev,
+                                   const double* gx_dev, double* gb_dev, double* gx0_dev,
+                                   double* gweights);
+
+/* Reverse mode of one V-cycle z = B(beta) r with the smoothers set by
+ * amgps_set_smoother (FP64 hierarchies): recomputes the forward V-cycle from
+ * r (recording each level's post-smoother input), then returns gr = dL/dr
+ * (device, nullable) and, in gweights (host, nullable), dL/dbeta for every
+ * non-coarsest level l at gweights[16 l + j], j < that level's degree (zeros
+ * for kinds without weights).  Synchronous when gweights is requested. */
+amgps_status amgps_vcycle_backward(amgps_ctx* ctx, const double* r_dev, const double* gz_dev,
+                                   double* gr_dev, double* gweights);
+
 /* amgps_smooth without any device allocation, for callers that may not
  * allocate device memory at the point of the call (for example code running
  * under an allocator that owns all device memory, or a phase of a real-time

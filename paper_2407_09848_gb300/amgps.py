@@ -55,6 +55,10 @@ _SIGS = {
     "amgps_smooth_noalloc": ([C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int],
                              C.c_int),
     "amgps_vcycle": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "amgps_smooth_backward": ([C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "amgps_vcycle_backward": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+                              C.c_int),
     "amgps_pcg": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int),
                    C.POINTER(C.c_double)], C.c_int),
     "amgps_pcg_host": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int),
@@ -219,6 +223,31 @@ class Solver:
     def vcycle(self, r, z):
         n = self._n(0)
         self._check(lib().amgps_vcycle(self._h, _dptr(r, n, "r"), _dptr(z, n, "z")))
+
+    def smooth_backward(self, level, kind, degree, b, x0, gx, want_x0=True, want_weights=True):
+        """Reverse mode of one smoother application: (gb, gx0 or None, gweights or None)."""
+        import torch
+        n = self._n(level)
+        gb = torch.empty(n, dtype=torch.float64, device=gx.device)
+        gx0 = torch.empty_like(gb) if want_x0 else None
+        gw = np.zeros(degree) if want_weights else None
+        self._check(lib().amgps_smooth_backward(
+            self._h, level, KIND[kind], degree, _dptr(b, n, "b"),
+            None if x0 is None else _dptr(x0, n, "x0"), _dptr(gx, n, "gx"), _dptr(gb, n, "gb"),
+            None if gx0 is None else _dptr(gx0, n, "gx0"),
+            None if gw is None else gw.ctypes.data))
+        return gb, gx0, gw
+
+    def vcycle_backward(self, r, gz, want_r=True):
+        """Reverse mode of one V-cycle: (gr or None, [dL/dbeta_l] per non-coarsest level)."""
+        import torch
+        n = self._n(0)
+        gr = torch.empty(n, dtype=torch.float64, device=gz.device) if want_r else None
+        gw = np.zeros((max(self.n_levels - 1, 1), 16))
+        self._check(lib().amgps_vcycle_backward(self._h, _dptr(r, n, "r"), _dptr(gz, n, "gz"),
+                                                None if gr is None else _dptr(gr, n, "gr"),
+                                                gw.ctypes.data))
+        return gr, gw[: self.n_levels - 1]
 
     def pcg(self, b, x, rtol=1e-8, maxit=1000, raise_on_noconv=True):
         n = self._n(0)

@@ -126,6 +126,9 @@ void launch_aggregate(const int32_t* cptr, const int32_t* cidx, int64_t nc, cons
                       cudaStream_t s);
 template <class XT>
 void launch_prolong(int64_t n, const int32_t* agg, const XT* ec, XT* x, cudaStream_t s);
+// out = x + y
+template <class XT>
+void launch_add(int64_t n, const XT* x, const XT* y, XT* out, cudaStream_t s);
 template <class VT, class XT>
 void launch_l1diag(const DevMat<VT>& A, XT* dinv, cudaStream_t s);
 template <class A, class B>

@@ -45,6 +45,7 @@ struct Fail {
   } while (0)
 
 thread_local std::string g_err;
+constexpr int kDotSlots = 32 * 32;  // 32 levels x (16 post + 16 pre) weight-gradient dots
 
 struct Spec {
   int kind = AMGPS_CHEB4_OPT;
@@ -125,6 +126,9 @@ struct Level {
   int tma_grid = 0;
   int32_t* gen_slices = nullptr;
   int64_t ngen = 0;
+  // reverse-mode buffers (allocated on the first backward call)
+  void *bx2 = nullptr, *bgx = nullptr, *bgb = nullptr, *bt1 = nullptr, *bt2 = nullptr,
+       *bt3 = nullptr;
 };
 
 struct HostSell {
@@ -421,6 +425,9 @@ struct amgps_ctx {
   size_t h_stage_n = 0;
   double* dscal = nullptr;
   double* hscal = nullptr;
+  double* ddots = nullptr;      // dots of the weight gradients: [level][post 0..15 | pre 16..31]
+  double* hdots = nullptr;
+  bool bwd_ready = false;
   double* part = nullptr;
   unsigned* counters = nullptr;
   int red_grid = 0;
@@ -497,6 +504,7 @@ void free_hierarchy(amgps_ctx* c) {
   c->allocs.clear();
   c->lv.clear();
   c->loaded = false;
+  c->bwd_ready = false;
   c->pr = c->pp = c->pq = c->pz = c->stage_b = c->stage_x = nullptr;
 }
 
@@ -728,7 +736,8 @@ struct Engine {
     check_launch();
   }
 
-  static void vcycle_level(amgps_ctx* c, int l, const XT* b, XT* x) {
+  // record: keep each level's post-smoother input (for the reverse pass)
+  static void vcycle_level(amgps_ctx* c, int l, const XT* b, XT* x, bool record = false) {
     Level& L = c->lv[l];
     cudaStream_t s = c->stream;
     if (L.coarsest) {
@@ -756,15 +765,157 @@ struct Engine {
       launch_aggregate<XT>(L.cptr, L.cidx, L.nc, (const XT*)L.r, (XT*)C.b, s);
       ps.done();
     }
-    if (l + 1 == 1 && c->graph_ok && !capturing(c)) {
+    if (l + 1 == 1 && c->graph_ok && !record && !capturing(c)) {
       CK(cudaGraphLaunch(c->gexec, s));
       c->launch_adjust += c->graph_kernels;
     } else {
-      vcycle_level(c, l + 1, (const XT*)C.b, (XT*)C.x);
+      vcycle_level(c, l + 1, (const XT*)C.b, (XT*)C.x, record);
     }
     launch_prolong<XT>(L.n, L.agg, (const XT*)C.x, x, s);
+    if (record) CK(cudaMemcpyAsync(L.bx2, x, L.n * sizeof(XT), cudaMemcpyDeviceToDevice, s));
     smooth(c, l, cf, b, x, false);
     check_launch();
+  }
+
+  // ---- reverse mode (FP64 hierarchies) ----
+  // One application x = x0 + Q (b - A x0) has Q = q(M^{-1}A) M^{-1}, a symmetric
+  // operator, so dL/db = Q gx is one more application of the same smoother to
+  // gx from zero, and dL/dx0 = gx - A dL/db one residual step.  For the
+  // 4th-kind family x = x0 + sum_j beta_j z_j with z_j independent of beta, so
+  // dL/dbeta_j = <gx, z_j>: the z recurrence is recomputed from (b, x0) (no
+  // recurrence vector is stored) and each z_j is dotted with gx.
+
+  // <gx, z_j> for j = 1..k into ddots[slot0 + j - 1]
+  static void zdots(amgps_ctx* c, int l, const Coefs& cf, const XT* b, const XT* x0,
+                    const XT* gx, int slot0) {
+    Level& L = c->lv[l];
+    cudaStream_t s = c->stream;
+    const DevMat<VT> A = devmat<VT>(L);
+    const XT* md = (const XT*)L.dinv;
+    XT* r = (XT*)L.r;
+    XT* zc = (XT*)L.za;
+    XT* zn = (XT*)L.zb;
+    XT* xs = (XT*)L.xb;
+    const int64_t n = L.n;
+    const int k = cf.k;
+    RedWork rw = redwork(c, 5, n);
+    const XT* rin_next;
+    if (!x0) {
+      launch_first<XT>(FAM_CHEB4, n, b, md, r, zc, xs, XT(cf.c2[1]), XT(0), XT(1), s);
+      rin_next = b;
+    } else {
+      StepArgs<VT, XT> a;
+      a.A = A;
+      a.u = x0;
+      a.rin = b;
+      a.rout = r;
+      a.write_r = k > 1;
+      a.zout = zc;
+      a.xin = x0;
+      a.xout = xs;
+      a.dinv = md;
+      a.c2 = XT(cf.c2[1]);
+      a.beta = XT(0);
+      a.fam = FAM_CHEB4;
+      a.init = true;
+      run_step(c, L, a, s);
+      rin_next = r;
+    }
+    launch_dot(n, (const double*)gx, (const double*)zc, rw, c->ddots, slot0, false, s);
+    for (int j = 1; j < k; ++j) {
+      StepArgs<VT, XT> a;
+      a.A = A;
+      a.u = zc;
+      a.rin = rin_next;
+      a.rout = r;
+      a.write_r = (j < k - 1);
+      a.zown = zc;
+      a.zout = zn;
+      a.xin = xs;
+      a.xout = xs;
+      a.dinv = md;
+      a.c1 = XT(cf.c1[j + 1]);
+      a.c2 = XT(cf.c2[j + 1]);
+      a.beta = XT(0);
+      a.fam = FAM_CHEB4;
+      run_step(c, L, a, s);
+      launch_dot(n, (const double*)gx, (const double*)zn, rw, c->ddots, slot0 + j, false, s);
+      rin_next = r;
+      std::swap(zc, zn);
+    }
+    check_launch();
+  }
+
+  // gb = dL/db, gx0 = dL/dx0 (nullable), weight dots into ddots[slot0..] (slot0 < 0: none)
+  static void smooth_bwd(amgps_ctx* c, int l, const Coefs& cf, const XT* b, const XT* x0,
+                         const XT* gx, XT* gb, XT* gx0, int slot0) {
+    Level& L = c->lv[l];
+    smooth(c, l, cf, gx, gb, true);
+    if (gx0) {
+      StepArgs<VT, XT> a;
+      a.A = devmat<VT>(L);
+      a.u = gb;
+      a.rin = gx;
+      a.zout = gx0;
+      a.fam = FAM_RES;
+      a.init = true;
+      run_step(c, L, a, c->stream);
+    }
+    if (slot0 >= 0 && cf.fam == FAM_CHEB4) zdots(c, l, cf, b, x0, gx, slot0);
+    check_launch();
+  }
+
+  // reverse pass of vcycle_level (after a recorded forward): gbout = dL/db_l
+  static void vcycle_bwd(amgps_ctx* c, int l, const XT* bl, const XT* xbar, XT* gbout) {
+    Level& L = c->lv[l];
+    cudaStream_t s = c->stream;
+    if (L.coarsest) {
+      launch_coarse_gemv<XT>((int)L.n, L.ainv, xbar, gbout, s);  // A_c^{-1} is symmetric
+      check_launch();
+      return;
+    }
+    const Coefs cf = make_coefs(L.spec.kind, L.spec.k, L.spec.w, L.spec.rho);
+    Level& C = c->lv[l + 1];
+    XT* t1 = (XT*)L.bt1;
+    XT* t2 = (XT*)L.bt2;
+    XT* t3 = (XT*)L.bt3;
+    // post-smoother x = S(b, x2): t1 = dL/db (post part), t2 = dL/dx2
+    smooth_bwd(c, l, cf, bl, (const XT*)L.bx2, xbar, t1, t2, l * 32);
+    // x2 = x1 + P xc ; xc = V_{l+1}(P^T (b - A x1))
+    launch_aggregate<XT>(L.cptr, L.cidx, L.nc, t2, (XT*)C.bgx, s);
+    vcycle_bwd(c, l + 1, (const XT*)C.b, (const XT*)C.bgx, (XT*)C.bgb);
+    CK(cudaMemsetAsync(t3, 0, L.n * sizeof(XT), s));
+    launch_prolong<XT>(L.n, L.agg, (const XT*)C.bgb, t3, s);  // dL/dres = P dL/db_c
+    launch_add<XT>(L.n, t1, t3, gbout, s);
+    {
+      StepArgs<VT, XT> a;  // dL/dx1 = dL/dx2 - A dL/dres  -> t1
+      a.A = devmat<VT>(L);
+      a.u = t3;
+      a.rin = t2;
+      a.zout = t1;
+      a.fam = FAM_RES;
+      a.init = true;
+      run_step(c, L, a, s);
+    }
+    // pre-smoother x1 = S(b, 0)
+    smooth_bwd(c, l, cf, bl, nullptr, t1, t2, nullptr, l * 32 + 16);
+    launch_add<XT>(L.n, gbout, t2, gbout, s);
+    check_launch();
+  }
+
+  static void ensure_bwd(amgps_ctx* c) {
+    if (c->bwd_ready) return;
+    for (auto& L : c->lv) {
+      const size_t bytes = L.n * sizeof(XT);
+      L.bgx = dalloc(c, bytes);
+      L.bgb = dalloc(c, bytes);
+      if (L.coarsest) continue;
+      L.bx2 = dalloc(c, bytes);
+      L.bt1 = dalloc(c, bytes);
+      L.bt2 = dalloc(c, bytes);
+      L.bt3 = dalloc(c, bytes);
+    }
+    c->bwd_ready = true;
   }
 
   static bool capturing(amgps_ctx* c) {
@@ -1008,6 +1159,8 @@ amgps_status amgps_create(amgps_ctx** out, int device, void* user_stream) {
     CK(cudaMalloc(&u->dscal, S_COUNT * sizeof(double)));
     CK(cudaMemset(u->dscal, 0, S_COUNT * sizeof(double)));
     CK(cudaMallocHost(&u->hscal, S_COUNT * sizeof(double)));
+    CK(cudaMalloc(&u->ddots, kDotSlots * sizeof(double)));
+    CK(cudaMallocHost(&u->hdots, kDotSlots * sizeof(double)));
     const int maxgrid = u->nsm * 4;
     CK(cudaMalloc(&u->part, (size_t)maxgrid * sizeof(double)));
     CK(cudaMalloc(&u->counters, 8 * sizeof(unsigned)));
@@ -1029,6 +1182,8 @@ amgps_status amgps_destroy(amgps_ctx* c) {
   for (auto e : c->pool) cudaEventDestroy(e);
   if (c->h_stage) cudaFreeHost(c->h_stage);
   if (c->hscal) cudaFreeHost(c->hscal);
+  if (c->hdots) cudaFreeHost(c->hdots);
+  if (c->ddots) cudaFree(c->ddots);
   if (c->dscal) cudaFree(c->dscal);
   if (c->part) cudaFree(c->part);
   if (c->counters) cudaFree(c->counters);
@@ -1288,6 +1443,77 @@ amgps_status amgps_smooth_noalloc(amgps_ctx* c, int level, amgps_kind kind, int 
     with_engine(c, [&](auto eng) {
       decltype(eng)::smooth_public(c, level, cf, b, x, x_is_zero != 0);
     });
+    leave(c);
+  });
+}
+
+amgps_status amgps_smooth_backward(amgps_ctx* c, int level, amgps_kind kind, int degree,
+                                   const double* b, const double* x0, const double* gx, double* gb,
+                                   double* gx0, double* gweights) {
+  return guard(c, [&] {
+    need_loaded(c);
+    check_kind_degree(kind, degree);
+    REQ(c->prec == AMGPS_F64, AMGPS_E_ARG, "the backward pass needs an FP64 hierarchy");
+    REQ(level >= 0 && level < (int)c->lv.size() - 1, AMGPS_E_ARG,
+        "level out of range (the coarsest level has no smoother)");
+    REQ(b && gx, AMGPS_E_ARG, "null b or gx");
+    const Spec& sp = c->lv[level].spec;
+    REQ(kind != AMGPS_WEIGHTS || (sp.kind == AMGPS_WEIGHTS && sp.k == degree), AMGPS_E_STATE,
+        "AMGPS_WEIGHTS: set the level's weights of this degree first");
+    const Coefs cf = make_coefs(kind, degree, sp.w, sp.rho);
+    using E = Engine<double, double>;
+    enter(c);
+    E::ensure_bwd(c);
+    Level& L = c->lv[level];
+    double* gbuf = gb ? gb : (double*)L.bgb;
+    const bool want_w = gweights && cf.fam == FAM_CHEB4;
+    E::smooth_bwd(c, level, cf, b, x0, gx, gbuf, gx0, want_w ? 0 : -1);
+    if (gweights) {
+      std::fill(gweights, gweights + degree, 0.0);
+      if (want_w) {
+        CK(cudaMemcpyAsync(c->hdots, c->ddots, degree * sizeof(double), cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        std::copy(c->hdots, c->hdots + degree, gweights);
+      }
+    }
+    leave(c);
+  });
+}
+
+amgps_status amgps_vcycle_backward(amgps_ctx* c, const double* r, const double* gz, double* gr,
+                                   double* gweights) {
+  return guard(c, [&] {
+    need_loaded(c);
+    REQ(c->prec == AMGPS_F64, AMGPS_E_ARG, "the backward pass needs an FP64 hierarchy");
+    REQ(r && gz, AMGPS_E_ARG, "null r or gz");
+    REQ(c->lv.size() <= 32, AMGPS_E_ARG, "too many levels");
+    using E = Engine<double, double>;
+    enter(c);
+    E::ensure_bwd(c);
+    Level& L0 = c->lv[0];
+    if (L0.coarsest) {
+      launch_coarse_gemv<double>((int)L0.n, L0.ainv, gz, gr ? gr : (double*)L0.bgb, c->stream);
+      check_launch();
+    } else {
+      E::vcycle_level(c, 0, r, (double*)L0.x, true);  // forward, recording each level's x2
+      E::vcycle_bwd(c, 0, r, gz, gr ? gr : (double*)L0.bgb);
+    }
+    if (gweights) {
+      const int nl = (int)c->lv.size();
+      CK(cudaMemcpyAsync(c->hdots, c->ddots, kDotSlots * sizeof(double), cudaMemcpyDeviceToHost,
+                         c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      for (int l = 0; l < nl - 1; ++l) {
+        const Spec& sp = c->lv[l].spec;
+        const Coefs cf = make_coefs(sp.kind, sp.k, sp.w, sp.rho);
+        for (int j = 0; j < kMaxDegree; ++j)
+          gweights[l * kMaxDegree + j] =
+              (cf.fam == FAM_CHEB4 && j < sp.k)
+                  ? c->hdots[l * 32 + j] + c->hdots[l * 32 + 16 + j]
+                  : 0.0;
+      }
+    }
     leave(c);
   });
 }

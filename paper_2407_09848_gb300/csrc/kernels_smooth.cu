@@ -171,6 +171,20 @@ void launch_prolong(int64_t n, const int32_t* agg, const XT* ec, XT* x, cudaStre
   count_launch();
 }
 
+template <class XT>
+__global__ void __launch_bounds__(kBlock) k_add(int64_t n, const XT* __restrict__ x,
+                                                const XT* __restrict__ y, XT* out) {
+  const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (i < n) out[i] = x[i] + y[i];
+}
+
+template <class XT>
+void launch_add(int64_t n, const XT* x, const XT* y, XT* out, cudaStream_t s) {
+  if (n == 0) return;
+  k_add<XT><<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, x, y, out);
+  count_launch();
+}
+
 // 1/M_i with M_i of Eq. l1smooth (a_ii + sum_{j != i} |a_ij|), formed once per level.
 template <class VT, class XT>
 __global__ void __launch_bounds__(kBlock) k_l1diag(const DevMat<VT> A, XT* __restrict__ dinv) {
@@ -235,6 +249,7 @@ template void launch_aggregate<double>(const int32_t*, const int32_t*, int64_t, 
 template void launch_aggregate<float>(const int32_t*, const int32_t*, int64_t, const float*, float*,
                                       cudaStream_t);
 template void launch_prolong<double>(int64_t, const int32_t*, const double*, double*, cudaStream_t);
+template void launch_add<double>(int64_t, const double*, const double*, double*, cudaStream_t);
 template void launch_prolong<float>(int64_t, const int32_t*, const float*, float*, cudaStream_t);
 template void launch_convert<double, float>(int64_t, const double*, float*, cudaStream_t);
 template void launch_convert<float, double>(int64_t, const float*, double*, cudaStream_t);

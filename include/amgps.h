@@ -157,6 +157,36 @@ amgps_status amgps_smooth_backward(amgps_ctx* ctx, int level, amgps_kind kind, i
 amgps_status amgps_vcycle_backward(amgps_ctx* ctx, const double* r_dev, const double* gz_dev,
                                    double* gr_dev, double* gweights);
 
+/* Mean A-norm error reduction of one V-cycle over m error vectors and its
+ * gradient in every level's weights (the training loss of the learned
+ * weights; no passage of the paper defines it):
+ *   loss = (1/m) sum_i ||(I - B A) e_i||_A^2 / ||e_i||_A^2,
+ * E0_dev holds e_0..e_{m-1} (m x n_0 doubles, vector i at E0_dev + i n_0),
+ * m <= 4096, FP64 hierarchies.  *loss (host) and gweights (host, nullable,
+ * 16 per non-coarsest level as in amgps_vcycle_backward).  Every product,
+ * V-cycle, reverse pass and dot runs in the library's kernels.  Synchronous. */
+amgps_status amgps_vcycle_loss_grad(amgps_ctx* ctx, const double* E0_dev, int m, double* loss,
+                                    double* gweights);
+
+/* The weight-predicting MLP of the learned smoother (not in the paper):
+ * 8 level features -> 64 -> 64 -> 4, ReLU, beta = beta_ref exp(0.5 tanh(o)).
+ * Stateless FP32 kernels on caller-owned device buffers, enqueued on `stream`
+ * (cudaStream_t, may be NULL); errors through amgps_last_error(NULL).
+ * params: 4996 floats [W1 (64x8 row-major), b1 (64), W2 (64x64), b2, W3 (4x64),
+ * b3 (4)]; feats: batch x 8; beta_ref: 4; beta: batch x 4; acts: batch x 132
+ * (saved by forward for backward); work: batch x 132 scratch; grads: 4996
+ * (overwritten with dL/dparams for the given gbeta = dL/dbeta, batch x 4);
+ * Adam: step counts from 1, m and v are 4996-float moment buffers. */
+amgps_status amgps_mlp_forward(const float* params_dev, const float* feats_dev, int batch,
+                               const float* beta_ref_dev, float* beta_dev, float* acts_dev,
+                               void* stream);
+amgps_status amgps_mlp_backward(const float* params_dev, const float* feats_dev,
+                                const float* acts_dev, const float* beta_dev, int batch,
+                                const float* gbeta_dev, float* work_dev, float* grads_dev,
+                                void* stream);
+amgps_status amgps_mlp_adam(float* params_dev, const float* grads_dev, float* m_dev, float* v_dev,
+                            int step, float lr, float beta1, float beta2, float eps, void* stream);
+
 /* amgps_smooth without any device allocation, for callers that may not
  * allocate device memory at the point of the call (for example code running
  * under an allocator that owns all device memory, or a phase of a real-time

@@ -64,6 +64,14 @@ _SIGS = {
     "amgps_pcg_host": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int),
                         C.POINTER(C.c_double)], C.c_int),
     "amgps_synchronize": ([C.c_void_p], C.c_int),
+    "amgps_vcycle_loss_grad": ([C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p],
+                               C.c_int),
+    "amgps_mlp_forward": ([C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                           C.c_void_p], C.c_int),
+    "amgps_mlp_backward": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                            C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "amgps_mlp_adam": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_float, C.c_float,
+                        C.c_float, C.c_float, C.c_void_p], C.c_int),
     "amgps_opt4_weights": ([C.c_int, C.c_void_p], C.c_int),
     "amgps_cheb1_astar": ([C.c_int, C.POINTER(C.c_double)], C.c_int),
     "amgps_profile_enable": ([C.c_void_p, C.c_int], C.c_int),
@@ -112,6 +120,46 @@ def cheb1_astar(k):
     if st:
         raise AmgpsError(st, "bad degree")
     return a.value
+
+
+def _fptr(t, n, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+            and t.is_contiguous() and t.numel() == n):
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor of {n} entries")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _raise_global(st):
+    if st:
+        raise AmgpsError(st, lib().amgps_last_error(None).decode())
+
+
+def mlp_forward(params, feats, beta_ref, beta, acts):
+    """Library MLP forward (FP32 device tensors; see amgps_mlp_forward)."""
+    B = feats.numel() // 8
+    _raise_global(lib().amgps_mlp_forward(
+        _fptr(params, 4996, "params"), _fptr(feats, B * 8, "feats"), B, _fptr(beta_ref, 4, "beta_ref"),
+        _fptr(beta, B * 4, "beta"), _fptr(acts, B * 132, "acts"), _stream()))
+
+
+def mlp_backward(params, feats, acts, beta, gbeta, work, grads):
+    B = feats.numel() // 8
+    _raise_global(lib().amgps_mlp_backward(
+        _fptr(params, 4996, "params"), _fptr(feats, B * 8, "feats"), _fptr(acts, B * 132, "acts"),
+        _fptr(beta, B * 4, "beta"), B, _fptr(gbeta, B * 4, "gbeta"), _fptr(work, B * 132, "work"),
+        _fptr(grads, 4996, "grads"), _stream()))
+
+
+def mlp_adam(params, grads, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
+    _raise_global(lib().amgps_mlp_adam(
+        _fptr(params, 4996, "params"), _fptr(grads, 4996, "grads"), _fptr(m, 4996, "m"),
+        _fptr(v, 4996, "v"), int(step), float(lr), float(b1), float(b2), float(eps), _stream()))
 
 
 def tma_plan_stats(A, prec="f64"):
@@ -248,6 +296,16 @@ class Solver:
                                                 None if gr is None else _dptr(gr, n, "gr"),
                                                 gw.ctypes.data))
         return gr, gw[: self.n_levels - 1]
+
+    def loss_grad(self, E0):
+        """Mean A-norm error reduction of one V-cycle over the rows of E0
+        (m x n_0 CUDA float64) and its weight gradient: (loss, (levels-1, 16))."""
+        m = E0.shape[0]
+        loss = C.c_double()
+        gw = np.zeros((max(self.n_levels - 1, 1), 16))
+        self._check(lib().amgps_vcycle_loss_grad(self._h, _dptr(E0, m * self._n(0), "E0"), m,
+                                                 C.byref(loss), gw.ctypes.data))
+        return loss.value, gw[: self.n_levels - 1]
 
     def pcg(self, b, x, rtol=1e-8, maxit=1000, raise_on_noconv=True):
         n = self._n(0)

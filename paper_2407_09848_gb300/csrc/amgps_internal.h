@@ -126,9 +126,22 @@ void launch_aggregate(const int32_t* cptr, const int32_t* cidx, int64_t nc, cons
                       cudaStream_t s);
 template <class XT>
 void launch_prolong(int64_t n, const int32_t* agg, const XT* ec, XT* x, cudaStream_t s);
-// out = x + y
+// out = x + y ; out = x - y ; out = (factor / *s_dev) * x
 template <class XT>
 void launch_add(int64_t n, const XT* x, const XT* y, XT* out, cudaStream_t s);
+void launch_sub(int64_t n, const double* x, const double* y, double* out, cudaStream_t s);
+void launch_scale_dev(int64_t n, const double* x, double* out, const double* s_dev, double factor,
+                      cudaStream_t s);
+
+// ---- weight-predicting MLP (kernels_mlp.cu) ----
+constexpr int kMlpParams = 4996;
+constexpr int kMlpActs = 132;
+void mlp_forward(const float* th, const float* F, int batch, const float* ref, float* beta,
+                 float* acts, cudaStream_t s);
+void mlp_backward(const float* th, const float* F, const float* acts, const float* beta,
+                  int batch, const float* gbeta, float* work, float* grads, cudaStream_t s);
+void mlp_adam(float* th, const float* g, float* m, float* v, int step, float lr, float b1,
+              float b2, float eps, cudaStream_t s);
 template <class VT, class XT>
 void launch_l1diag(const DevMat<VT>& A, XT* dinv, cudaStream_t s);
 template <class A, class B>

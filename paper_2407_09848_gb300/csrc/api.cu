@@ -46,6 +46,7 @@ struct Fail {
 
 thread_local std::string g_err;
 constexpr int kDotSlots = 32 * 32;  // 32 levels x (16 post + 16 pre) weight-gradient dots
+constexpr int kMaxLossVectors = 4096;
 
 struct Spec {
   int kind = AMGPS_CHEB4_OPT;
@@ -426,6 +427,8 @@ struct amgps_ctx {
   double* dscal = nullptr;
   double* hscal = nullptr;
   double* ddots = nullptr;      // dots of the weight gradients: [level][post 0..15 | pre 16..31]
+  double* dacc = nullptr;       // their sum over the error vectors of a loss evaluation
+  double* dloss = nullptr;      // per error vector: <e0, A e0>, <e1, A e1>
   double* hdots = nullptr;
   bool bwd_ready = false;
   double* part = nullptr;
@@ -905,6 +908,8 @@ struct Engine {
 
   static void ensure_bwd(amgps_ctx* c) {
     if (c->bwd_ready) return;
+    c->dacc = (double*)dalloc(c, kDotSlots * sizeof(double));
+    c->dloss = (double*)dalloc(c, 2 * kMaxLossVectors * sizeof(double));
     for (auto& L : c->lv) {
       const size_t bytes = L.n * sizeof(XT);
       L.bgx = dalloc(c, bytes);
@@ -1515,6 +1520,95 @@ amgps_status amgps_vcycle_backward(amgps_ctx* c, const double* r, const double* 
       }
     }
     leave(c);
+  });
+}
+
+amgps_status amgps_vcycle_loss_grad(amgps_ctx* c, const double* E0, int m, double* loss,
+                                    double* gweights) {
+  return guard(c, [&] {
+    need_loaded(c);
+    REQ(c->prec == AMGPS_F64, AMGPS_E_ARG, "the loss gradient needs an FP64 hierarchy");
+    REQ(E0 && loss && m >= 1 && m <= kMaxLossVectors, AMGPS_E_ARG,
+        "null arguments or m outside 1..4096");
+    REQ(c->lv.size() >= 2 && c->lv.size() <= 32, AMGPS_E_ARG, "needs 2..32 levels");
+    using E = Engine<double, double>;
+    enter(c);
+    E::ensure_bwd(c);
+    cudaStream_t s = c->stream;
+    Level& L0 = c->lv[0];
+    const int64_t n = L0.n;
+    const DevMat<double> A = devmat64(L0, c->prec);
+    RedWork rw = redwork(c, 1, n);
+    rw.grid = reduction_grid(L0.nslices * kSlice, c->nsm);
+    double *r = c->pp, *z = c->pz, *e1 = c->pr, *q1 = c->pq, *gz = c->stage_x;
+    CK(cudaMemsetAsync(c->dacc, 0, kDotSlots * sizeof(double), s));
+    for (int i = 0; i < m; ++i) {
+      const double* e0 = E0 + (size_t)i * n;
+      launch_spmv_dot(A, e0, r, rw, c->dscal, s);  // r = A e0, <e0, A e0>
+      CK(cudaMemcpyAsync(c->dloss + 2 * i, c->dscal + S_PQ, sizeof(double),
+                         cudaMemcpyDeviceToDevice, s));
+      E::vcycle_level(c, 0, r, z, true);            // z = B r, recorded
+      launch_sub(n, e0, z, e1, s);                  // e1 = (I - B A) e0
+      launch_spmv_dot(A, e1, q1, rw, c->dscal, s);  // A e1, <e1, A e1>
+      CK(cudaMemcpyAsync(c->dloss + 2 * i + 1, c->dscal + S_PQ, sizeof(double),
+                         cudaMemcpyDeviceToDevice, s));
+      launch_scale_dev(n, q1, gz, c->dloss + 2 * i, -2.0 / m, s);  // dL/dz
+      E::vcycle_bwd(c, 0, r, gz, (double*)L0.bgb);
+      launch_add<double>(kDotSlots, c->dacc, c->ddots, c->dacc, s);
+      check_launch();
+    }
+    std::vector<double> hl(2 * (size_t)m);
+    CK(cudaMemcpyAsync(hl.data(), c->dloss, 2 * m * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->hdots, c->dacc, kDotSlots * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double acc = 0.0;
+    for (int i = 0; i < m; ++i) acc += hl[2 * i + 1] / hl[2 * i] / m;
+    *loss = acc;
+    if (gweights) {
+      const int nl = (int)c->lv.size();
+      for (int l = 0; l < nl - 1; ++l) {
+        const Spec& sp = c->lv[l].spec;
+        const Coefs cf = make_coefs(sp.kind, sp.k, sp.w, sp.rho);
+        for (int j = 0; j < kMaxDegree; ++j)
+          gweights[l * kMaxDegree + j] =
+              (cf.fam == FAM_CHEB4 && j < sp.k)
+                  ? c->hdots[l * 32 + j] + c->hdots[l * 32 + 16 + j]
+                  : 0.0;
+      }
+    }
+    leave(c);
+  });
+}
+
+amgps_status amgps_mlp_forward(const float* params, const float* feats, int batch,
+                               const float* beta_ref, float* beta, float* acts, void* stream) {
+  return guard(nullptr, [&] {
+    REQ(params && feats && beta_ref && beta && acts, AMGPS_E_ARG, "null argument");
+    REQ(batch >= 1 && batch <= 65535, AMGPS_E_ARG, "batch outside 1..65535");
+    mlp_forward(params, feats, batch, beta_ref, beta, acts, (cudaStream_t)stream);
+    check_launch();
+  });
+}
+
+amgps_status amgps_mlp_backward(const float* params, const float* feats, const float* acts,
+                                const float* beta, int batch, const float* gbeta, float* work,
+                                float* grads, void* stream) {
+  return guard(nullptr, [&] {
+    REQ(params && feats && acts && beta && gbeta && work && grads, AMGPS_E_ARG,
+        "null argument");
+    REQ(batch >= 1 && batch <= 65535, AMGPS_E_ARG, "batch outside 1..65535");
+    mlp_backward(params, feats, acts, beta, batch, gbeta, work, grads, (cudaStream_t)stream);
+    check_launch();
+  });
+}
+
+amgps_status amgps_mlp_adam(float* params, const float* grads, float* m, float* v, int step,
+                            float lr, float beta1, float beta2, float eps, void* stream) {
+  return guard(nullptr, [&] {
+    REQ(params && grads && m && v, AMGPS_E_ARG, "null argument");
+    REQ(step >= 1, AMGPS_E_ARG, "Adam steps count from 1");
+    mlp_adam(params, grads, m, v, step, lr, beta1, beta2, eps, (cudaStream_t)stream);
+    check_launch();
   });
 }
 

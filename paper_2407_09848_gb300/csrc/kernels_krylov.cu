@@ -112,6 +112,35 @@ void launch_xpay(int64_t n, const double* z, double* p, const double* scal, cuda
   count_launch();
 }
 
+__global__ void __launch_bounds__(kBlock) k_sub(int64_t n, const double* __restrict__ x,
+                                                const double* __restrict__ y,
+                                                double* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (i < n) out[i] = x[i] - y[i];
+}
+
+void launch_sub(int64_t n, const double* x, const double* y, double* out, cudaStream_t s) {
+  if (n == 0) return;
+  k_sub<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, x, y, out);
+  count_launch();
+}
+
+__global__ void __launch_bounds__(kBlock) k_scale_dev(int64_t n, const double* __restrict__ x,
+                                                      double* __restrict__ out,
+                                                      const double* __restrict__ sd,
+                                                      double factor) {
+  const double f = factor / sd[0];
+  const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (i < n) out[i] = f * x[i];
+}
+
+void launch_scale_dev(int64_t n, const double* x, double* out, const double* s_dev, double factor,
+                      cudaStream_t s) {
+  if (n == 0) return;
+  k_scale_dev<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, x, out, s_dev, factor);
+  count_launch();
+}
+
 // Coarsest level: x = A_c^{-1} b with the inverse formed at load time from the
 // Cholesky factor (FP64).  One warp per row, lanes stride the columns.
 template <class XT>

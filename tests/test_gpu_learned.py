@@ -1,0 +1,113 @@
+"""The learned weights on the GPU: the MLP kernels against the FP64 oracle MLP,
+the V-cycle loss gradient against the oracle's reverse mode, checkpointing,
+the safety fallback, and what a trained network gains over the optimal
+4th-kind weights on held-out problems."""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+from oracle.adjoint import error_reduction_loss
+from oracle.amg import OracleAMG
+from oracle.smoother import SmootherSpec
+from paper_2407_09848_gb300 import problems as pr
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_09848_gb300 import build
+    build.build()
+    return torch
+
+
+def test_mlp_kernels_match_oracle(torch_cuda):
+    torch = torch_cuda
+    from paper_2407_09848_gb300 import amgps
+    rng = np.random.default_rng(0)
+    th = (rng.standard_normal(4996) * 0.3).astype(np.float32)
+    B = 37
+    F = rng.standard_normal((B, 8)).astype(np.float32)
+    ref = amgps.opt4_weights(4).astype(np.float32)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a).ravel()).cuda()
+    tp, Fd, rd = d(th), d(F), d(ref)
+    beta = torch.empty(B * 4, dtype=torch.float32, device="cuda")
+    acts = torch.empty(B * 132, dtype=torch.float32, device="cuda")
+    amgps.mlp_forward(tp, Fd, rd, beta, acts)
+    ob, cache = omlp.forward(th.astype(np.float64), F.astype(np.float64), ref.astype(np.float64))
+    gb = beta.cpu().numpy().reshape(B, 4)
+    assert np.max(np.abs(gb - ob)) <= 1e-5 * np.max(np.abs(ob))
+    G = rng.standard_normal((B, 4)).astype(np.float32)
+    grads = torch.empty(4996, dtype=torch.float32, device="cuda")
+    work = torch.empty(B * 132, dtype=torch.float32, device="cuda")
+    amgps.mlp_backward(tp, Fd, acts, beta, d(G), work, grads)
+    og = omlp.backward(th.astype(np.float64), cache, G.astype(np.float64))
+    gg = grads.cpu().numpy()
+    assert np.linalg.norm(gg - og) <= 1e-5 * np.linalg.norm(og)
+    m = torch.zeros(4996, dtype=torch.float32, device="cuda")
+    v = torch.zeros_like(m)
+    amgps.mlp_adam(tp, grads, m, v, 1, 1e-3)
+    onew, _, _ = omlp.adam(th.astype(np.float64), gg.astype(np.float64), np.zeros(4996),
+                           np.zeros(4996), 1, 1e-3)
+    assert np.max(np.abs(tp.cpu().numpy() - onew)) <= 1e-6
+
+
+def test_loss_grad_matches_oracle(torch_cuda):
+    torch = torch_cuda
+    from paper_2407_09848_gb300.amgps import Solver
+    H = pr.build_hierarchy(pr.varcoef(14, 1.2, 3.0, seed=3, ny=12, nz=10), coarse_max=30)
+    S = Solver().load(H.A, H.P)
+    rng = np.random.default_rng(4)
+    specs = []
+    for l in range(H.n_levels - 1):
+        b = 1 + 0.2 * rng.uniform(-1, 1, 4)
+        S.set_smoother(l, "weights", 4, weights=b)
+        specs.append(SmootherSpec("weights", 4, beta=b))
+    E0 = rng.standard_normal((5, H.A[0].shape[0]))
+    loss, gw = S.loss_grad(torch.from_numpy(E0).cuda())
+    oloss, og = error_reduction_loss(OracleAMG(H.A, H.P, specs), E0.T)
+    assert abs(loss - oloss) <= 1e-11 * oloss
+    for l in range(H.n_levels - 1):
+        assert np.max(np.abs(gw[l, :4] - og[l])) <= 1e-10 * np.max(np.abs(og[l]))
+
+
+def test_safety_fallback_and_checkpoint(torch_cuda, tmp_path):
+    from paper_2407_09848_gb300 import amgps, learn
+    assert learn.is_safe(amgps.opt4_weights(4))
+    assert not learn.is_safe(np.array([3.0, 3.0, 3.0, 3.0]))
+    H = pr.build_hierarchy(pr.varcoef(12, 1.0, 3.0, seed=5), coarse_max=30)
+    p = learn.Problem(H, nvec=4, seed=1)
+    ref = amgps.opt4_weights(4)
+    nl = H.n_levels - 1
+    l_ref, _ = p.loss_grad([ref] * nl)
+    l_bad, g_bad = p.loss_grad([np.array([3.0, 3.0, 3.0, 3.0])] * nl)
+    assert l_bad == l_ref and np.all(g_bad == 0)   # unsafe weights fall back
+    net = learn.WeightMLP(seed=1)
+    probs = [p, learn.Problem(pr.build_hierarchy(pr.varcoef(12, 1.5, 4.0, seed=6), coarse_max=30),
+                              nvec=4, seed=2)]
+    learn.train(net, probs, 3, batch=2, lr=1e-3)
+    net.save(tmp_path / "ckpt.npz")
+    net2 = learn.WeightMLP(seed=99).load(tmp_path / "ckpt.npz")
+    learn.train(net, probs, 1, batch=2, lr=1e-3, seed=5)
+    learn.train(net2, probs, 1, batch=2, lr=1e-3, seed=5)
+    assert np.array_equal(net.params.cpu().numpy(), net2.params.cpu().numpy())
+
+
+def test_trained_network_gain_over_optimal_weights(torch_cuda):
+    # train on 12 log-normal 24^3 problems, evaluate on 6 held-out ones
+    from paper_2407_09848_gb300 import learn
+    train_set = learn.make_training_set(12, 24, seed0=0, nvec=8)
+    test_set = learn.make_training_set(6, 24, seed0=5000, nvec=8)
+    net = learn.WeightMLP(seed=0)
+    before_learned, ref = learn.evaluate(net, test_set)
+    assert abs(before_learned - ref) <= 1e-6 * ref   # untrained network = optimal weights
+    hist = learn.train(net, train_set, 60, batch=12, lr=5e-3)
+    after, _ = learn.evaluate(net, test_set)
+    gain = 1.0 - after / ref
+    print(f"held-out V-cycle error reduction: optimal weights {ref:.5f}, learned {after:.5f} "
+          f"(gain {100 * gain:.2f}%); training loss {hist[0]:.5f} -> {hist[-1]:.5f}")
+    assert hist[-1] < hist[0]
+    assert after < ref

@@ -39,7 +39,9 @@ METRIC = "PCG-AMG time-to-1e-8 and smoother HBM GB/s: plain FP64 vs learned/mixe
 GOLDEN_ITERS = os.path.join(ROOT, "tests", "golden", "oracle_pcg_iterations.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_poisson256_traffic.json")
 STEP_SOURCES = [os.path.join(ROOT, "paper_2407_09848_gb300", "csrc", f)
-                for f in ("kernels_smooth.cu", "kernels_common.cuh", "amgps_internal.h")]
+                for f in ("kernels_tma.cu", "kernels_smooth.cu", "kernels_common.cuh",
+                          "amgps_internal.h")]
+LEARNED = os.path.join(ROOT, "paper_2407_09848_gb300", "data", "learned_weights_lognormal64.npz")
 
 
 def parse():
@@ -55,6 +57,8 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the mixed-precision (192^3) and learned+mixed (256^3) comparisons")
     return ap.parse_args()
 
 
@@ -207,6 +211,87 @@ def time_oracle_iteration(H, b, kind, degree):
     return time.perf_counter() - t, ora
 
 
+def timed_solve(S, bd, x, rtol, torch, reps=2):
+    """(iterations, ms, relres) of one PCG solve, best of `reps` after one warm-up."""
+    S.pcg(bd, x, rtol=rtol, maxit=2000)
+    best = None
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        it, rel = S.pcg(bd, x, rtol=rtol, maxit=2000)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return it, best, rel
+
+
+def run_mixed_c2(a, torch):
+    """192^3 variable coefficient (k = exp(g), GRF sigma 1, ell 8): FP64 vs
+    FP32 / BF16 values on the smoother and transfer path (CHEB4_OPT k = 4)."""
+    import numpy as np
+    from paper_2407_09848_gb300 import problems as pr
+    from paper_2407_09848_gb300.amgps import Solver
+    H = pr.build_hierarchy(pr.varcoef(192, 1.0, 8.0, seed=0), coarse_max=512)
+    b = pr.rhs_uniform(H.levels[0].A.shape[0], seed=0)
+    bd = torch.from_numpy(b).cuda()
+    out, ref = {}, None
+    for prec in ("f64", "f32", "bf16"):
+        S = Solver().load(H.A, H.P, prec=prec)
+        x = torch.empty_like(bd)
+        it, ms, rel = timed_solve(S, bd, x, a.rtol, torch)
+        xs = x.cpu().numpy()
+        true = float(np.linalg.norm(b - H.levels[0].A @ xs) / np.linalg.norm(b))
+        if ref is None:
+            ref = xs
+        out[prec] = {"iterations": it, "ms": round(ms, 3), "relres": rel, "true_relres": true,
+                     "solution_rel_diff_vs_f64": float(np.linalg.norm(xs - ref) / np.linalg.norm(ref))}
+        S.close()
+    return {"workload": "varcoef192^3 sigma1 ell8, CHEB4_OPT k4, rtol 1e-8", **out}
+
+
+def run_learned_c4(a, torch):
+    """256^3 log-normal (sigma 2, ell 16) and anisotropic (eps 1e-3 in z):
+    plain FP64 with the optimal 4th-kind weights vs learned weights with
+    BF16 / FP32 values (FP64 PCG and coarse solve)."""
+    import numpy as np
+    from paper_2407_09848_gb300 import learn
+    from paper_2407_09848_gb300 import problems as pr
+    from paper_2407_09848_gb300.amgps import Solver
+    if not os.path.exists(LEARNED):
+        return {"unavailable": "no trained weights file"}
+    net = learn.WeightMLP(seed=0).load(LEARNED)
+    res = {"workload": "256^3, PCG to 1e-8; learned = MLP trained on 512 log-normal 64^3 problems"}
+    for name, st in (("lognormal_s2_l16", pr.varcoef(256, 2.0, 16.0, seed=0)),
+                     ("aniso_eps1e-3", pr.aniso(256, 1e-3))):
+        H = pr.build_hierarchy(st, coarse_max=512)
+        b = pr.rhs_uniform(H.levels[0].A.shape[0], seed=0)
+        bd = torch.from_numpy(b).cuda()
+        S64 = Solver().load(H.A, H.P, prec="f64")
+        feats = learn.level_features(S64, H)
+        betas = net.predict(feats)
+        safe = [learn.is_safe(bb) for bb in betas]
+        x = torch.empty_like(bd)
+        row = {"learned_weights": [list(map(float, bb)) for bb in betas], "safe": safe}
+        it, ms, rel = timed_solve(S64, bd, x, a.rtol, torch)
+        row["f64_opt"] = {"iterations": it, "ms": round(ms, 3), "relres": rel}
+        S64.close()
+        for prec in ("bf16", "f32"):
+            S = Solver().load(H.A, H.P, prec=prec)
+            it, ms, rel = timed_solve(S, bd, x, a.rtol, torch)
+            row[f"{prec}_opt"] = {"iterations": it, "ms": round(ms, 3), "relres": rel}
+            ref = learn.amgps.opt4_weights(4)
+            for l, bb in enumerate(betas):
+                S.set_smoother(l, "weights", 4, weights=bb if safe[l] else ref)
+            it, ms, rel = timed_solve(S, bd, x, a.rtol, torch)
+            row[f"{prec}_learned"] = {"iterations": it, "ms": round(ms, 3), "relres": rel}
+            S.close()
+        row["speedup_bf16_learned_vs_f64_opt"] = round(row["f64_opt"]["ms"] / row["bf16_learned"]["ms"], 3)
+        res[name] = row
+    return res
+
+
 def run_reference(a):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -344,6 +429,12 @@ def run_ours(a):
                               "oracle_iterations": golden_iterations(a.grid, kind, k)})
         configure(S, H, a.kind, a.degree, torch)
 
+    # ---- comparisons: mixed precision (192^3) and learned + mixed (256^3) ----
+    extras = None
+    if not a.no_extras and rank == 0:
+        S.close()
+        extras = {"mixed_c2": run_mixed_c2(a, torch), "learned_c4": run_learned_c4(a, torch)}
+
     # ---- CPU baseline: the oracle on a bounded sample ----
     cpu = None
     if not a.no_cpu and rank == 0:
@@ -370,7 +461,8 @@ def run_ours(a):
            "clocks": clk.summary(),
            "kernel_ms": {"k_step_level0": ms_step / a.steps, "k_resid_restrict_level0": ms_rr / a.steps,
                          "k_spmv_dot": ms_sp / a.steps},
-           "sweep": sweep}
+           "sweep": sweep,
+           "comparisons": extras}
     if rank == 0:
         print(json.dumps(out))
     if pg:

@@ -168,6 +168,15 @@ amgps_status amgps_vcycle_backward(amgps_ctx* ctx, const double* r_dev, const do
 amgps_status amgps_vcycle_loss_grad(amgps_ctx* ctx, const double* E0_dev, int m, double* loss,
                                     double* gweights);
 
+/* Apply the V-cycle error propagation E = I - B A `cycles` times, in place,
+ * to each of the m vectors of E_dev (m x n_0 doubles, vector i at
+ * E_dev + i n_0), with the current smoothers.  Repeated application
+ * concentrates the vectors on the slowest modes of E, so the loss of
+ * amgps_vcycle_loss_grad on them estimates the squared convergence factor
+ * rho(E)^2 (E is self-adjoint in the A inner product) and its gradient.  No
+ * passage of the paper defines it.  Asynchronous. */
+amgps_status amgps_error_cycles(amgps_ctx* ctx, double* E_dev, int m, int cycles);
+
 /* The weight-predicting MLP of the learned smoother (not in the paper):
  * 8 level features -> 64 -> 64 -> 4, ReLU, beta = beta_ref exp(0.5 tanh(o)).
  * Stateless FP32 kernels on caller-owned device buffers, enqueued on `stream`

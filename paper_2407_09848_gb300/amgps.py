@@ -66,6 +66,7 @@ _SIGS = {
     "amgps_synchronize": ([C.c_void_p], C.c_int),
     "amgps_vcycle_loss_grad": ([C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p],
                                C.c_int),
+    "amgps_error_cycles": ([C.c_void_p, C.c_void_p, C.c_int, C.c_int], C.c_int),
     "amgps_mlp_forward": ([C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                            C.c_void_p], C.c_int),
     "amgps_mlp_backward": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
@@ -306,6 +307,11 @@ class Solver:
         self._check(lib().amgps_vcycle_loss_grad(self._h, _dptr(E0, m * self._n(0), "E0"), m,
                                                  C.byref(loss), gw.ctypes.data))
         return loss.value, gw[: self.n_levels - 1]
+
+    def error_cycles(self, E, cycles):
+        """E <- (I - B A)^cycles E, in place, for each row of E (m x n_0 CUDA float64)."""
+        m = E.shape[0]
+        self._check(lib().amgps_error_cycles(self._h, _dptr(E, m * self._n(0), "E"), m, int(cycles)))
 
     def pcg(self, b, x, rtol=1e-8, maxit=1000, raise_on_noconv=True):
         n = self._n(0)

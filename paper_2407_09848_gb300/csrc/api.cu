@@ -1580,6 +1580,30 @@ amgps_status amgps_vcycle_loss_grad(amgps_ctx* c, const double* E0, int m, doubl
   });
 }
 
+amgps_status amgps_error_cycles(amgps_ctx* c, double* E, int m, int cycles) {
+  return guard(c, [&] {
+    need_loaded(c);
+    REQ(E && m >= 1 && cycles >= 0 && cycles <= 1000, AMGPS_E_ARG, "bad arguments");
+    enter(c);
+    cudaStream_t s = c->stream;
+    Level& L0 = c->lv[0];
+    const int64_t n = L0.n;
+    const DevMat<double> A = devmat64(L0, c->prec);
+    RedWork rw = redwork(c, 1, n);
+    rw.grid = reduction_grid(L0.nslices * kSlice, c->nsm);
+    for (int i = 0; i < m; ++i) {
+      double* e = E + (size_t)i * n;
+      for (int q = 0; q < cycles; ++q) {
+        launch_spmv_dot(A, e, c->pp, rw, c->dscal, s);  // r = A e
+        with_engine(c, [&](auto eng) { decltype(eng)::vcycle(c, c->pp, c->pz); });
+        launch_sub(n, e, c->pz, e, s);                   // e <- (I - B A) e
+      }
+    }
+    check_launch();
+    leave(c);
+  });
+}
+
 amgps_status amgps_mlp_forward(const float* params, const float* feats, int batch,
                                const float* beta_ref, float* beta, float* acts, void* stream) {
   return guard(nullptr, [&] {

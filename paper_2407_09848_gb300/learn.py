@@ -128,11 +128,22 @@ class WeightMLP:
         return self
 
 
+PRE_CYCLES = 6
+
+
 class Problem:
     """One training problem: hierarchy, library context, features and the
-    seeded error vectors of its loss."""
+    seeded error vectors of its loss.
 
-    def __init__(self, H, nvec=32, seed=0, solver=None):
+    The loss is the one-cycle A-norm error reduction of vectors that first ran
+    through `pre_cycles` V-cycles with the weights being evaluated: those
+    vectors concentrate on the slowest modes of E = I - B A, so the loss
+    estimates the squared convergence factor rho(E)^2 -- the quantity that
+    decides PCG iterations -- and, E being A-self-adjoint, the one-cycle
+    gradient with the pre-cycled vectors held fixed is its gradient.  With
+    pre_cycles = 0 it is the plain mean reduction of random vectors."""
+
+    def __init__(self, H, nvec=32, seed=0, solver=None, pre_cycles=PRE_CYCLES):
         import torch
         from .amgps import Solver
         self.H = H
@@ -140,6 +151,7 @@ class Problem:
         self.feats = level_features(self.S, H)
         n = H.levels[0].A.shape[0]
         self.E0 = torch.from_numpy(pr.vec_normal(n, seed=seed, count=nvec)).cuda()
+        self.pre_cycles = pre_cycles
 
     def set_weights(self, betas):
         used = []
@@ -153,7 +165,10 @@ class Problem:
 
     def loss_grad(self, betas):
         used = self.set_weights(betas)
-        loss, gw = self.S.loss_grad(self.E0)
+        E = self.E0.clone()
+        if self.pre_cycles:
+            self.S.error_cycles(E, self.pre_cycles)
+        loss, gw = self.S.loss_grad(E)
         g = gw[:, :DEGREE].copy()
         g[~np.asarray(used)] = 0.0  # a level that fell back does not depend on the network
         return loss, g

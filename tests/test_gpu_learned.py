@@ -79,7 +79,7 @@ def test_safety_fallback_and_checkpoint(torch_cuda, tmp_path):
     assert learn.is_safe(amgps.opt4_weights(4))
     assert not learn.is_safe(np.array([3.0, 3.0, 3.0, 3.0]))
     H = pr.build_hierarchy(pr.varcoef(12, 1.0, 3.0, seed=5), coarse_max=30)
-    p = learn.Problem(H, nvec=4, seed=1)
+    p = learn.Problem(H, nvec=4, seed=1, pre_cycles=0)
     ref = amgps.opt4_weights(4)
     nl = H.n_levels - 1
     l_ref, _ = p.loss_grad([ref] * nl)
@@ -96,8 +96,30 @@ def test_safety_fallback_and_checkpoint(torch_cuda, tmp_path):
     assert np.array_equal(net.params.cpu().numpy(), net2.params.cpu().numpy())
 
 
+def test_error_cycles_estimate_convergence_factor(torch_cuda):
+    # after many cycles the one-cycle reduction approaches rho(E)^2, the
+    # largest eigenvalue of E in the A inner product (dense check on 8^3)
+    torch = torch_cuda
+    from paper_2407_09848_gb300.amgps import Solver
+    H = pr.build_hierarchy(pr.varcoef(8, 1.0, 3.0, seed=2), coarse_max=8)
+    S = Solver().load(H.A, H.P)
+    n = H.A[0].shape[0]
+    ora = OracleAMG(H.A, H.P, SmootherSpec("cheb4_opt", 4))
+    B = np.stack([ora.vcycle(e) for e in np.eye(n)], axis=1)
+    Ad = H.A[0].toarray()
+    L = np.linalg.cholesky(Ad)
+    Et = L.T @ (np.eye(n) - B @ Ad) @ np.linalg.inv(L.T)   # E in the A-orthonormal basis
+    rho = np.max(np.abs(np.linalg.eigvalsh(0.5 * (Et + Et.T))))
+    E = torch.from_numpy(np.random.default_rng(0).standard_normal((3, n))).cuda()
+    S.error_cycles(E, 60)
+    loss, _ = S.loss_grad(E)
+    # a Rayleigh quotient of E^2: approaches rho^2 from below
+    assert 0.99 * rho ** 2 <= loss <= (1 + 1e-9) * rho ** 2
+
+
 def test_trained_network_gain_over_optimal_weights(torch_cuda):
-    # train on 12 log-normal 24^3 problems, evaluate on 6 held-out ones
+    # train on 12 log-normal 24^3 problems, evaluate on 6 held-out ones, with the
+    # convergence-factor objective
     from paper_2407_09848_gb300 import learn
     train_set = learn.make_training_set(12, 24, seed0=0, nvec=8)
     test_set = learn.make_training_set(6, 24, seed0=5000, nvec=8)
@@ -107,7 +129,7 @@ def test_trained_network_gain_over_optimal_weights(torch_cuda):
     hist = learn.train(net, train_set, 60, batch=12, lr=5e-3)
     after, _ = learn.evaluate(net, test_set)
     gain = 1.0 - after / ref
-    print(f"held-out V-cycle error reduction: optimal weights {ref:.5f}, learned {after:.5f} "
+    print(f"held-out squared convergence factor: optimal weights {ref:.5f}, learned {after:.5f} "
           f"(gain {100 * gain:.2f}%); training loss {hist[0]:.5f} -> {hist[-1]:.5f}")
     assert hist[-1] < hist[0]
     assert after < ref

@@ -71,6 +71,17 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def max_over_ranks(value, dist=None):
+    """Largest `value` over all ranks (replicas report the slowest rank)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def step_source_hash():
     h = hashlib.sha256()
     for p in STEP_SOURCES:
@@ -376,11 +387,7 @@ def run_ours(a):
     n_rr, ms_rr, _ = S.profile_read(PROF_RESTRICT, reset=True)
     n_sp, ms_sp, _ = S.profile_read(PROF_SPMV, reset=True)
     launches, _, _ = S.profile_read(3, reset=True)
-    ms_per = total_ms / a.steps
-    if pg:
-        t = torch.tensor([ms_per], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms_per = float(t.item())
+    ms_per = max_over_ranks(total_ms / a.steps, pg)
     true_res = float(np.linalg.norm(b - H.levels[0].A @ x.cpu().numpy()) / np.linalg.norm(b))
 
     # ---- roofline of the fused smoother step on the finest level ----
@@ -392,12 +399,31 @@ def run_ours(a):
             tr = json.load(f)
         if tr.get("source_sha256") == step_source_hash() and tr.get("workload") == workload_name(a):
             traffic = tr.get("dram_bytes_per_launch")
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak if achieved else None, "traffic": traffic,
-            "kernel": "k_step (fused SpMV + residual + l1 scaling + recurrence update), level 0",
-            "launches": n_step, "avg_launch_us": 1e3 * ms_step / max(n_step, 1),
-            "bytes_per_launch": by_step / max(n_step, 1), "peak_source": peak_src,
-            "share_of_step_time": ms_step / total_ms if total_ms else None}
+    hbm = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": achieved / peak if achieved else None, "traffic": traffic,
+           "kernel": "fused smoother step on level 0 (k_step_tma + leftover k_step)",
+           "launches": n_step, "avg_launch_us": 1e3 * ms_step / max(n_step, 1),
+           "bytes_per_launch": by_step / max(n_step, 1), "peak_source": peak_src,
+           "share_of_step_time": ms_step / total_ms if total_ms else None}
+    roof = hbm
+    clk = clk.summary() if hasattr(clk, "summary") else clk
+    if a.prec == "f64" and a.kind in ("cheb4", "cheb4_opt", "weights") and n_step:
+        # FP64 path: the step is bound by the FP64 pipe (ncu: ~83% busy vs
+        # DRAM ~62%).  Flops per launch averaged over a V-cycle's level-0 steps:
+        # (2k-2) steps of 2 nnz + 6 n (with the c1 z term) and one initial step
+        # of 2 nnz + 4 n.  Peak: 304 FP64 FMA thread-instructions per clock
+        # (152 SMs x 2, ncu peak_sustained) x 2 flops x the sampled SM clock.
+        k = a.degree
+        nnz0 = float(H.levels[0].A.nnz)
+        fl = ((2 * k - 2) * (2 * nnz0 + 6 * n) + (2 * nnz0 + 4 * n)) / (2 * k - 1)
+        mhz = clk.get("sm_mhz") or 2070.0
+        fpeak = 304 * 2 * mhz * 1e6 / 1e12
+        fach = fl / (1e-3 * ms_step / n_step) / 1e12
+        roof = {"bound": "alu", "achieved": fach, "peak": fpeak, "unit": "TFLOP/s",
+                "frac": fach / fpeak, "traffic": traffic, "kernel": hbm["kernel"],
+                "flops_per_launch": fl, "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2 flops x sampled SM clock",
+                "launches": n_step, "avg_launch_us": hbm["avg_launch_us"],
+                "share_of_step_time": hbm["share_of_step_time"], "hbm": hbm}
 
     # ---- end to end through the host-buffer C-ABI call ----
     bh = torch.from_numpy(b.copy()).pin_memory()
@@ -458,7 +484,7 @@ def run_ours(a):
            "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 8 * n,
                    "d2h_bytes_per_step": 8 * n},
            "gpu_launches": launches,
-           "clocks": clk.summary(),
+           "clocks": clk,
            "kernel_ms": {"k_step_level0": ms_step / a.steps, "k_resid_restrict_level0": ms_rr / a.steps,
                          "k_spmv_dot": ms_sp / a.steps},
            "sweep": sweep,

@@ -1,0 +1,60 @@
+"""bench.py's multi-process plumbing on the CPU (gloo, world size 2): the
+replicas report the slowest rank, and the reference arm runs on rank 0 only."""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    got = bench.max_over_ranks(10.0 + rank, dist)
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, got))
+
+
+def test_max_over_ranks_gloo():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    res = dict(q.get(timeout=10) for _ in range(2))
+    assert res == {0: 11.0, 1: 11.0}
+
+
+def test_single_process_and_reference_rank():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(3.5) == 3.5
+    old = dict(os.environ)
+    try:
+        os.environ.update(RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+        import argparse
+        args = argparse.Namespace(impl="reference", steps=1, warmup=0, grid=8, kind="cheb4_opt",
+                                  degree=4, prec="f64", rtol=1e-8)
+        assert bench.run_reference(args) == 0   # non-zero ranks exit without work
+    finally:
+        os.environ.clear()
+        os.environ.update(old)

@@ -224,6 +224,16 @@ amgps_status amgps_vcycle(amgps_ctx* ctx, const double* r_dev, double* z_dev);
 amgps_status amgps_pcg(amgps_ctx* ctx, const double* b_dev, double* x_dev, double rtol,
                        int maxit, int* iters, double* relres);
 
+/* PCG on A_0 x = b preconditioned by ONE smoother application on level 0
+ * from zero, z = S(r, 0) = q(M^{-1}A) M^{-1} r (SPD because |p| < 1 on (0,1]),
+ * without coarse levels: the smoother-only experiment of the remark in
+ * Sec. 2.3 (PCG iteration counts for the 1st- and 4th-kind polynomials on
+ * A = Q D Q^T).  Needs a hierarchy of two or more levels (level 0 must own a
+ * smoother).  Otherwise as amgps_pcg (honours AMGPS_OPT_FLEXIBLE). */
+amgps_status amgps_pcg_smoother(amgps_ctx* ctx, amgps_kind kind, int degree, const double* b_dev,
+                                double* x_dev, double rtol, int maxit, int* iters,
+                                double* relres);
+
 /* amgps_pcg with host vectors: copies b (pinned staging) to the device,
  * solves, copies x back.  b_host, x_host: n_0 doubles. Synchronous. */
 amgps_status amgps_pcg_host(amgps_ctx* ctx, const double* b_host, double* x_host,
@@ -234,8 +244,12 @@ amgps_status amgps_synchronize(amgps_ctx* ctx);
 
 /* Context options.  AMGPS_OPT_TMA (default 1): run the fused smoother step
  * through the TMA-fed pipelined kernel where the level's layout allows it
- * (0: the direct-load kernel everywhere; results are identical). */
-enum { AMGPS_OPT_TMA = 1 };
+ * (0: the direct-load kernel everywhere; results are identical).
+ * AMGPS_OPT_FLEXIBLE (default 0): amgps_pcg uses the flexible (Polak-Ribiere)
+ * direction update beta = r_{k+1}.(z_{k+1} - z_k) / (r_k.z_k) -- the flexible
+ * CG family of the paper's outer solver (Sec. 4), robust when the
+ * preconditioner is not exactly a fixed symmetric operator (FP32/BF16). */
+enum { AMGPS_OPT_TMA = 1, AMGPS_OPT_FLEXIBLE = 2 };
 amgps_status amgps_set_option(amgps_ctx* ctx, int option, int64_t value);
 
 /* Host-only planning query (no device needed): how the TMA-fed step would

@@ -57,11 +57,18 @@ class OracleAMG:
         x = smooth(A, b, x, spec, M=M)
         return x
 
-    def pcg(self, b, rtol=1e-8, maxit=1000, x0=None):
+    def pcg(self, b, rtol=1e-8, maxit=1000, x0=None, flexible=False, precond=None):
         """Preconditioned CG, preconditioner = one V-cycle.
 
-        Returns (x, iterations, recurrence residual ratio, history).  The
-        iteration count is the number of products A p performed."""
+        flexible=True takes the Polak-Ribiere form of the direction update,
+        beta = r_{k+1}.(z_{k+1} - z_k) / (r_k.z_k), the flexible CG that Sec. 4
+        uses as its outer solver (there in a one-reduction variant), which
+        stays robust when the preconditioner is not exactly a fixed symmetric
+        operator.  precond (optional) replaces the V-cycle, e.g. one smoother
+        application for the smoother-only experiment of the remark in
+        Sec. 2.3.  Returns (x, iterations, recurrence residual ratio,
+        history); the iteration count is the number of products A p performed."""
+        B = self.vcycle if precond is None else precond
         A = self.A[0]
         b = np.asarray(b, dtype=np.float64)
         x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
@@ -70,7 +77,7 @@ class OracleAMG:
         hist = [np.linalg.norm(r) / bnorm]
         if hist[-1] <= rtol:
             return x, 0, hist[-1], hist
-        z = self.vcycle(r)
+        z = B(r)
         p = z.copy()
         rz = r @ z
         it = 0
@@ -83,8 +90,13 @@ class OracleAMG:
             hist.append(rn / bnorm)
             if rn <= rtol * bnorm or it == maxit:
                 break
-            z = self.vcycle(r)
+            z_old = z
+            z = B(r)
             rz_new = r @ z
-            p = z + (rz_new / rz) * p
+            if flexible:
+                beta = (rz_new - r @ z_old) / rz
+            else:
+                beta = rz_new / rz
+            p = z + beta * p
             rz = rz_new
         return x, it, hist[-1], hist

@@ -61,6 +61,8 @@ _SIGS = {
                               C.c_int),
     "amgps_pcg": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int),
                    C.POINTER(C.c_double)], C.c_int),
+    "amgps_pcg_smoother": ([C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
+                            C.POINTER(C.c_int), C.POINTER(C.c_double)], C.c_int),
     "amgps_pcg_host": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int),
                         C.POINTER(C.c_double)], C.c_int),
     "amgps_synchronize": ([C.c_void_p], C.c_int),
@@ -323,6 +325,17 @@ class Solver:
         self._check(st)
         return it.value, rel.value
 
+    def pcg_smoother(self, kind, degree, b, x, rtol=1e-5, maxit=10000, raise_on_noconv=True):
+        """PCG preconditioned by one level-0 smoother application (no coarse levels)."""
+        n = self._n(0)
+        it, rel = C.c_int(), C.c_double()
+        st = lib().amgps_pcg_smoother(self._h, KIND[kind], degree, _dptr(b, n, "b"), _dptr(x, n, "x"),
+                                      rtol, maxit, C.byref(it), C.byref(rel))
+        if st == 3 and not raise_on_noconv:
+            return it.value, rel.value
+        self._check(st)
+        return it.value, rel.value
+
     def pcg_host(self, b, x, rtol=1e-8, maxit=1000):
         """b, x: host arrays (numpy float64, or pinned CPU torch tensors)."""
         n = self._n(0)
@@ -349,6 +362,10 @@ class Solver:
     def set_tma(self, on):
         """Use the TMA-fed step kernel where possible (default) or the direct one."""
         self._check(lib().amgps_set_option(self._h, 1, 1 if on else 0))
+
+    def set_flexible(self, on):
+        """Flexible (Polak-Ribiere) CG in pcg (default off)."""
+        self._check(lib().amgps_set_option(self._h, 2, 1 if on else 0))
 
     def synchronize(self):
         self._check(lib().amgps_synchronize(self._h))

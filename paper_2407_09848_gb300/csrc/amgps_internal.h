@@ -100,6 +100,7 @@ struct TmaPlan {
 enum Scalar {
   S_PQ = 0, S_RR = 1, S_RZ = 2, S_RZOLD = 3, S_ALPHA = 4, S_BB = 5, S_NRM = 6, S_BETA = 7,
   S_ERR = 8,  // set non-zero by a kernel whose bounded wait gave up
+  S_RZP = 9,  // r . z_old (flexible CG)
   S_COUNT = 16
 };
 
@@ -152,9 +153,11 @@ void launch_spmv_dot(const DevMat<double>& A, const double* p, double* q, const 
                      double* scal, cudaStream_t s);
 void launch_cg_update(int64_t n, const double* p, const double* q, double* x, double* r,
                       const RedWork& w, double* scal, cudaStream_t s);
-// out_slot receives a.b; if rz_shift, scal[S_RZOLD] <- scal[S_RZ] first and the dot goes to S_RZ
+// rz_mode 0: scal[out_slot] = a.b.  1: scal[S_RZOLD] <- scal[S_RZ], scal[S_RZ] = a.b,
+// scal[S_BETA] = S_RZ / S_RZOLD.  2: as 1 with the flexible (Polak-Ribiere)
+// beta = (S_RZ - S_RZP) / S_RZOLD.
 void launch_dot(int64_t n, const double* a, const double* b, const RedWork& w, double* scal,
-                int out_slot, bool rz_shift, cudaStream_t s);
+                int out_slot, int rz_mode, cudaStream_t s);
 void launch_xpay(int64_t n, const double* z, double* p, const double* scal, cudaStream_t s);
 template <class XT>
 void launch_coarse_gemv(int nc, const double* ainv, const XT* b, XT* x, cudaStream_t s);

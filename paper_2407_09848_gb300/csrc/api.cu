@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -420,7 +421,7 @@ struct amgps_ctx {
   amgps_prec prec = AMGPS_F64;
   std::vector<Level> lv;
   std::vector<void*> allocs;
-  double *pr = nullptr, *pp = nullptr, *pq = nullptr, *pz = nullptr;
+  double *pr = nullptr, *pp = nullptr, *pq = nullptr, *pz = nullptr, *pz2 = nullptr;
   double *stage_b = nullptr, *stage_x = nullptr;
   double* h_stage = nullptr;
   size_t h_stage_n = 0;
@@ -438,6 +439,7 @@ struct amgps_ctx {
   bool graph_ok = false;
   int64_t graph_kernels = 0;   // kernel nodes in gexec
   bool use_tma = true;         // TMA-fed step kernels (option AMGPS_OPT_TMA)
+  bool flexible = false;       // flexible (Polak-Ribiere) CG (option AMGPS_OPT_FLEXIBLE)
   int64_t launch_adjust = 0;   // captured (not run) launches removed, replays added
   int64_t launch_base = 0;     // reset point of the launch counter
   bool prof = false;
@@ -508,7 +510,7 @@ void free_hierarchy(amgps_ctx* c) {
   c->lv.clear();
   c->loaded = false;
   c->bwd_ready = false;
-  c->pr = c->pp = c->pq = c->pz = c->stage_b = c->stage_x = nullptr;
+  c->pr = c->pp = c->pq = c->pz = c->pz2 = c->stage_b = c->stage_x = nullptr;
 }
 
 void enter(amgps_ctx* c) {
@@ -824,7 +826,7 @@ struct Engine {
       run_step(c, L, a, s);
       rin_next = r;
     }
-    launch_dot(n, (const double*)gx, (const double*)zc, rw, c->ddots, slot0, false, s);
+    launch_dot(n, (const double*)gx, (const double*)zc, rw, c->ddots, slot0, 0, s);
     for (int j = 1; j < k; ++j) {
       StepArgs<VT, XT> a;
       a.A = A;
@@ -842,7 +844,7 @@ struct Engine {
       a.beta = XT(0);
       a.fam = FAM_CHEB4;
       run_step(c, L, a, s);
-      launch_dot(n, (const double*)gx, (const double*)zn, rw, c->ddots, slot0 + j, false, s);
+      launch_dot(n, (const double*)gx, (const double*)zn, rw, c->ddots, slot0 + j, 0, s);
       rin_next = r;
       std::swap(zc, zn);
     }
@@ -1033,9 +1035,17 @@ void check_kind_degree(int kind, int degree) {
   REQ(degree >= 1 && degree <= kMaxDegree, AMGPS_E_ARG, "degree must be in 1..16");
 }
 
-// Outer PCG (Sec. 4; standard Hestenes-Stiefel form, one V-cycle per iteration).
+// Outer PCG (Sec. 4): one application of the preconditioner (a V-cycle unless
+// `precond` is given) per iteration; beta = r.z / r_old.z_old, or with the
+// flexible option the Polak-Ribiere beta = r.(z - z_old) / r_old.z_old.
+using Precond = std::function<void(const double* r, double* z)>;
+
 void pcg_impl(amgps_ctx* c, const double* b, double* x, double rtol, int maxit, int* iters,
-              double* relres, bool* converged) {
+              double* relres, bool* converged, const Precond& precond = nullptr) {
+  const Precond vcyc = [c](const double* r, double* z) {
+    with_engine(c, [&](auto eng) { decltype(eng)::vcycle(c, r, z); });
+  };
+  const Precond& M = precond ? precond : vcyc;
   Level& L = c->lv[0];
   cudaStream_t s = c->stream;
   const int64_t n = L.n;
@@ -1044,10 +1054,12 @@ void pcg_impl(amgps_ctx* c, const double* b, double* x, double rtol, int maxit, 
   rw_spmv.grid = reduction_grid(L.nslices * kSlice, c->nsm);
   CK(cudaMemcpyAsync(c->pr, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
-  launch_dot(n, b, b, rw_dot, c->dscal, S_BB, false, s);
-  with_engine(c, [&](auto eng) { decltype(eng)::vcycle(c, c->pr, c->pz); });
-  launch_dot(n, c->pr, c->pz, rw_dot, c->dscal, S_RZ, true, s);
-  CK(cudaMemcpyAsync(c->pp, c->pz, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  double* z = c->pz;    // current preconditioned residual
+  double* zo = c->pz2;  // previous one (flexible CG)
+  launch_dot(n, b, b, rw_dot, c->dscal, S_BB, 0, s);
+  M(c->pr, z);
+  launch_dot(n, c->pr, z, rw_dot, c->dscal, S_RZ, 1, s);
+  CK(cudaMemcpyAsync(c->pp, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(c->hscal, c->dscal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   harvest(c);
@@ -1084,9 +1096,11 @@ void pcg_impl(amgps_ctx* c, const double* b, double* x, double rtol, int maxit, 
     rel = std::sqrt(rr) / bnorm;
     if (rel <= rtol) break;
     if (it == maxit) break;
-    with_engine(c, [&](auto eng) { decltype(eng)::vcycle(c, c->pr, c->pz); });
-    launch_dot(n, c->pr, c->pz, rw_dot, c->dscal, S_RZ, true, s);
-    launch_xpay(n, c->pz, c->pp, c->dscal, s);
+    std::swap(z, zo);
+    M(c->pr, z);
+    if (c->flexible) launch_dot(n, c->pr, zo, rw_dot, c->dscal, S_RZP, 0, s);
+    launch_dot(n, c->pr, z, rw_dot, c->dscal, S_RZ, c->flexible ? 2 : 1, s);
+    launch_xpay(n, z, c->pp, c->dscal, s);
     check_launch();
   }
   *iters = std::min(it, maxit);
@@ -1338,6 +1352,7 @@ amgps_status amgps_hierarchy_load(amgps_ctx* c, int n_levels, const amgps_csr* A
     c->pp = (double*)dalloc(c, n0 * sizeof(double));
     c->pq = (double*)dalloc(c, n0 * sizeof(double));
     c->pz = (double*)dalloc(c, n0 * sizeof(double));
+    c->pz2 = (double*)dalloc(c, n0 * sizeof(double));
     c->stage_b = (double*)dalloc(c, n0 * sizeof(double));
     c->stage_x = (double*)dalloc(c, n0 * sizeof(double));
     CK(cudaStreamSynchronize(c->stream));
@@ -1661,6 +1676,30 @@ amgps_status amgps_pcg(amgps_ctx* c, const double* b, double* x, double rtol, in
   });
 }
 
+amgps_status amgps_pcg_smoother(amgps_ctx* c, amgps_kind kind, int degree, const double* b,
+                                double* x, double rtol, int maxit, int* iters, double* relres) {
+  return guard(c, [&] {
+    need_loaded(c);
+    check_kind_degree(kind, degree);
+    REQ(c->lv.size() >= 2, AMGPS_E_ARG, "level 0 must have a smoother (two or more levels)");
+    REQ(b && x && iters && relres && (const void*)b != (const void*)x, AMGPS_E_ARG,
+        "null or aliased arguments");
+    REQ(rtol > 0.0 && maxit >= 1, AMGPS_E_ARG, "rtol must be > 0 and maxit >= 1");
+    const Spec& sp = c->lv[0].spec;
+    REQ(kind != AMGPS_WEIGHTS || (sp.kind == AMGPS_WEIGHTS && sp.k == degree), AMGPS_E_STATE,
+        "AMGPS_WEIGHTS: set the level's weights of this degree first");
+    const Coefs cf = make_coefs(kind, degree, sp.w, sp.rho);
+    enter(c);
+    bool conv = false;
+    const Precond smoother = [&](const double* r, double* z) {
+      with_engine(c, [&](auto eng) { decltype(eng)::smooth_public(c, 0, cf, r, z, true); });
+    };
+    pcg_impl(c, b, x, rtol, maxit, iters, relres, &conv, smoother);
+    leave(c);
+    REQ(conv, AMGPS_E_NOCONV, "PCG did not reach rtol within maxit");
+  });
+}
+
 amgps_status amgps_pcg_host(amgps_ctx* c, const double* b_host, double* x_host, double rtol,
                             int maxit, int* iters, double* relres) {
   return guard(c, [&] {
@@ -1719,9 +1758,13 @@ amgps_status amgps_synchronize(amgps_ctx* c) {
 amgps_status amgps_set_option(amgps_ctx* c, int option, int64_t value) {
   return guard(c, [&] {
     REQ(c, AMGPS_E_ARG, "null context");
-    REQ(option == AMGPS_OPT_TMA, AMGPS_E_ARG, "unknown option");
-    c->use_tma = value != 0;
-    c->graph_ok = false;
+    REQ(option == AMGPS_OPT_TMA || option == AMGPS_OPT_FLEXIBLE, AMGPS_E_ARG, "unknown option");
+    if (option == AMGPS_OPT_TMA) {
+      c->use_tma = value != 0;
+      c->graph_ok = false;
+    } else {
+      c->flexible = value != 0;
+    }
   });
 }
 

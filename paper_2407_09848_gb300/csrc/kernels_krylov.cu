@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kBlock) k_dot(int64_t n, const double* __restr
     if (rz_shift) {
       scal[S_RZOLD] = scal[S_RZ];
       scal[S_RZ] = tot;
-      scal[S_BETA] = tot / scal[S_RZOLD];
+      scal[S_BETA] = (rz_shift == 2 ? tot - scal[S_RZP] : tot) / scal[S_RZOLD];
     } else {
       scal[slot] = tot;
     }
@@ -92,8 +92,8 @@ __global__ void __launch_bounds__(kBlock) k_dot(int64_t n, const double* __restr
 }
 
 void launch_dot(int64_t n, const double* a, const double* b, const RedWork& w, double* scal,
-                int out_slot, bool rz_shift, cudaStream_t s) {
-  k_dot<<<w.grid, kBlock, 0, s>>>(n, a, b, w, scal, out_slot, rz_shift ? 1 : 0);
+                int out_slot, int rz_mode, cudaStream_t s) {
+  k_dot<<<w.grid, kBlock, 0, s>>>(n, a, b, w, scal, out_slot, rz_mode);
   count_launch();
 }
 

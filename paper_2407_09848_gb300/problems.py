@@ -259,6 +259,44 @@ def build_hierarchy(st: Stencil7, coarse_max=512, name="") -> Hierarchy:
     return Hierarchy(levels=levels, name=name)
 
 
+def spectral_test_matrix(N, spectrum):
+    """Dense SPD A = Q D Q^T of the smoother-only experiment (remark of
+    Sec. 2.3): Q the orthonormal eigenvectors of the 1-D finite-difference
+    second-derivative matrix (discrete sine basis), D one of three spectra:
+      "equispaced": N points evenly spaced in [1/N, 1];
+      "boundary":   1 - logspace(-8,-1,N/2) and logspace(-8,-1,N/2)
+                    (accumulating at both ends of (0, 1));
+      "gap":        logspace(-8,-1,N/2) and N/2 points log-spaced between
+                    10 and pi.
+    Returns (A as CSR with all N^2 entries, b = A 1)."""
+    i = np.arange(1, N + 1)
+    Q = np.sqrt(2.0 / (N + 1)) * np.sin(np.outer(i, i) * np.pi / (N + 1))
+    h = N // 2
+    if spectrum == "equispaced":
+        d = np.linspace(1.0 / N, 1.0, N)
+    elif spectrum == "boundary":
+        d = np.concatenate([1.0 - np.logspace(-8, -1, h), np.logspace(-8, -1, N - h)])
+    elif spectrum == "gap":
+        d = np.concatenate([np.logspace(-8, -1, h), np.logspace(1, np.log10(np.pi), N - h)])
+    else:
+        raise ValueError(spectrum)
+    A = (Q * d) @ Q.T
+    A = 0.5 * (A + A.T)
+    Acsr = sp.csr_matrix(A)
+    # keep every entry (the matrix is dense; scipy drops exact zeros only)
+    return Acsr, Acsr @ np.ones(N)
+
+
+def single_aggregate_hierarchy(A):
+    """Two levels for a matrix without geometry: A and the 1x1 Galerkin
+    coarse matrix of P = (1,...,1)^T (the level-0 smoother is what matters)."""
+    n = A.shape[0]
+    P = sp.csr_matrix((np.ones(n), np.zeros(n, dtype=np.int32), np.arange(n + 1, dtype=np.int32)),
+                      shape=(n, 1))
+    Ac = sp.csr_matrix(P.T @ A @ P)
+    return [sp.csr_matrix(A), Ac], [P]
+
+
 def rhs_uniform(n, seed=0):
     """b ~ U[-1,1]^n (PCG64 generator, ``seed``)."""
     return np.random.default_rng(seed).uniform(-1.0, 1.0, n)

@@ -23,6 +23,7 @@ sys.path.insert(0, ROOT)
 OUT = os.path.join(ROOT, "tests", "golden", "oracle_pcg_iterations.json")
 KINDS = ["cheb1", "cheb4", "cheb4_opt", "cheb1_opt"]
 DEGREES = [1, 2, 3, 4, 5, 6]
+ALL_KINDS = KINDS + ["l1jacobi"]
 
 _H = {}
 
@@ -59,10 +60,14 @@ def run_one(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--grids", default="32,256")
+    ap.add_argument("--kinds", default=",".join(KINDS))
+    ap.add_argument("--degrees", default=",".join(map(str, DEGREES)))
     ap.add_argument("--jobs", type=int, default=4)
     a = ap.parse_args()
     grids = [int(g) for g in a.grids.split(",")]
-    tasks = [(g, kd, k) for g in grids for kd in KINDS for k in DEGREES]
+    kinds = [k for k in a.kinds.split(",") if k in ALL_KINDS]
+    degrees = [int(k) for k in a.degrees.split(",")]
+    tasks = [(g, kd, k) for g in grids for kd in kinds for k in degrees]
     ctx = mp.get_context("spawn")
     with ctx.Pool(a.jobs) as pool:
         rows = pool.map(run_one, tasks, chunksize=1)

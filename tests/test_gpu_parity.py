@@ -357,3 +357,21 @@ def test_tma_step_equals_direct_step(torch_cuda, prec):
     S.vcycle(r, z2)
     S.synchronize()
     assert torch.equal(z1, z2)
+
+
+@pytest.mark.parametrize("prec", ["f64", "bf16"])
+def test_flexible_pcg_iterations_identical(torch_cuda, prec):
+    from paper_2407_09848_gb300.amgps import Solver
+    torch = torch_cuda
+    H = pr.build_hierarchy(pr.varcoef(24, 1.5, 4.0, seed=7), coarse_max=200)
+    S = Solver().load(H.A, H.P, prec=prec)
+    S.set_flexible(True)
+    b = pr.rhs_uniform(H.A[0].shape[0], seed=2)
+    x = torch.empty(H.A[0].shape[0], dtype=torch.float64, device="cuda")
+    it, rel = S.pcg(to_dev(torch, b), x, rtol=1e-9)
+    true = np.linalg.norm(b - H.A[0] @ to_np(x)) / np.linalg.norm(b)
+    assert rel <= 1e-9 and true <= 2e-9
+    if prec == "f64":
+        _, ito, _, _ = OracleAMG(H.A, H.P, SmootherSpec("cheb4_opt", 4)).pcg(b, rtol=1e-9,
+                                                                            flexible=True)
+        assert it == ito

@@ -1,0 +1,77 @@
+"""Smoother-only PCG (the remark of Sec. 2.3) on the GPU against the oracle.
+
+Equispaced and boundary-clustered spectra: identical iteration counts.  The
+gapped spectrum has kappa(A) ~ 3e9; after ~90 CG steps its count is not fixed
+by FP64 arithmetic (the oracle alone, from the same seeded construction, stops
+at 87 on one host and at 100 on another, where sin and the BLAS product round
+differently), so there the test compares the early iterates element-wise and
+bounds the count."""
+import numpy as np
+import pytest
+
+from oracle.amg import OracleAMG
+from oracle.smoother import SmootherSpec, smooth
+from paper_2407_09848_gb300 import problems as pr
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_09848_gb300 import build
+    build.build()
+    return torch
+
+
+def _oracle(As, Ps, kind, k, b, maxit):
+    sp = SmootherSpec(kind, k)
+    ora = OracleAMG(As, Ps, sp)
+    x, it, rel, _ = ora.pcg(b, rtol=1e-5, maxit=maxit,
+                            precond=lambda r: smooth(As[0], r, None, sp, M=ora.M[0]))
+    return x, it, rel
+
+
+@pytest.mark.parametrize("spectrum", ["equispaced", "boundary"])
+def test_smoother_only_iterations_match_oracle(torch_cuda, spectrum):
+    torch = torch_cuda
+    from paper_2407_09848_gb300.amgps import Solver
+    A, b = pr.spectral_test_matrix(200, spectrum)
+    As, Ps = pr.single_aggregate_hierarchy(A)
+    S = Solver().load(As, Ps)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.empty_like(bd)
+    for kind in ("cheb1_opt", "cheb4_opt"):
+        for k in (2, 5):
+            it, rel = S.pcg_smoother(kind, k, bd, x, rtol=1e-5)
+            xo, ito, _ = _oracle(As, Ps, kind, k, b, 10000)
+            assert it == ito, (spectrum, kind, k, it, ito)
+            assert rel <= 1e-5
+            assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-6 * np.linalg.norm(xo)
+    S.close()
+
+
+def test_smoother_only_gap_spectrum(torch_cuda):
+    torch = torch_cuda
+    from paper_2407_09848_gb300.amgps import Solver
+    A, b = pr.spectral_test_matrix(200, "gap")
+    As, Ps = pr.single_aggregate_hierarchy(A)
+    S = Solver().load(As, Ps)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.empty_like(bd)
+    for kind in ("cheb1_opt", "cheb4_opt"):
+        for k in (2, 5):
+            for m in (3, 10):
+                it, _ = S.pcg_smoother(kind, k, bd, x, rtol=1e-5, maxit=m,
+                                       raise_on_noconv=False)
+                xo, ito, _ = _oracle(As, Ps, kind, k, b, m)
+                assert it == ito == m
+                err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
+                assert err <= 1e-9, (kind, k, m, err)
+            it, rel = S.pcg_smoother(kind, k, bd, x, rtol=1e-5)
+            _, ito, _ = _oracle(As, Ps, kind, k, b, 10000)
+            assert rel <= 1e-5
+            assert abs(it - ito) <= max(3, 0.15 * ito), (kind, k, it, ito)
+    S.close()

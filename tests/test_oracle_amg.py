@@ -121,3 +121,37 @@ def test_pcg_poisson32_opt4_k4_sanity():
     x, it, rel, _ = amg.pcg(b, rtol=1e-8)
     assert rel <= 1e-8 and 5 <= it <= 20
     assert np.linalg.norm(b - A[0] @ x) <= 2e-8 * np.linalg.norm(b)
+
+
+def test_flexible_pcg_matches_dense_solve_and_standard_on_linear_precond():
+    # with an exactly linear symmetric preconditioner, r_{k+1}.z_k = 0 in exact
+    # arithmetic, so the flexible and standard forms take the same iterations
+    A, Pl = hier(pr.varcoef(10, 1.0, 3.0, seed=4), 20)
+    amg = OracleAMG(A, Pl, SmootherSpec("cheb4_opt", 3))
+    b = pr.rhs_uniform(A[0].shape[0], seed=1)
+    x1, it1, _, _ = amg.pcg(b, rtol=1e-10)
+    x2, it2, rel2, _ = amg.pcg(b, rtol=1e-10, flexible=True)
+    assert it1 == it2 and rel2 <= 1e-10
+    xd = np.linalg.solve(A[0].toarray(), b)
+    assert np.linalg.norm(x2 - xd) <= 1e-8 * np.linalg.norm(xd)
+
+
+def test_pcg_precond_hook_textbook_cases():
+    # identity preconditioner: plain CG, which on an SPD matrix with m distinct
+    # eigenvalues reaches the solution in m steps (exact arithmetic; here to
+    # ~1e-12 with m = 3)
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(rng.standard_normal((30, 30)))
+    d = np.repeat([1.0, 2.0, 5.0], 10)
+    import scipy.sparse as sp
+    A = sp.csr_matrix((Q * d) @ Q.T)
+    As, Ps = pr.single_aggregate_hierarchy(A)
+    amg = OracleAMG(As, Ps, SmootherSpec("cheb4", 1))
+    b = rng.standard_normal(30)
+    x, it, rel, _ = amg.pcg(b, rtol=1e-11, precond=lambda r: r.copy())
+    assert it == 3 and rel <= 1e-11
+    # exact inverse as preconditioner: one step
+    Ainv = np.linalg.inv(A.toarray())
+    x, it, rel, _ = amg.pcg(b, rtol=1e-11, precond=lambda r: Ainv @ r)
+    assert it == 1
+    assert np.allclose(x, Ainv @ b, atol=1e-12 * np.linalg.norm(Ainv @ b))

@@ -46,3 +46,35 @@ def test_seeded_and_grf_normalised():
     assert np.array_equal(pr.rhs_uniform(100, 3), pr.rhs_uniform(100, 3))
     g = pr.grf((20, 18, 16), 3.0, seed=7)
     assert abs(g.mean()) < 1e-12 and abs(g.std() - 1) < 1e-12
+
+
+@pytest.mark.parametrize("spectrum", ["equispaced", "boundary", "gap"])
+def test_spectral_test_matrix_has_the_stated_spectrum(spectrum):
+    N = 64
+    A, b = pr.spectral_test_matrix(N, spectrum)
+    Ad = A.toarray()
+    assert A.nnz == N * N and np.array_equal(Ad, Ad.T)
+    ev = np.linalg.eigvalsh(Ad)
+    h = N // 2
+    if spectrum == "equispaced":
+        d = np.arange(1, N + 1) / N
+    elif spectrum == "boundary":
+        d = np.concatenate([10.0 ** np.linspace(-8, -1, h), 1 - 10.0 ** np.linspace(-8, -1, h)])
+    else:
+        d = np.concatenate([10.0 ** np.linspace(-8, -1, h),
+                            10.0 ** np.linspace(1, np.log10(np.pi), h)])
+    assert np.max(np.abs(ev - np.sort(d))) <= 1e-13 * d.max()
+    assert np.allclose(b, Ad.sum(axis=1), rtol=0, atol=1e-14 * N)
+    if spectrum == "equispaced":
+        # the eigenvectors are the discrete sine modes: A v_j = (j/N) v_j
+        i = np.arange(1, N + 1)
+        j = 5
+        v = np.sin(i * j * np.pi / (N + 1))
+        assert np.allclose(Ad @ v, (j / N) * v, rtol=0, atol=1e-13)
+
+
+def test_single_aggregate_hierarchy_is_galerkin():
+    A, _ = pr.spectral_test_matrix(16, "equispaced")
+    As, Ps = pr.single_aggregate_hierarchy(A)
+    assert As[1].shape == (1, 1) and Ps[0].shape == (16, 1)
+    assert np.isclose(As[1][0, 0], A.sum())

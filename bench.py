@@ -442,7 +442,7 @@ def run_ours(a):
     sweep = None
     if not a.no_sweep and rank == 0:
         sweep = []
-        for kind in ("cheb1", "cheb4", "cheb4_opt", "cheb1_opt"):
+        for kind in ("cheb1", "cheb4", "cheb4_opt", "cheb1_opt", "l1jacobi"):
             for k in range(1, 7):
                 configure(S, H, kind, k, torch)
                 S.pcg(bd, x, rtol=a.rtol, maxit=1000)
@@ -454,6 +454,20 @@ def run_ours(a):
                               "ms": round(1e3 * (time.perf_counter() - t0), 3),
                               "oracle_iterations": golden_iterations(a.grid, kind, k)})
         configure(S, H, a.kind, a.degree, torch)
+        # outer CG forms at the timed configuration: standard, flexible
+        # (Polak-Ribiere), flexible with one reduction per iteration
+        outer = []
+        for form in ("cg", "flexible", "fcg1"):
+            S.set_flexible(form)
+            S.pcg(bd, x, rtol=a.rtol, maxit=1000)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it_f, rel_f = S.pcg(bd, x, rtol=a.rtol, maxit=1000)
+            torch.cuda.synchronize()
+            outer.append({"form": form, "iterations": it_f,
+                          "ms": round(1e3 * (time.perf_counter() - t0), 3), "relres": rel_f})
+        S.set_flexible("cg")
+        sweep = {"smoothers": sweep, "outer_cg_forms": outer}
 
     # ---- comparisons: mixed precision (192^3) and learned + mixed (256^3) ----
     extras = None

@@ -245,10 +245,18 @@ amgps_status amgps_synchronize(amgps_ctx* ctx);
 /* Context options.  AMGPS_OPT_TMA (default 1): run the fused smoother step
  * through the TMA-fed pipelined kernel where the level's layout allows it
  * (0: the direct-load kernel everywhere; results are identical).
- * AMGPS_OPT_FLEXIBLE (default 0): amgps_pcg uses the flexible (Polak-Ribiere)
- * direction update beta = r_{k+1}.(z_{k+1} - z_k) / (r_k.z_k) -- the flexible
- * CG family of the paper's outer solver (Sec. 4), robust when the
- * preconditioner is not exactly a fixed symmetric operator (FP32/BF16). */
+ * AMGPS_OPT_FLEXIBLE (default 0) selects the outer CG form of amgps_pcg and
+ * amgps_pcg_smoother, all three equal in exact arithmetic for a fixed SPD
+ * preconditioner:
+ *   0  standard PCG, beta = r_{k+1}.z_{k+1} / (r_k.z_k);
+ *   1  flexible, Polak-Ribiere beta = r_{k+1}.(z_{k+1} - z_k) / (r_k.z_k),
+ *      robust when the preconditioner is not exactly a fixed symmetric
+ *      operator (FP32/BF16 smoothers);
+ *   2  flexible CG with one global reduction per iteration, the outer solver
+ *      of Sec. 4: w = A z, then rho = z.r, gamma = z.q, delta = z.w in one
+ *      reduction; beta = gamma / eta_old, p = z - beta p, q = w - beta q
+ *      (q = A p kept by recurrence), eta = delta - beta gamma, alpha = rho/eta.
+ *      Other values: AMGPS_E_ARG. */
 enum { AMGPS_OPT_TMA = 1, AMGPS_OPT_FLEXIBLE = 2 };
 amgps_status amgps_set_option(amgps_ctx* ctx, int option, int64_t value);
 

@@ -100,3 +100,49 @@ class OracleAMG:
             p = z + beta * p
             rz = rz_new
         return x, it, hist[-1], hist
+
+    def fcg1(self, b, rtol=1e-8, maxit=1000, precond=None):
+        """Flexible CG needing one global reduction per iteration: the outer
+        solver named in Sec. 4 (the paper cites the method and prints no
+        algorithm; this is the textbook truncated flexible CG, FCG(1), with
+        q = A p carried by recurrence).  Per iteration:
+            z = B r;  w = A z
+            rho = z.r,  gamma = z.q,  delta = z.w       (one reduction)
+            beta = gamma / eta                          (A-orthogonalise z to p)
+            p = z - beta p;  q = w - beta q;  eta = delta - beta gamma
+            alpha = rho / eta;  x += alpha p;  r -= alpha q
+        eta = p.A p follows from A being symmetric (p.w = q.z); rho stands for
+        p.r because the previous update made r orthogonal to p.  x0 = 0;
+        returns as pcg."""
+        B = self.vcycle if precond is None else precond
+        A = self.A[0]
+        b = np.asarray(b, dtype=np.float64)
+        x = np.zeros_like(b)
+        r = b.copy()
+        bnorm = np.linalg.norm(b)
+        hist = [1.0]
+        if bnorm == 0.0:
+            return x, 0, 0.0, [0.0]
+        p = q = None
+        eta = None
+        it = 0
+        for it in range(1, maxit + 1):
+            z = B(r)
+            w = A @ z
+            rho, delta = z @ r, z @ w
+            if p is None:
+                p, q, eta = z.copy(), w.copy(), delta
+            else:
+                gamma = z @ q
+                beta = gamma / eta
+                p = z - beta * p
+                q = w - beta * q
+                eta = delta - beta * gamma
+            alpha = rho / eta
+            x = x + alpha * p
+            r = r - alpha * q
+            rn = np.linalg.norm(r)
+            hist.append(rn / bnorm)
+            if rn <= rtol * bnorm:
+                break
+        return x, it, hist[-1], hist

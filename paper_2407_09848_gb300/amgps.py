@@ -363,9 +363,14 @@ class Solver:
         """Use the TMA-fed step kernel where possible (default) or the direct one."""
         self._check(lib().amgps_set_option(self._h, 1, 1 if on else 0))
 
+    OUTER = {"cg": 0, "flexible": 1, "fcg1": 2}
+
     def set_flexible(self, on):
-        """Flexible (Polak-Ribiere) CG in pcg (default off)."""
-        self._check(lib().amgps_set_option(self._h, 2, 1 if on else 0))
+        """Outer CG form of pcg / pcg_smoother: False or "cg" (standard),
+        True or "flexible" (Polak-Ribiere beta), "fcg1" (flexible CG with one
+        reduction per iteration)."""
+        v = self.OUTER[on] if isinstance(on, str) else (1 if on else 0)
+        self._check(lib().amgps_set_option(self._h, 2, v))
 
     def synchronize(self):
         self._check(lib().amgps_synchronize(self._h))

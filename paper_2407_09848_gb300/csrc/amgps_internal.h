@@ -96,20 +96,6 @@ struct TmaPlan {
   int vals_bytes = 0, vec_bytes = 0, win_bytes = 0, stage_bytes = 0, nstages = 0;
 };
 
-// Device scalar slots of the Krylov solver.
-enum Scalar {
-  S_PQ = 0, S_RR = 1, S_RZ = 2, S_RZOLD = 3, S_ALPHA = 4, S_BB = 5, S_NRM = 6, S_BETA = 7,
-  S_ERR = 8,  // set non-zero by a kernel whose bounded wait gave up
-  S_RZP = 9,  // r . z_old (flexible CG)
-  S_COUNT = 16
-};
-
-struct RedWork {
-  double* part = nullptr;       // per-block partial sums [grid]
-  unsigned* counter = nullptr;  // arrival counter (reset by the last block)
-  int grid = 0;
-};
-
 // ---- launchers (kernels_smooth.cu) ----
 template <class VT, class XT>
 void launch_step(const StepArgs<VT, XT>& a, cudaStream_t s);
@@ -148,31 +134,6 @@ void launch_l1diag(const DevMat<VT>& A, XT* dinv, cudaStream_t s);
 template <class A, class B>
 void launch_convert(int64_t n, const A* in, B* out, cudaStream_t s);
 
-// ---- launchers (kernels_krylov.cu) ----
-void launch_spmv_dot(const DevMat<double>& A, const double* p, double* q, const RedWork& w,
-                     double* scal, cudaStream_t s);
-void launch_cg_update(int64_t n, const double* p, const double* q, double* x, double* r,
-                      const RedWork& w, double* scal, cudaStream_t s);
-// rz_mode 0: scal[out_slot] = a.b.  1: scal[S_RZOLD] <- scal[S_RZ], scal[S_RZ] = a.b,
-// scal[S_BETA] = S_RZ / S_RZOLD.  2: as 1 with the flexible (Polak-Ribiere)
-// beta = (S_RZ - S_RZP) / S_RZOLD.
-void launch_dot(int64_t n, const double* a, const double* b, const RedWork& w, double* scal,
-                int out_slot, int rz_mode, cudaStream_t s);
-void launch_xpay(int64_t n, const double* z, double* p, const double* scal, cudaStream_t s);
-template <class XT>
-void launch_coarse_gemv(int nc, const double* ainv, const XT* b, XT* x, cudaStream_t s);
-void launch_chol_inverse(int n, double* work, double* ainv, int* status, cudaStream_t s);
-template <class VT, class XT>
-void launch_power_step(const DevMat<VT>& A, const XT* v, const XT* dinv, XT* w, const RedWork& rw,
-                       double* scal, cudaStream_t s);
-template <class XT>
-void launch_scale_by_norm(int64_t n, const XT* w, XT* v, const double* scal, int slot,
-                          cudaStream_t s);
-template <class XT>
-void launch_norm2(int64_t n, const XT* v, const RedWork& rw, double* scal, int slot,
-                  cudaStream_t s);
-
-int reduction_grid(int64_t work_items, int nsm);
 void tma_configure(int max_dynamic_smem);
 
 // Kernels enqueued through the launchers above (graph captures included; the
@@ -181,3 +142,5 @@ int64_t launches_enqueued();
 void count_launch();
 
 }  // namespace amgps
+
+#include "krylov.h"

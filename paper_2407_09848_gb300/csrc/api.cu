@@ -439,7 +439,7 @@ struct amgps_ctx {
   bool graph_ok = false;
   int64_t graph_kernels = 0;   // kernel nodes in gexec
   bool use_tma = true;         // TMA-fed step kernels (option AMGPS_OPT_TMA)
-  bool flexible = false;       // flexible (Polak-Ribiere) CG (option AMGPS_OPT_FLEXIBLE)
+  int flexible = 0;            // AMGPS_OPT_FLEXIBLE: 0 standard, 1 Polak-Ribiere, 2 one-reduction
   int64_t launch_adjust = 0;   // captured (not run) launches removed, replays added
   int64_t launch_base = 0;     // reset point of the launch counter
   bool prof = false;
@@ -1040,12 +1040,76 @@ void check_kind_degree(int kind, int degree) {
 // flexible option the Polak-Ribiere beta = r.(z - z_old) / r_old.z_old.
 using Precond = std::function<void(const double* r, double* z)>;
 
+// One-reduction flexible CG (AMGPS_OPT_FLEXIBLE = 2): per iteration one
+// preconditioner application z = B r, w = A z with the three inner products
+// in one grid reduction, and one update kernel that keeps q = A p by the
+// recurrence q = w - beta q_old.  The iteration count is the number of
+// updates of x, as in the standard form.
+void fcg1_impl(amgps_ctx* c, const double* b, double* x, double rtol, int maxit, int* iters,
+               double* relres, bool* converged, const Precond& M) {
+  Level& L = c->lv[0];
+  cudaStream_t s = c->stream;
+  const int64_t n = L.n;
+  const DevMat<double> A = devmat64(L, c->prec);
+  RedWork rw_dot = redwork(c, 0, n), rw_spmv = redwork(c, 1, n), rw_upd = redwork(c, 2, n);
+  rw_spmv.grid = reduction_grid(L.nslices * kSlice, c->nsm);
+  double *z = c->pz, *w = c->pz2, *p = c->pp, *q = c->pq;
+  CK(cudaMemcpyAsync(c->pr, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  launch_dot(n, b, b, rw_dot, c->dscal, S_BB, 0, s);
+  CK(cudaMemcpyAsync(c->hscal, c->dscal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const double bnorm = std::sqrt(c->hscal[S_BB]);
+  *converged = false;
+  *iters = 0;
+  *relres = 0.0;
+  if (bnorm == 0.0) {
+    *converged = true;
+    return;
+  }
+  REQ(std::isfinite(bnorm), AMGPS_E_NAN, "right-hand side is not finite");
+  int it = 0;
+  double rel = 1.0;
+  for (it = 1; it <= maxit; ++it) {
+    const int first = it == 1;
+    M(c->pr, z);
+    {
+      ProfScope ps(c, true, 2, (double)L.nnz * 8 + (double)L.explicit_entries * 4.0 + n * 8.0 * 4);
+      launch_spmv_dot3(A, z, w, c->pr, q, first, rw_spmv, c->dscal, s);
+      ps.done();
+    }
+    launch_fcg_update(n, z, w, p, q, x, c->pr, first, rw_upd, c->dscal, s);
+    check_launch();
+    CK(cudaMemcpyAsync(c->hscal, c->dscal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(c->ev_sync, s));
+    CK(cudaEventSynchronize(c->ev_sync));
+    harvest(c);
+    if (c->hscal[S_ERR] != 0.0) {
+      CK(cudaMemsetAsync(c->dscal + S_ERR, 0, sizeof(double), s));
+      throw Fail{AMGPS_E_TIMEOUT, "a bounded wait inside a pipelined kernel gave up"};
+    }
+    const double eta = c->hscal[S_PQ], rr = c->hscal[S_RR];
+    REQ(std::isfinite(eta) && std::isfinite(rr) && std::isfinite(c->hscal[S_ALPHA]), AMGPS_E_NAN,
+        "NaN/Inf in PCG scalars");
+    REQ(eta > 0.0, AMGPS_E_NOT_SPD, "p^T A p <= 0 in PCG");
+    rel = std::sqrt(rr) / bnorm;
+    if (rel <= rtol || it == maxit) break;
+  }
+  *iters = std::min(it, maxit);
+  *relres = rel;
+  *converged = rel <= rtol;
+}
+
 void pcg_impl(amgps_ctx* c, const double* b, double* x, double rtol, int maxit, int* iters,
               double* relres, bool* converged, const Precond& precond = nullptr) {
   const Precond vcyc = [c](const double* r, double* z) {
     with_engine(c, [&](auto eng) { decltype(eng)::vcycle(c, r, z); });
   };
   const Precond& M = precond ? precond : vcyc;
+  if (c->flexible == 2) {
+    fcg1_impl(c, b, x, rtol, maxit, iters, relres, converged, M);
+    return;
+  }
   Level& L = c->lv[0];
   cudaStream_t s = c->stream;
   const int64_t n = L.n;
@@ -1098,8 +1162,8 @@ void pcg_impl(amgps_ctx* c, const double* b, double* x, double rtol, int maxit, 
     if (it == maxit) break;
     std::swap(z, zo);
     M(c->pr, z);
-    if (c->flexible) launch_dot(n, c->pr, zo, rw_dot, c->dscal, S_RZP, 0, s);
-    launch_dot(n, c->pr, z, rw_dot, c->dscal, S_RZ, c->flexible ? 2 : 1, s);
+    if (c->flexible == 1) launch_dot(n, c->pr, zo, rw_dot, c->dscal, S_RZP, 0, s);
+    launch_dot(n, c->pr, z, rw_dot, c->dscal, S_RZ, c->flexible == 1 ? 2 : 1, s);
     launch_xpay(n, z, c->pp, c->dscal, s);
     check_launch();
   }
@@ -1181,7 +1245,7 @@ amgps_status amgps_create(amgps_ctx** out, int device, void* user_stream) {
     CK(cudaMalloc(&u->ddots, kDotSlots * sizeof(double)));
     CK(cudaMallocHost(&u->hdots, kDotSlots * sizeof(double)));
     const int maxgrid = u->nsm * 4;
-    CK(cudaMalloc(&u->part, (size_t)maxgrid * sizeof(double)));
+    CK(cudaMalloc(&u->part, (size_t)maxgrid * 3 * sizeof(double)));  // grid_sum3: 3 x grid
     CK(cudaMalloc(&u->counters, 8 * sizeof(unsigned)));
     CK(cudaMemset(u->counters, 0, 8 * sizeof(unsigned)));
     c = u.release();
@@ -1763,7 +1827,8 @@ amgps_status amgps_set_option(amgps_ctx* c, int option, int64_t value) {
       c->use_tma = value != 0;
       c->graph_ok = false;
     } else {
-      c->flexible = value != 0;
+      REQ(value >= 0 && value <= 2, AMGPS_E_ARG, "AMGPS_OPT_FLEXIBLE takes 0, 1 or 2");
+      c->flexible = (int)value;
     }
   });
 }

@@ -73,6 +73,120 @@ void launch_cg_update(int64_t n, const double* p, const double* q, double* x, do
   count_launch();
 }
 
+// Three sums in one pass (the one-reduction flexible CG): partials are laid
+// out [v0 of every block | v1 ... | v2 ...] in w.part (3 x grid doubles); the
+// last block adds each column in index order and calls fin(t0, t1, t2).
+template <class Fin>
+__device__ __forceinline__ void grid_sum3(double v0, double v1, double v2, const RedWork& w,
+                                          Fin fin) {
+  __shared__ double sh[32];
+  __shared__ bool last;
+  const double b0 = block_sum(v0, sh);
+  const double b1 = block_sum(v1, sh);
+  const double b2 = block_sum(v2, sh);
+  if (threadIdx.x == 0) {
+    w.part[blockIdx.x] = b0;
+    w.part[gridDim.x + blockIdx.x] = b1;
+    w.part[2 * gridDim.x + blockIdx.x] = b2;
+    __threadfence();
+    const unsigned t = atomicAdd(w.counter, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    double t[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0;
+      for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x)
+        s += __ldcg(w.part + j * gridDim.x + i);
+      t[j] = block_sum(s, sh);
+    }
+    if (threadIdx.x == 0) {
+      fin(t[0], t[1], t[2]);
+      *w.counter = 0u;
+    }
+  }
+}
+
+// One-reduction flexible CG (the outer solver of Sec. 4): w = A z and the
+// three inner products rho = z.r, gamma = z.q_old, delta = z.w in a single
+// grid reduction.  The last block forms beta = gamma / eta_old (the
+// A-orthogonalisation of z against p_old), eta = p.A p = delta - beta gamma
+// (by symmetry of A, with q = A p), and alpha = rho / eta.
+__global__ void __launch_bounds__(kBlock) k_spmv_dot3(const DevMat<double> A,
+                                                      const double* __restrict__ z,
+                                                      double* __restrict__ w,
+                                                      const double* __restrict__ r,
+                                                      const double* __restrict__ q, int first,
+                                                      const RedWork rw, double* scal) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * kWarpsPerBlock;
+  double zr = 0.0, zq = 0.0, zw = 0.0;
+  for (int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); s < A.nslices;
+       s += nw) {
+    const int64_t row = s * kSlice + lane;
+    const double t = row_spmv<1, double, double>(A, s, lane, row, z, 0.0);
+    if (row < A.n) {
+      w[row] = t;
+      const double zi = z[row];
+      zw = fma(zi, t, zw);
+      zr = fma(zi, r[row], zr);
+      if (!first) zq = fma(zi, q[row], zq);
+    }
+  }
+  grid_sum3(zr, zq, zw, rw, [&](double rho, double gam, double del) {
+    const double beta = first ? 0.0 : gam / scal[S_PQ];
+    const double eta = first ? del : del - beta * gam;
+    scal[S_RZ] = rho;
+    scal[S_GAMMA] = gam;
+    scal[S_DELTA] = del;
+    scal[S_BETA] = beta;
+    scal[S_PQ] = eta;
+    scal[S_ALPHA] = rho / eta;
+  });
+}
+
+void launch_spmv_dot3(const DevMat<double>& A, const double* z, double* w, const double* r,
+                      const double* q, int first, const RedWork& rw, double* scal,
+                      cudaStream_t s) {
+  k_spmv_dot3<<<rw.grid, kBlock, 0, s>>>(A, z, w, r, q, first, rw, scal);
+  count_launch();
+}
+
+// p = z - beta p, q = w - beta q (first: p = z, q = w), x += alpha p,
+// r -= alpha q, r.r (S_RR)
+__global__ void __launch_bounds__(kBlock) k_fcg_update(int64_t n, const double* __restrict__ z,
+                                                       const double* __restrict__ w,
+                                                       double* __restrict__ p,
+                                                       double* __restrict__ q,
+                                                       double* __restrict__ x,
+                                                       double* __restrict__ r, int first,
+                                                       const RedWork rw, double* scal) {
+  const double alpha = scal[S_ALPHA], beta = scal[S_BETA];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kBlock) {
+    const double pi = first ? z[i] : fma(-beta, p[i], z[i]);
+    const double qi = first ? w[i] : fma(-beta, q[i], w[i]);
+    p[i] = pi;
+    q[i] = qi;
+    x[i] = fma(alpha, pi, x[i]);
+    const double ri = fma(-alpha, qi, r[i]);
+    r[i] = ri;
+    acc = fma(ri, ri, acc);
+  }
+  grid_sum(acc, rw, [&](double tot) { scal[S_RR] = tot; });
+}
+
+void launch_fcg_update(int64_t n, const double* z, const double* w, double* p, double* q,
+                       double* x, double* r, int first, const RedWork& rw, double* scal,
+                       cudaStream_t s) {
+  k_fcg_update<<<rw.grid, kBlock, 0, s>>>(n, z, w, p, q, x, r, first, rw, scal);
+  count_launch();
+}
+
 __global__ void __launch_bounds__(kBlock) k_dot(int64_t n, const double* __restrict__ a,
                                                 const double* __restrict__ b, const RedWork w,
                                                 double* scal, int slot, int rz_shift) {

@@ -1,0 +1,62 @@
+"""GPU PCG iteration counts against the oracle's stored counts
+(tests/golden/oracle_pcg_iterations.json, written by make_oracle_iterations.py
+from oracle/ alone): every stored kind and degree, on the 32^3 Poisson problem
+and on the full 256^3 problem the benchmark times (same hierarchy, b, rtol,
+launch configuration)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2407_09848_gb300 import problems as pr
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "oracle_pcg_iterations.json")
+
+
+def runs_for(grid):
+    with open(GOLDEN) as f:
+        return [r for r in json.load(f)["runs"] if r["grid"] == grid]
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_09848_gb300 import build
+    build.build()
+    return torch
+
+
+def configure(S, H, kind, k, torch):
+    # kind "cheb1": rho_l = 1.1 x the 10-step power estimate from v0 = U[-1,1]
+    # (seed 0), computed here by the library's own power iteration
+    if kind == "cheb1":
+        for l in range(H.n_levels - 1):
+            v0 = torch.from_numpy(pr.vec_uniform(H.levels[l].A.shape[0], seed=0)).cuda()
+            S.set_smoother(l, "cheb1", k, rho=1.1 * S.estimate_lambda(l, v0, iters=10))
+    else:
+        S.set_smoother(-1, kind, k)
+
+
+@pytest.mark.parametrize("grid", [32, 256])
+def test_iterations_equal_stored_oracle_counts(torch_cuda, grid):
+    torch = torch_cuda
+    from paper_2407_09848_gb300.amgps import Solver
+    runs = runs_for(grid)
+    assert runs, "no stored counts"
+    H = pr.build_hierarchy(pr.poisson(grid), coarse_max=512)
+    S = Solver().load(H.A, H.P)
+    b = torch.from_numpy(pr.rhs_uniform(H.levels[0].A.shape[0], seed=0)).cuda()
+    x = torch.empty_like(b)
+    bad = []
+    for r in runs:
+        configure(S, H, r["kind"], r["degree"], torch)
+        it, rel = S.pcg(b, x, rtol=1e-8, maxit=1000)
+        if it != r["iterations"] or rel > 1e-8:
+            bad.append((r["kind"], r["degree"], it, r["iterations"]))
+    S.close()
+    assert not bad, bad

@@ -375,3 +375,32 @@ def test_flexible_pcg_iterations_identical(torch_cuda, prec):
         _, ito, _, _ = OracleAMG(H.A, H.P, SmootherSpec("cheb4_opt", 4)).pcg(b, rtol=1e-9,
                                                                             flexible=True)
         assert it == ito
+
+
+@pytest.mark.parametrize("prec", ["f64", "bf16"])
+def test_fcg1_iterations_identical(torch_cuda, prec):
+    # the one-reduction flexible CG: FP64 iteration counts equal the oracle's,
+    # x agrees with the oracle's iterate; BF16 smoothers still reach 1e-9
+    from paper_2407_09848_gb300.amgps import Solver
+    torch = torch_cuda
+    H = pr.build_hierarchy(pr.varcoef(24, 1.5, 4.0, seed=7), coarse_max=200)
+    S = Solver().load(H.A, H.P, prec=prec)
+    S.set_flexible("fcg1")
+    b = pr.rhs_uniform(H.A[0].shape[0], seed=2)
+    x = torch.empty(H.A[0].shape[0], dtype=torch.float64, device="cuda")
+    it, rel = S.pcg(to_dev(torch, b), x, rtol=1e-9)
+    true = np.linalg.norm(b - H.A[0] @ to_np(x)) / np.linalg.norm(b)
+    assert rel <= 1e-9 and true <= 2e-9
+    if prec == "f64":
+        xo, ito, _, _ = OracleAMG(H.A, H.P, SmootherSpec("cheb4_opt", 4)).fcg1(b, rtol=1e-9)
+        assert it == ito
+        assert np.linalg.norm(to_np(x) - xo) <= 1e-7 * np.linalg.norm(xo)
+        # after two iterations (far from cancellation) the iterates agree to 1e-12
+        it2, _ = S.pcg(to_dev(torch, b), x, rtol=1e-9, maxit=2, raise_on_noconv=False)
+        xo2, _, _, _ = OracleAMG(H.A, H.P, SmootherSpec("cheb4_opt", 4)).fcg1(b, rtol=1e-9,
+                                                                               maxit=2)
+        assert it2 == 2
+        assert np.linalg.norm(to_np(x) - xo2) <= 1e-12 * np.linalg.norm(xo2)
+    S.set_flexible("cg")
+    it_cg, _ = S.pcg(to_dev(torch, b), x, rtol=1e-9)
+    assert abs(it_cg - it) <= 1

@@ -155,3 +155,41 @@ def test_pcg_precond_hook_textbook_cases():
     x, it, rel, _ = amg.pcg(b, rtol=1e-11, precond=lambda r: Ainv @ r)
     assert it == 1
     assert np.allclose(x, Ainv @ b, atol=1e-12 * np.linalg.norm(Ainv @ b))
+
+
+def test_fcg1_equals_pcg_on_fixed_spd_preconditioner():
+    # for a fixed SPD preconditioner the one-reduction flexible CG generates the
+    # same Krylov iterates as standard PCG (exact arithmetic); q stays A p
+    A, Pl = hier(pr.varcoef(10, 1.0, 3.0, seed=4), 20)
+    amg = OracleAMG(A, Pl, SmootherSpec("cheb4_opt", 3))
+    b = pr.rhs_uniform(A[0].shape[0], seed=1)
+    x1, it1, _, h1 = amg.pcg(b, rtol=1e-10)
+    x2, it2, rel2, h2 = amg.fcg1(b, rtol=1e-10)
+    assert it1 == it2 and rel2 <= 1e-10
+    # residual histories agree until cancellation near convergence
+    assert np.allclose(h1[:6], h2[:6], rtol=1e-8, atol=0)
+    xd = np.linalg.solve(A[0].toarray(), b)
+    assert np.linalg.norm(x2 - xd) <= 1e-8 * np.linalg.norm(xd)
+
+
+def test_fcg1_textbook_cases():
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(rng.standard_normal((30, 30)))
+    import scipy.sparse as sp
+    A = sp.csr_matrix((Q * np.repeat([1.0, 2.0, 5.0], 10)) @ Q.T)
+    As, Ps = pr.single_aggregate_hierarchy(A)
+    amg = OracleAMG(As, Ps, SmootherSpec("cheb4", 1))
+    b = rng.standard_normal(30)
+    # identity preconditioner: CG, 3 distinct eigenvalues -> 3 steps
+    _, it, rel, _ = amg.fcg1(b, rtol=1e-11, precond=lambda r: r.copy())
+    assert it == 3 and rel <= 1e-11
+    # exact inverse: one step
+    Ainv = np.linalg.inv(A.toarray())
+    x, it, _, _ = amg.fcg1(b, rtol=1e-11, precond=lambda r: Ainv @ r)
+    assert it == 1 and np.allclose(x, Ainv @ b, atol=1e-12 * np.linalg.norm(Ainv @ b))
+    # agrees with standard PCG under a non-trivial diagonal preconditioner (a
+    # sign error in beta = z.Ap / p.Ap loses A-conjugacy and does not converge)
+    M = np.diag(1.0 / np.linspace(1, 3, 30))
+    _, it_ok, _, _ = amg.fcg1(b, rtol=1e-10, precond=lambda r: M @ r)
+    _, it_pcg, _, _ = amg.pcg(b, rtol=1e-10, precond=lambda r: M @ r)
+    assert it_ok == it_pcg

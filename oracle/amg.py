@@ -7,7 +7,8 @@ coarsest level solved exactly by a dense Cholesky factorisation (the paper uses
 30 l1-Jacobi sweeps there, Sec. 4); the outer solver is textbook
 Hestenes-Stiefel PCG stopped on the recurrence residual
 ||r_k||_2 <= rtol ||b||_2 (the paper uses flexible CG with one reduction per
-iteration, Sec. 4).
+iteration, Sec. 4); ``fcg1`` gives that variant and ``pcg(flexible=True)`` the
+two-reduction flexible form.
 """
 from __future__ import annotations
 

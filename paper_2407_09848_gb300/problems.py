@@ -259,6 +259,24 @@ def build_hierarchy(st: Stencil7, coarse_max=512, name="") -> Hierarchy:
     return Hierarchy(levels=levels, name=name)
 
 
+def geometric_aggregates(shape, coarse_max=512):
+    """Aggregate maps of 2x2x2 blocks of a lexicographic (x fastest) grid,
+    level by level until a grid has <= coarse_max points (the same coarse grids
+    as build_hierarchy).  Pure index maps -- the tentative prolongators of
+    smoothed aggregation.  Returns [(agg, n_coarse, coarse_shape), ...] with
+    agg[i] the coarse index of fine point i."""
+    out = []
+    nz, ny, nx = shape
+    while nx * ny * nz > coarse_max and min(nx, ny, nz) >= 2:
+        cnx, cny, cnz = (nx + 1) // 2, (ny + 1) // 2, (nz + 1) // 2
+        zz, yy, xx = np.meshgrid(np.arange(nz) // 2, np.arange(ny) // 2,
+                                 np.arange(nx) // 2, indexing="ij")
+        agg = (xx + cnx * (yy + cny * zz)).reshape(-1).astype(np.int32)
+        out.append((agg, cnx * cny * cnz, (cnz, cny, cnx)))
+        nz, ny, nx = cnz, cny, cnx
+    return out
+
+
 def spectral_test_matrix(N, spectrum):
     """Dense SPD A = Q D Q^T of the smoother-only experiment (remark of
     Sec. 2.3): Q the orthonormal eigenvectors of the 1-D finite-difference

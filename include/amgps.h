@@ -95,15 +95,55 @@ amgps_status amgps_destroy(amgps_ctx* ctx);
 const char* amgps_last_error(const amgps_ctx* ctx);
 
 /* Load the level hierarchy (Sec. 2): A[0..n_levels-1] square SPD CSR with
- * n_rows(A[l+1]) == n_cols(P[l]); P[0..n_levels-2] the prolongators, each an
- * unsmoothed aggregation: every row of P[l] holds exactly one entry equal to
- * 1 (the aggregate of that fine row); other P are rejected with AMGPS_E_ARG.
+ * n_rows(A[l+1]) == n_cols(P[l]); P[0..n_levels-2] the prolongators (any
+ * sparsity; A[l+1] should be P[l]^T A[l] P[l]).  A P[l] whose every row holds
+ * one entry equal to 1 (unsmoothed aggregation) restricts by summing each
+ * aggregate's children and prolongs by a gather; any other P (e.g. smoothed
+ * aggregation, amgps_sa_level) is stored with its transpose in explicit
+ * SELL-32 form and both transfers are sparse products.
  * The coarsest level (n <= 1024) is solved by a dense FP64 Cholesky
  * factorisation computed here on the device (AMGPS_E_NOT_SPD if a pivot is
  * not positive).  Replaces any earlier hierarchy; every level's smoother is
  * reset to CHEB4_OPT of degree 4.  Synchronous. */
 amgps_status amgps_hierarchy_load(amgps_ctx* ctx, int n_levels, const amgps_csr* A,
                                   const amgps_csr* P, amgps_prec prec);
+
+/* Host CSR allocated by the library (results of amgps_galerkin and
+ * amgps_sa_level).  Rows are sorted by column.  Release with
+ * amgps_csr_buf_free, which frees the three arrays and zeroes the struct
+ * (NULL allowed). */
+typedef struct {
+  int64_t n_rows, n_cols, nnz;
+  int32_t* rowptr; /* n_rows + 1 */
+  int32_t* col;    /* nnz */
+  double* val;     /* nnz */
+} amgps_csr_buf;
+void amgps_csr_buf_free(amgps_csr_buf* m);
+
+/* Galerkin coarse operator A_c = P^T A P (Sec. 2), computed on the context's
+ * device by two sparse products (A P, then P^T (A P)) with P^T formed on the
+ * device.  A: square CSR; P: n_rows(A) x n_c CSR whose rows have strictly
+ * ascending columns.  Every entry of the product is summed in a fixed order,
+ * so repeated calls give identical bits.  AMGPS_E_ARG for malformed input or
+ * when a row of an intermediate product exceeds 768 distinct columns;
+ * AMGPS_E_NOMEM when device scratch cannot be allocated.  Synchronous; needs
+ * no loaded hierarchy.  *Ac receives library-allocated host CSR. */
+amgps_status amgps_galerkin(amgps_ctx* ctx, const amgps_csr* A, const amgps_csr* P,
+                            amgps_csr_buf* Ac);
+
+/* One level of smoothed aggregation (Sec. 4): from the aggregates agg
+ * (n_rows(A) entries in [0, n_coarse), every coarse index used) the
+ * tentative prolongator P_hat (P_hat[i, agg[i]] = 1) is smoothed by one damped
+ * Jacobi step,
+ *     P = (I - omega D^{-1} A) P_hat,  D = diag(A),  omega = 4 / (3 lambda),
+ * with lambda = max_i sum_j |a_ij| / a_ii, the row-sum bound on the spectrum
+ * of D^{-1} A, and A_c = P^T A P as in amgps_galerkin.  All of it runs on the
+ * device.  Returns omega, P (n x n_coarse) and A_c as library-allocated host
+ * CSR.  AMGPS_E_NOT_SPD for a missing or non-positive diagonal entry;
+ * otherwise errors as amgps_galerkin.  Synchronous. */
+amgps_status amgps_sa_level(amgps_ctx* ctx, const amgps_csr* A, const int32_t* agg,
+                            int64_t n_coarse, double* omega, amgps_csr_buf* P,
+                            amgps_csr_buf* Ac);
 
 /* Rows, nonzeros and stored matrix entries (after padding) of a level. */
 amgps_status amgps_level_info(amgps_ctx* ctx, int level, int64_t* n, int64_t* nnz,

@@ -39,6 +39,13 @@ class CSR(C.Structure):
                 ("rowptr", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p)]
 
 
+class CSRBuf(C.Structure):
+    """Library-allocated host CSR (amgps_csr_buf)."""
+    _fields_ = [("n_rows", C.c_int64), ("n_cols", C.c_int64), ("nnz", C.c_int64),
+                ("rowptr", C.POINTER(C.c_int32)), ("col", C.POINTER(C.c_int32)),
+                ("val", C.POINTER(C.c_double))]
+
+
 _lib = None
 
 _SIGS = {
@@ -81,6 +88,10 @@ _SIGS = {
     "amgps_set_option": ([C.c_void_p, C.c_int, C.c_int64], C.c_int),
     "amgps_tma_plan_stats": ([C.POINTER(CSR), C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                               C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
+    "amgps_csr_buf_free": ([C.POINTER(CSRBuf)], None),
+    "amgps_galerkin": ([C.c_void_p, C.POINTER(CSR), C.POINTER(CSR), C.POINTER(CSRBuf)], C.c_int),
+    "amgps_sa_level": ([C.c_void_p, C.POINTER(CSR), C.c_void_p, C.c_int64, C.POINTER(C.c_double),
+                        C.POINTER(CSRBuf), C.POINTER(CSRBuf)], C.c_int),
     "amgps_profile_read": ([C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double),
                             C.POINTER(C.c_double)], C.c_int),
 }
@@ -187,6 +198,25 @@ def _csr_struct(A, keep):
     return CSR(A.shape[0], A.shape[1], A.nnz, rowptr.ctypes.data, col.ctypes.data, val.ctypes.data)
 
 
+def _from_buf(b):
+    """Copy a library-allocated CSR into scipy and release it."""
+    import scipy.sparse as sp
+    n, nnz, ncol = b.n_rows, b.nnz, b.n_cols
+    try:
+        rp = np.ctypeslib.as_array(b.rowptr, shape=(n + 1,)).copy()
+        col = np.ctypeslib.as_array(b.col, shape=(max(nnz, 1),))[:nnz].copy()
+        val = np.ctypeslib.as_array(b.val, shape=(max(nnz, 1),))[:nnz].copy()
+    finally:
+        lib().amgps_csr_buf_free(C.byref(b))
+    return sp.csr_matrix((val, col, rp), shape=(n, ncol))
+
+
+def _sorted_csr(A):
+    import scipy.sparse as sp
+    A = sp.csr_matrix(A)
+    return A if A.has_sorted_indices else A.sorted_indices()
+
+
 def _dptr(t, n=None, name="vector"):
     import torch
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
@@ -236,6 +266,40 @@ class Solver:
         self.sizes = [A.shape[0] for A in A_list]
         self.prec = prec
         return self
+
+    def galerkin(self, A, P):
+        """A_c = P^T A P on the device (amgps_galerkin); returns scipy CSR."""
+        keep = []
+        a, p = _csr_struct(_sorted_csr(A), keep), _csr_struct(_sorted_csr(P), keep)
+        out = CSRBuf()
+        self._check(lib().amgps_galerkin(self._h, C.byref(a), C.byref(p), C.byref(out)))
+        return _from_buf(out)
+
+    def sa_level(self, A, agg, n_coarse):
+        """Smoothed-aggregation level on the device (amgps_sa_level):
+        returns (P, A_c, omega) with P, A_c scipy CSR."""
+        keep = []
+        a = _csr_struct(_sorted_csr(A), keep)
+        g = np.ascontiguousarray(agg, dtype=np.int32)
+        if g.size != a.n_rows:
+            raise ValueError("agg needs one entry per row of A")
+        om = C.c_double()
+        P, Ac = CSRBuf(), CSRBuf()
+        self._check(lib().amgps_sa_level(self._h, C.byref(a), g.ctypes.data, int(n_coarse),
+                                         C.byref(om), C.byref(P), C.byref(Ac)))
+        return _from_buf(P), _from_buf(Ac), om.value
+
+    def sa_hierarchy(self, A0, levels):
+        """Smoothed-aggregation hierarchy built on the device from the
+        aggregate maps [(agg, n_coarse, ...), ...] of each level; returns
+        (A_list, P_list, omegas) ready for load()."""
+        As, Ps, oms = [_sorted_csr(A0)], [], []
+        for lv in levels:
+            P, Ac, om = self.sa_level(As[-1], lv[0], lv[1])
+            Ps.append(P)
+            As.append(Ac)
+            oms.append(om)
+        return As, Ps, oms
 
     def level_info(self, level):
         n, nnz, stored = C.c_int64(), C.c_int64(), C.c_int64()

@@ -113,6 +113,9 @@ void launch_aggregate(const int32_t* cptr, const int32_t* cidx, int64_t nc, cons
                       cudaStream_t s);
 template <class XT>
 void launch_prolong(int64_t n, const int32_t* agg, const XT* ec, XT* x, cudaStream_t s);
+// general prolongator transfers: y = M u (add = 0) or y += M u (add = 1)
+template <class XT>
+void launch_xfer(const DevMat<double>& M, const XT* u, XT* y, int add, cudaStream_t s);
 // out = x + y ; out = x - y ; out = (factor / *s_dev) * x
 template <class XT>
 void launch_add(int64_t n, const XT* x, const XT* y, XT* out, cudaStream_t s);

@@ -9,6 +9,7 @@
 // levels are launch-bound; the finest level is launched eagerly so that its
 // kernels can be timed with plain CUDA events.
 #include <algorithm>
+#include <cstdlib>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -24,6 +25,7 @@
 
 #include "amgps_internal.h"
 #include "amgps_tables.h"
+#include "setup.h"
 
 using namespace amgps;
 
@@ -116,6 +118,11 @@ struct Level {
   int32_t* cptr = nullptr;
   int32_t* cidx = nullptr;
   int64_t nc = 0;
+  // general prolongator (not one unit entry per row): P (n x nc) and R = P^T
+  // (nc x n), FP64 values, explicit SELL-32 slices
+  bool xfer_general = false;
+  DevMat<double> Pm, Rm;
+  int64_t xfer_stored = 0;  // stored entries of P and R together
   void* dinv = nullptr;   // 1 / M_i
   void *b = nullptr, *x = nullptr, *r = nullptr, *za = nullptr, *zb = nullptr, *xb = nullptr;
   double* ainv = nullptr;
@@ -158,7 +165,9 @@ void validate_csr(const amgps_csr& A, const char* what, bool square) {
   }
 }
 
-HostSell build_sell(const amgps_csr& A) {
+// allow_uniform = false keeps every slice explicit (required for rectangular
+// matrices: a uniform slice's padding column row + off may fall outside n_cols)
+HostSell build_sell(const amgps_csr& A, bool allow_uniform = true) {
   HostSell h;
   const int64_t n = A.n_rows;
   h.n = n;
@@ -175,7 +184,7 @@ HostSell build_sell(const amgps_csr& A) {
     int maxlen = 0;
     for (int64_t r = r0; r < r1; ++r) maxlen = std::max(maxlen, A.rowptr[r + 1] - A.rowptr[r]);
     // fast path: every offset of the slice already in the previous pattern
-    bool reuse = prev_ref >= 0 && (int64_t)prev.size() <= maxlen + 1;
+    bool reuse = allow_uniform && prev_ref >= 0 && (int64_t)prev.size() <= maxlen + 1;
     for (int64_t r = r0; r < r1 && reuse; ++r)
       for (int e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e) {
         const int32_t o = (int32_t)((int64_t)A.col[e] - r);
@@ -194,7 +203,7 @@ HostSell build_sell(const amgps_csr& A) {
       for (int e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e) offs.push_back((int64_t)A.col[e] - r);
     std::sort(offs.begin(), offs.end());
     offs.erase(std::unique(offs.begin(), offs.end()), offs.end());
-    const bool uniform = (int64_t)offs.size() <= maxlen + 1 && offs.size() <= 64;
+    const bool uniform = allow_uniform && (int64_t)offs.size() <= maxlen + 1 && offs.size() <= 64;
     if (uniform) {
       std::vector<int32_t> p(offs.begin(), offs.end());
       auto it = pats.find(p);
@@ -247,7 +256,7 @@ HostSell build_sell(const amgps_csr& A) {
           h.col[d.vbase + (int64_t)k * kSlice + lane] = rowbuf[k].first;
         }
         for (int k = (int)rowbuf.size(); k < d.w; ++k)
-          h.col[d.vbase + (int64_t)k * kSlice + lane] = (int32_t)r;
+          h.col[d.vbase + (int64_t)k * kSlice + lane] = (int32_t)std::min<int64_t>(r, A.n_cols - 1);
       }
     }
   }
@@ -758,7 +767,8 @@ struct Engine {
       // free between the smoothers), then the children sums of each aggregate
       ProfScope ps(c, l == 0, 1,
                    (double)L.nnz * sizeof(VT) + (double)L.explicit_entries * 4.0 +
-                       (double)L.n * sizeof(XT) * 4 + (double)L.n * 4 + (double)C.n * 12);
+                       (double)L.n * sizeof(XT) * 4 + (double)L.n * 4 + (double)C.n * 12 +
+                       (L.xfer_general ? (double)L.xfer_stored * 6.0 : 0.0));
       StepArgs<VT, XT> a;
       a.A = devmat<VT>(L);
       a.u = x;
@@ -767,7 +777,8 @@ struct Engine {
       a.fam = FAM_RES;
       a.init = true;
       run_step(c, L, a, s);
-      launch_aggregate<XT>(L.cptr, L.cidx, L.nc, (const XT*)L.r, (XT*)C.b, s);
+      if (L.xfer_general) launch_xfer<XT>(L.Rm, (const XT*)L.r, (XT*)C.b, 0, s);
+      else launch_aggregate<XT>(L.cptr, L.cidx, L.nc, (const XT*)L.r, (XT*)C.b, s);
       ps.done();
     }
     if (l + 1 == 1 && c->graph_ok && !record && !capturing(c)) {
@@ -776,7 +787,8 @@ struct Engine {
     } else {
       vcycle_level(c, l + 1, (const XT*)C.b, (XT*)C.x, record);
     }
-    launch_prolong<XT>(L.n, L.agg, (const XT*)C.x, x, s);
+    if (L.xfer_general) launch_xfer<XT>(L.Pm, (const XT*)C.x, x, 1, s);
+    else launch_prolong<XT>(L.n, L.agg, (const XT*)C.x, x, s);
     if (record) CK(cudaMemcpyAsync(L.bx2, x, L.n * sizeof(XT), cudaMemcpyDeviceToDevice, s));
     smooth(c, l, cf, b, x, false);
     check_launch();
@@ -887,10 +899,12 @@ struct Engine {
     // post-smoother x = S(b, x2): t1 = dL/db (post part), t2 = dL/dx2
     smooth_bwd(c, l, cf, bl, (const XT*)L.bx2, xbar, t1, t2, l * 32);
     // x2 = x1 + P xc ; xc = V_{l+1}(P^T (b - A x1))
-    launch_aggregate<XT>(L.cptr, L.cidx, L.nc, t2, (XT*)C.bgx, s);
+    if (L.xfer_general) launch_xfer<XT>(L.Rm, (const XT*)t2, (XT*)C.bgx, 0, s);
+    else launch_aggregate<XT>(L.cptr, L.cidx, L.nc, t2, (XT*)C.bgx, s);
     vcycle_bwd(c, l + 1, (const XT*)C.b, (const XT*)C.bgx, (XT*)C.bgb);
     CK(cudaMemsetAsync(t3, 0, L.n * sizeof(XT), s));
-    launch_prolong<XT>(L.n, L.agg, (const XT*)C.bgb, t3, s);  // dL/dres = P dL/db_c
+    if (L.xfer_general) launch_xfer<XT>(L.Pm, (const XT*)C.bgb, t3, 1, s);  // dL/dres = P dL/db_c
+    else launch_prolong<XT>(L.n, L.agg, (const XT*)C.bgb, t3, s);
     launch_add<XT>(L.n, t1, t3, gbout, s);
     {
       StepArgs<VT, XT> a;  // dL/dx1 = dL/dx2 - A dL/dres  -> t1
@@ -1211,6 +1225,190 @@ void* noalloc_scratch(int device) {
 // ===========================================================================
 // C ABI
 // ===========================================================================
+namespace {
+
+bool is_aggregation(const amgps_csr& P) {
+  for (int64_t i = 0; i < P.n_rows; ++i)
+    if (P.rowptr[i + 1] - P.rowptr[i] != 1 || P.val[P.rowptr[i]] != 1.0) return false;
+  return true;
+}
+
+// P and R = P^T in explicit SELL-32 form for the sparse-product transfers
+void load_general_transfer(amgps_ctx* c, Level& L, const amgps_csr& P) {
+  const int64_t n = P.n_rows, nc = P.n_cols;
+  // R = P^T by a counting sort over columns; rows of R come out in
+  // ascending column order because P's rows are visited in order
+  std::vector<int32_t> rptr(nc + 1, 0), rcol(P.nnz);
+  std::vector<double> rval(P.nnz);
+  for (int64_t e = 0; e < P.nnz; ++e) rptr[P.col[e] + 1]++;
+  for (int64_t I = 0; I < nc; ++I) rptr[I + 1] += rptr[I];
+  std::vector<int32_t> fill(rptr.begin(), rptr.end() - 1);
+  for (int64_t i = 0; i < n; ++i)
+    for (int e = P.rowptr[i]; e < P.rowptr[i + 1]; ++e) {
+      const int32_t f = fill[P.col[e]]++;
+      rcol[f] = (int32_t)i;
+      rval[f] = P.val[e];
+    }
+  const amgps_csr R{nc, n, P.nnz, rptr.data(), rcol.data(), rval.data()};
+  auto put = [&](const amgps_csr& M, DevMat<double>& d) {
+    HostSell h = build_sell(M, false);
+    d.n = M.n_rows;
+    d.nslices = h.nslices;
+    d.sd = dupload(c, h.sd.data(), h.sd.size());
+    d.val = dupload(c, h.val.data(), h.val.size());
+    d.col = dupload(c, h.col.data(), h.col.size());
+    const int32_t zero = 0;
+    d.off = dupload(c, &zero, 1);  // never read: every slice is explicit
+    L.xfer_stored += h.stored;
+  };
+  put(P, L.Pm);
+  put(R, L.Rm);
+  L.xfer_general = true;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Hierarchy set-up on the device (amgps_galerkin, amgps_sa_level): CSR inputs
+// are uploaded, the products run in kernels_setup.cu, results come back as
+// library-allocated host CSR.  Device scratch lives for one call.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct DevScratch {
+  std::vector<void*> ptrs;
+  ~DevScratch() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <class T>
+  T* alloc(size_t count) {
+    void* p = nullptr;
+    const cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+    REQ(e == cudaSuccess, AMGPS_E_NOMEM, std::string("set-up scratch: ") + cudaGetErrorString(e));
+    ptrs.push_back(p);
+    return (T*)p;
+  }
+  template <class T>
+  T* upload(const T* h, size_t count, cudaStream_t s) {
+    T* d = alloc<T>(count);
+    if (count) CK(cudaMemcpyAsync(d, h, count * sizeof(T), cudaMemcpyHostToDevice, s));
+    return d;
+  }
+};
+
+// every row strictly ascending: the product kernels rely on distinct columns
+void require_sorted_rows(const amgps_csr& A, const char* what) {
+  for (int64_t i = 0; i < A.n_rows; ++i)
+    for (int e = A.rowptr[i] + 1; e < A.rowptr[i + 1]; ++e)
+      REQ(A.col[e] > A.col[e - 1], AMGPS_E_ARG,
+          std::string(what) + ": columns of a row must be strictly ascending");
+}
+
+DevCsr upload_csr(DevScratch& B, const amgps_csr& A, cudaStream_t s) {
+  DevCsr d;
+  d.n_rows = A.n_rows;
+  d.n_cols = A.n_cols;
+  d.nnz = A.nnz;
+  d.rowptr = B.upload(A.rowptr, (size_t)A.n_rows + 1, s);
+  d.col = B.upload(A.col, (size_t)A.nnz, s);
+  d.val = B.upload(A.val, (size_t)A.nnz, s);
+  return d;
+}
+
+void check_dev_err(int* derr, cudaStream_t s, const char* what) {
+  check_launch();
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, derr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  REQ(h == 0, AMGPS_E_ARG, what);
+}
+
+// rowptr from per-row counts (prefix on the host); allocates col and val
+DevCsr from_counts(DevScratch& B, const int32_t* dcnt, int64_t rows, int64_t cols,
+                   cudaStream_t s) {
+  std::vector<int32_t> h((size_t)rows);
+  if (rows) CK(cudaMemcpyAsync(h.data(), dcnt, rows * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<int32_t> rp((size_t)rows + 1, 0);
+  int64_t acc = 0;
+  for (int64_t i = 0; i < rows; ++i) {
+    acc += h[i];
+    REQ(acc < (int64_t(1) << 31), AMGPS_E_ARG, "sparse product exceeds 2^31 entries");
+    rp[i + 1] = (int32_t)acc;
+  }
+  DevCsr C;
+  C.n_rows = rows;
+  C.n_cols = cols;
+  C.nnz = acc;
+  C.rowptr = B.upload(rp.data(), rp.size(), s);
+  C.col = B.alloc<int32_t>(acc);
+  C.val = B.alloc<double>(acc);
+  return C;
+}
+
+DevCsr dev_spgemm(amgps_ctx* c, DevScratch& B, const DevCsr& X, const DevCsr& Y, int* derr) {
+  cudaStream_t s = c->stream;
+  int32_t* cnt = B.alloc<int32_t>(X.n_rows);
+  launch_spgemm(X, Y, cnt, DevCsr{}, derr, false, c->nsm, s);
+  check_dev_err(derr, s, "sparse product: a row has more than 768 distinct columns");
+  DevCsr C = from_counts(B, cnt, X.n_rows, Y.n_cols, s);
+  launch_spgemm(X, Y, nullptr, C, derr, true, c->nsm, s);
+  check_dev_err(derr, s, "sparse product: numeric pass failed");
+  return C;
+}
+
+DevCsr dev_transpose(amgps_ctx* c, DevScratch& B, const DevCsr& M, int* derr) {
+  cudaStream_t s = c->stream;
+  int32_t* cnt = B.alloc<int32_t>(M.n_cols);
+  CK(cudaMemsetAsync(cnt, 0, M.n_cols * sizeof(int32_t), s));
+  launch_col_count(M.nnz, M.col, cnt, s);
+  check_launch();
+  DevCsr T = from_counts(B, cnt, M.n_cols, M.n_rows, s);
+  int32_t* cursor = B.alloc<int32_t>(M.n_cols);
+  CK(cudaMemcpyAsync(cursor, T.rowptr, M.n_cols * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  launch_transpose_fill(M, cursor, T, s);
+  launch_sort_rows(T, derr, c->nsm, s);
+  check_dev_err(derr, s, "transpose: a row has more than 768 entries");
+  return T;
+}
+
+DevCsr dev_galerkin(amgps_ctx* c, DevScratch& B, const DevCsr& A, const DevCsr& P, int* derr) {
+  const DevCsr AP = dev_spgemm(c, B, A, P, derr);
+  const DevCsr R = dev_transpose(c, B, P, derr);
+  return dev_spgemm(c, B, R, AP, derr);
+}
+
+void download_csr(const DevCsr& M, amgps_csr_buf* out, cudaStream_t s) {
+  amgps_csr_buf o{};
+  o.n_rows = M.n_rows;
+  o.n_cols = M.n_cols;
+  o.nnz = M.nnz;
+  o.rowptr = (int32_t*)std::malloc(((size_t)M.n_rows + 1) * sizeof(int32_t));
+  o.col = (int32_t*)std::malloc(std::max<size_t>(M.nnz, 1) * sizeof(int32_t));
+  o.val = (double*)std::malloc(std::max<size_t>(M.nnz, 1) * sizeof(double));
+  if (!o.rowptr || !o.col || !o.val) {
+    std::free(o.rowptr);
+    std::free(o.col);
+    std::free(o.val);
+    throw std::bad_alloc();
+  }
+  CK(cudaMemcpyAsync(o.rowptr, M.rowptr, (M.n_rows + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  if (M.nnz) {
+    CK(cudaMemcpyAsync(o.col, M.col, M.nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(o.val, M.val, M.nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  const cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    std::free(o.rowptr);
+    std::free(o.col);
+    std::free(o.val);
+    throw Fail{AMGPS_E_CUDA, std::string("download: ") + cudaGetErrorString(e)};
+  }
+  *out = o;
+}
+
+}  // namespace
+
 extern "C" {
 
 int amgps_version(void) { return 1; }
@@ -1304,11 +1502,6 @@ amgps_status amgps_hierarchy_load(amgps_ctx* c, int n_levels, const amgps_csr* A
       validate_csr(P[l], "P", false);
       REQ(P[l].n_rows == A[l].n_rows && P[l].n_cols == A[l + 1].n_rows, AMGPS_E_ARG,
           "P dimensions do not match A_l / A_{l+1}");
-      for (int64_t i = 0; i < P[l].n_rows; ++i) {
-        REQ(P[l].rowptr[i + 1] - P[l].rowptr[i] == 1, AMGPS_E_ARG,
-            "P is not an unsmoothed aggregation (one entry per row)");
-        REQ(P[l].val[P[l].rowptr[i]] == 1.0, AMGPS_E_ARG, "P entries must equal 1");
-      }
     }
     REQ(A[n_levels - 1].n_rows <= 1024, AMGPS_E_ARG, "coarsest level larger than 1024 rows");
     enter(c);
@@ -1391,9 +1584,15 @@ amgps_status amgps_hierarchy_load(amgps_ctx* c, int n_levels, const amgps_csr* A
       else if (prec == AMGPS_F32) launch_l1diag<float, float>(devmat<float>(L), (float*)L.dinv, c->stream);
       else launch_l1diag<__nv_bfloat16, float>(devmat<__nv_bfloat16>(L), (float*)L.dinv, c->stream);
       check_launch();
-      // aggregation maps: agg[i] and the children lists of every coarse row
       const amgps_csr& Pl = P[l];
       const int64_t nc = Pl.n_cols;
+      L.nc = nc;
+      L.spec = Spec{};
+      if (!is_aggregation(Pl)) {
+        load_general_transfer(c, L, Pl);
+        continue;
+      }
+      // aggregation maps: agg[i] and the children lists of every coarse row
       std::vector<int32_t> agg(L.n), cptr(nc + 1, 0), cidx(L.n);
       for (int64_t i = 0; i < L.n; ++i) {
         agg[i] = Pl.col[Pl.rowptr[i]];
@@ -1405,11 +1604,9 @@ amgps_status amgps_hierarchy_load(amgps_ctx* c, int n_levels, const amgps_csr* A
       }
       std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
       for (int64_t i = 0; i < L.n; ++i) cidx[fill[agg[i]]++] = (int32_t)i;
-      L.nc = nc;
       L.agg = dupload(c, agg.data(), agg.size());
       L.cptr = dupload(c, cptr.data(), cptr.size());
       L.cidx = dupload(c, cidx.data(), cidx.size());
-      L.spec = Spec{};
     }
     const int64_t n0 = c->lv[0].n;
     c->pr = (double*)dalloc(c, n0 * sizeof(double));
@@ -1894,6 +2091,101 @@ amgps_status amgps_profile_read(amgps_ctx* c, int cls, int reset, int64_t* launc
       c->prof_ms[cls] = 0.0;
       c->prof_bytes[cls] = 0.0;
     }
+  });
+}
+
+void amgps_csr_buf_free(amgps_csr_buf* m) {
+  if (!m) return;
+  std::free(m->rowptr);
+  std::free(m->col);
+  std::free(m->val);
+  *m = amgps_csr_buf{};
+}
+
+amgps_status amgps_galerkin(amgps_ctx* c, const amgps_csr* A, const amgps_csr* P,
+                            amgps_csr_buf* Ac) {
+  return guard(c, [&] {
+    REQ(c && A && P && Ac, AMGPS_E_ARG, "null argument");
+    validate_csr(*A, "A", true);
+    validate_csr(*P, "P", false);
+    REQ(P->n_rows == A->n_rows, AMGPS_E_ARG, "P rows must equal A rows");
+    require_sorted_rows(*P, "P");
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = c->stream;
+    DevScratch B;
+    int* derr = B.alloc<int>(1);
+    CK(cudaMemsetAsync(derr, 0, sizeof(int), s));
+    const DevCsr dA = upload_csr(B, *A, s), dP = upload_csr(B, *P, s);
+    download_csr(dev_galerkin(c, B, dA, dP, derr), Ac, s);
+  });
+}
+
+amgps_status amgps_sa_level(amgps_ctx* c, const amgps_csr* A, const int32_t* agg,
+                            int64_t n_coarse, double* omega, amgps_csr_buf* P_out,
+                            amgps_csr_buf* Ac_out) {
+  return guard(c, [&] {
+    REQ(c && A && agg && omega && P_out && Ac_out, AMGPS_E_ARG, "null argument");
+    validate_csr(*A, "A", true);
+    REQ(n_coarse >= 1 && n_coarse <= A->n_rows, AMGPS_E_ARG, "n_coarse out of range");
+    for (int64_t i = 0; i < A->n_rows; ++i) {
+      bool found = false;
+      for (int e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e)
+        if (A->col[e] == i) {
+          REQ(A->val[e] > 0.0, AMGPS_E_NOT_SPD, "non-positive diagonal entry");
+          found = true;
+        }
+      REQ(found, AMGPS_E_NOT_SPD, "missing diagonal entry");
+    }
+    std::vector<int32_t> used((size_t)n_coarse, 0);
+    for (int64_t i = 0; i < A->n_rows; ++i) {
+      REQ(agg[i] >= 0 && agg[i] < n_coarse, AMGPS_E_ARG, "aggregate index out of range");
+      used[agg[i]] = 1;
+    }
+    for (int64_t I = 0; I < n_coarse; ++I)
+      REQ(used[I], AMGPS_E_ARG, "empty aggregate (coarse index without a fine point)");
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = c->stream;
+    const int64_t n = A->n_rows;
+    DevScratch B;
+    int* derr = B.alloc<int>(1);
+    CK(cudaMemsetAsync(derr, 0, sizeof(int), s));
+    const DevCsr dA = upload_csr(B, *A, s);
+    int32_t* dagg = B.upload(agg, (size_t)n, s);
+    // omega = 4 / (3 lambda), lambda = max_i sum_j |a_ij| / a_ii
+    double* diag = B.alloc<double>(n);
+    double* part = B.alloc<double>((size_t)c->nsm * 4);
+    const int np = launch_rowstat(dA, diag, part, c->nsm, s);
+    check_launch();
+    std::vector<double> hp(np);
+    CK(cudaMemcpyAsync(hp.data(), part, np * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double lam = 0.0;
+    for (double v : hp) lam = std::max(lam, v);
+    REQ(std::isfinite(lam) && lam > 0.0, AMGPS_E_NAN, "row-sum bound not finite");
+    const double om = 4.0 / (3.0 * lam);
+    // P_hat (one unit entry per row), A P_hat, then P in place
+    std::vector<int32_t> iota((size_t)n + 1);
+    for (int64_t i = 0; i <= n; ++i) iota[i] = (int32_t)i;
+    std::vector<double> ones((size_t)n, 1.0);
+    DevCsr Ph;
+    Ph.n_rows = n;
+    Ph.n_cols = n_coarse;
+    Ph.nnz = n;
+    Ph.rowptr = B.upload(iota.data(), iota.size(), s);
+    Ph.col = dagg;
+    Ph.val = B.upload(ones.data(), ones.size(), s);
+    const DevCsr P = dev_spgemm(c, B, dA, Ph, derr);
+    launch_sa_combine(P, dagg, diag, om, s);
+    check_launch();
+    const DevCsr Ac = dev_galerkin(c, B, dA, P, derr);
+    download_csr(P, P_out, s);
+    try {
+      download_csr(Ac, Ac_out, s);
+    } catch (...) {
+      amgps_csr_buf_free(P_out);
+      throw;
+    }
+    *omega = om;
   });
 }
 

@@ -255,4 +255,29 @@ template void launch_convert<double, float>(int64_t, const double*, float*, cuda
 template void launch_convert<float, double>(int64_t, const float*, double*, cudaStream_t);
 template void launch_convert<double, double>(int64_t, const double*, double*, cudaStream_t);
 
+// Transfers through a general prolongator (explicit SELL-32, FP64 values):
+// y = M u (add = 0) or y += M u (add = 1), one warp per slice.  M = R = P^T
+// restricts (b_c = P^T r), M = P prolongs (x += P x_c).
+template <class XT>
+__global__ void __launch_bounds__(kBlock) k_xfer(const DevMat<double> M, const XT* __restrict__ u,
+                                                 XT* __restrict__ y, int add) {
+  const int lane = threadIdx.x & 31;
+  const int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (s >= M.nslices) return;
+  const int64_t row = s * kSlice + lane;
+  const XT init = (add && row < M.n) ? y[row] : XT(0);
+  const XT t = row_spmv<1, double, XT>(M, s, lane, row, u, init);
+  if (row < M.n) y[row] = t;
+}
+
+template <class XT>
+void launch_xfer(const DevMat<double>& M, const XT* u, XT* y, int add, cudaStream_t s) {
+  if (M.nslices == 0) return;
+  const unsigned grid = (unsigned)((M.nslices + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  k_xfer<XT><<<grid, kBlock, 0, s>>>(M, u, y, add);
+  count_launch();
+}
+template void launch_xfer<double>(const DevMat<double>&, const double*, double*, int, cudaStream_t);
+template void launch_xfer<float>(const DevMat<double>&, const float*, float*, int, cudaStream_t);
+
 }  // namespace amgps

@@ -270,8 +270,7 @@ def test_status_codes(torch_cuda):
     with pytest.raises(AmgpsError) as e:
         S.load([bad] + H.A[1:], H.P)
     assert e.value.name == "AMGPS_E_NOT_SPD"
-    P2 = H.P[0].copy().astype(np.float64)
-    P2.data[0] = 2.0
+    P2 = sp.csr_matrix(H.P[0])[:, :-1]  # one coarse column short of A_1
     with pytest.raises(AmgpsError) as e:
         S.load(H.A, [P2])
     assert e.value.name == "AMGPS_E_ARG"

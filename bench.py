@@ -37,6 +37,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "PCG-AMG time-to-1e-8 and smoother HBM GB/s: plain FP64 vs learned/mixed form"
 GOLDEN_ITERS = os.path.join(ROOT, "tests", "golden", "oracle_pcg_iterations.json")
+GOLDEN_SA = os.path.join(ROOT, "tests", "golden", "oracle_sa_pcg_iterations.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_poisson256_traffic.json")
 STEP_SOURCES = [os.path.join(ROOT, "paper_2407_09848_gb300", "csrc", f)
                 for f in ("kernels_tma.cu", "kernels_smooth.cu", "kernels_common.cuh",
@@ -262,6 +263,48 @@ def run_mixed_c2(a, torch):
     return {"workload": "varcoef192^3 sigma1 ell8, CHEB4_OPT k4, rtol 1e-8", **out}
 
 
+def run_sa_c1(a, torch):
+    """256^3 Poisson with a smoothed-aggregation hierarchy built on the GPU
+    (amgps_sa_level: SA prolongator + Galerkin SpGEMM per level) against the
+    unsmoothed-aggregation hierarchy of the headline run; FP64, CHEB4_OPT k4
+    and l1-Jacobi k4."""
+    import numpy as np
+    from paper_2407_09848_gb300 import problems as pr
+    from paper_2407_09848_gb300.amgps import Solver
+    st = pr.poisson(a.grid)
+    levels = pr.geometric_aggregates(st.shape, coarse_max=512)
+    A0 = pr.to_csr(st)
+    builder = Solver()
+    t0 = time.perf_counter()
+    As, Ps, oms = builder.sa_hierarchy(A0, levels)
+    t_build = time.perf_counter() - t0
+    builder.close()
+    t0 = time.perf_counter()
+    S = Solver().load(As, Ps, prec="f64")
+    t_load = time.perf_counter() - t0
+    b = pr.rhs_uniform(A0.shape[0], seed=0)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.empty_like(bd)
+    out = {"workload": f"poisson{a.grid}^3 smoothed aggregation, rtol {a.rtol}",
+           "levels": [m.shape[0] for m in As], "nnz_per_row": [round(m.nnz / m.shape[0], 1) for m in As],
+           "operator_complexity": round(sum(m.nnz for m in As) / As[0].nnz, 3),
+           "omega": [round(o, 6) for o in oms],
+           "setup_s": {"sa_levels_on_gpu_incl_transfers": round(t_build, 3), "load": round(t_load, 3)}}
+    gold = {}
+    if os.path.exists(GOLDEN_SA):
+        with open(GOLDEN_SA) as f:
+            gold = {(r["grid"], r["kind"], r["degree"]): r["iterations"] for r in json.load(f)["runs"]}
+    for kind, k in (("cheb4_opt", 4), ("l1jacobi", 4)):
+        S.set_smoother(-1, kind, k)
+        it, ms, rel = timed_solve(S, bd, x, a.rtol, torch)
+        true = float(np.linalg.norm(b - A0 @ x.cpu().numpy()) / np.linalg.norm(b))
+        out[f"{kind}_k{k}"] = {"iterations": it, "ms": round(ms, 3), "relres": rel,
+                               "true_relres": true,
+                               "oracle_iterations": gold.get((a.grid, kind, k))}
+    S.close()
+    return out
+
+
 def run_learned_c4(a, torch):
     """256^3 log-normal (sigma 2, ell 16) and anisotropic (eps 1e-3 in z):
     plain FP64 with the optimal 4th-kind weights vs learned weights with
@@ -473,7 +516,8 @@ def run_ours(a):
     extras = None
     if not a.no_extras and rank == 0:
         S.close()
-        extras = {"mixed_c2": run_mixed_c2(a, torch), "learned_c4": run_learned_c4(a, torch)}
+        extras = {"mixed_c2": run_mixed_c2(a, torch), "learned_c4": run_learned_c4(a, torch),
+                  "smoothed_aggregation": run_sa_c1(a, torch)}
 
     # ---- CPU baseline: the oracle on a bounded sample ----
     cpu = None

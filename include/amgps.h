@@ -125,7 +125,8 @@ void amgps_csr_buf_free(amgps_csr_buf* m);
  * device.  A: square CSR; P: n_rows(A) x n_c CSR whose rows have strictly
  * ascending columns.  Every entry of the product is summed in a fixed order,
  * so repeated calls give identical bits.  AMGPS_E_ARG for malformed input or
- * when a row of an intermediate product exceeds 768 distinct columns;
+ * when a row of an intermediate product (or of P^T) exceeds 6144 distinct
+ * columns;
  * AMGPS_E_NOMEM when device scratch cannot be allocated.  Synchronous; needs
  * no loaded hierarchy.  *Ac receives library-allocated host CSR. */
 amgps_status amgps_galerkin(amgps_ctx* ctx, const amgps_csr* A, const amgps_csr* P,

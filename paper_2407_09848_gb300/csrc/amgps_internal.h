@@ -64,7 +64,13 @@ struct StepArgs {
   bool write_r = false;
   const int32_t* slices = nullptr;  // optional list of slices to process (null: all)
   int64_t nlist = 0;                // entries in `slices`
+  int split = 1;  // > 1: one block of `split` warps per slice, entries split among them
 };
+
+// Warps per slice for a level whose rows are wide (the split form of the
+// step and transfer kernels): 1 below 48 stored entries per row on average,
+// else the power of two nearest (avg / 32), at most kMaxSplit.
+constexpr int kMaxSplit = 16;
 
 // ---- TMA-fed step (kernels_tma.cu) ----
 // A tile is `rows` consecutive rows (a multiple of 32 slices' worth, up to
@@ -113,9 +119,10 @@ void launch_aggregate(const int32_t* cptr, const int32_t* cidx, int64_t nc, cons
                       cudaStream_t s);
 template <class XT>
 void launch_prolong(int64_t n, const int32_t* agg, const XT* ec, XT* x, cudaStream_t s);
-// general prolongator transfers: y = M u (add = 0) or y += M u (add = 1)
+// general prolongator transfers: y = M u (add = 0) or y += M u (add = 1);
+// split > 1: one block of `split` warps per slice
 template <class XT>
-void launch_xfer(const DevMat<double>& M, const XT* u, XT* y, int add, cudaStream_t s);
+void launch_xfer(const DevMat<double>& M, const XT* u, XT* y, int add, int split, cudaStream_t s);
 // out = x + y ; out = x - y ; out = (factor / *s_dev) * x
 template <class XT>
 void launch_add(int64_t n, const XT* x, const XT* y, XT* out, cudaStream_t s);

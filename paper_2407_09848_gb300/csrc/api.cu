@@ -123,6 +123,8 @@ struct Level {
   bool xfer_general = false;
   DevMat<double> Pm, Rm;
   int64_t xfer_stored = 0;  // stored entries of P and R together
+  int psplit = 1, rsplit = 1;
+  int split = 1;  // warps per slice of the generic step kernel (wide rows)
   void* dinv = nullptr;   // 1 / M_i
   void *b = nullptr, *x = nullptr, *r = nullptr, *za = nullptr, *zb = nullptr, *xb = nullptr;
   double* ainv = nullptr;
@@ -163,6 +165,17 @@ void validate_csr(const amgps_csr& A, const char* what, bool square) {
     REQ(A.col[e] >= 0 && A.col[e] < A.n_cols, AMGPS_E_ARG, w + ": column index out of range");
     REQ(std::isfinite(A.val[e]), AMGPS_E_ARG, w + ": non-finite value");
   }
+}
+
+// Warps per slice for the split kernels: 1 while rows average under 48
+// stored entries, else the power of two nearest avg / 32, at most kMaxSplit.
+int split_for(int64_t stored, int64_t nslices) {
+  if (nslices == 0) return 1;
+  const double avg = (double)stored / ((double)nslices * kSlice);
+  if (avg < 48.0) return 1;
+  int g = 1;
+  while (g < kMaxSplit && 2.0 * g <= avg / 32.0 * 1.41421356) g *= 2;
+  return std::max(g, 2);
 }
 
 // allow_uniform = false keeps every slice explicit (required for rectangular
@@ -637,6 +650,7 @@ struct Engine {
   // One fused step on level L: the TMA-fed kernel over its tiles plus the
   // direct kernel over the remaining slices, or the direct kernel alone.
   static void run_step(amgps_ctx* c, const Level& L, StepArgs<VT, XT> a, cudaStream_t s) {
+    a.split = L.split;
     if (c->use_tma && L.ntma > 0 &&
         launch_step_tma<VT, XT>(a, L.plan, L.tma_tiles, L.ntma, L.tma_grid, c->dscal + S_ERR, s)) {
       if (L.ngen > 0) {
@@ -777,7 +791,7 @@ struct Engine {
       a.fam = FAM_RES;
       a.init = true;
       run_step(c, L, a, s);
-      if (L.xfer_general) launch_xfer<XT>(L.Rm, (const XT*)L.r, (XT*)C.b, 0, s);
+      if (L.xfer_general) launch_xfer<XT>(L.Rm, (const XT*)L.r, (XT*)C.b, 0, L.rsplit, s);
       else launch_aggregate<XT>(L.cptr, L.cidx, L.nc, (const XT*)L.r, (XT*)C.b, s);
       ps.done();
     }
@@ -787,7 +801,7 @@ struct Engine {
     } else {
       vcycle_level(c, l + 1, (const XT*)C.b, (XT*)C.x, record);
     }
-    if (L.xfer_general) launch_xfer<XT>(L.Pm, (const XT*)C.x, x, 1, s);
+    if (L.xfer_general) launch_xfer<XT>(L.Pm, (const XT*)C.x, x, 1, L.psplit, s);
     else launch_prolong<XT>(L.n, L.agg, (const XT*)C.x, x, s);
     if (record) CK(cudaMemcpyAsync(L.bx2, x, L.n * sizeof(XT), cudaMemcpyDeviceToDevice, s));
     smooth(c, l, cf, b, x, false);
@@ -899,11 +913,11 @@ struct Engine {
     // post-smoother x = S(b, x2): t1 = dL/db (post part), t2 = dL/dx2
     smooth_bwd(c, l, cf, bl, (const XT*)L.bx2, xbar, t1, t2, l * 32);
     // x2 = x1 + P xc ; xc = V_{l+1}(P^T (b - A x1))
-    if (L.xfer_general) launch_xfer<XT>(L.Rm, (const XT*)t2, (XT*)C.bgx, 0, s);
+    if (L.xfer_general) launch_xfer<XT>(L.Rm, (const XT*)t2, (XT*)C.bgx, 0, L.rsplit, s);
     else launch_aggregate<XT>(L.cptr, L.cidx, L.nc, t2, (XT*)C.bgx, s);
     vcycle_bwd(c, l + 1, (const XT*)C.b, (const XT*)C.bgx, (XT*)C.bgb);
     CK(cudaMemsetAsync(t3, 0, L.n * sizeof(XT), s));
-    if (L.xfer_general) launch_xfer<XT>(L.Pm, (const XT*)C.bgb, t3, 1, s);  // dL/dres = P dL/db_c
+    if (L.xfer_general) launch_xfer<XT>(L.Pm, (const XT*)C.bgb, t3, 1, L.psplit, s);  // dL/dres = P dL/db_c
     else launch_prolong<XT>(L.n, L.agg, (const XT*)C.bgb, t3, s);
     launch_add<XT>(L.n, t1, t3, gbout, s);
     {
@@ -1250,8 +1264,9 @@ void load_general_transfer(amgps_ctx* c, Level& L, const amgps_csr& P) {
       rval[f] = P.val[e];
     }
   const amgps_csr R{nc, n, P.nnz, rptr.data(), rcol.data(), rval.data()};
-  auto put = [&](const amgps_csr& M, DevMat<double>& d) {
+  auto put = [&](const amgps_csr& M, DevMat<double>& d, int& split) {
     HostSell h = build_sell(M, false);
+    split = split_for(h.stored, h.nslices);
     d.n = M.n_rows;
     d.nslices = h.nslices;
     d.sd = dupload(c, h.sd.data(), h.sd.size());
@@ -1261,8 +1276,8 @@ void load_general_transfer(amgps_ctx* c, Level& L, const amgps_csr& P) {
     d.off = dupload(c, &zero, 1);  // never read: every slice is explicit
     L.xfer_stored += h.stored;
   };
-  put(P, L.Pm);
-  put(R, L.Rm);
+  put(P, L.Pm, L.psplit);
+  put(R, L.Rm, L.rsplit);
   L.xfer_general = true;
 }
 
@@ -1315,12 +1330,18 @@ DevCsr upload_csr(DevScratch& B, const amgps_csr& A, cudaStream_t s) {
   return d;
 }
 
-void check_dev_err(int* derr, cudaStream_t s, const char* what) {
+// reads and clears the device error flag of the set-up kernels
+bool dev_err_set(int* derr, cudaStream_t s) {
   check_launch();
   int h = 0;
   CK(cudaMemcpyAsync(&h, derr, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  REQ(h == 0, AMGPS_E_ARG, what);
+  if (h) CK(cudaMemsetAsync(derr, 0, sizeof(int), s));
+  return h != 0;
+}
+
+void check_dev_err(int* derr, cudaStream_t s, const char* what) {
+  REQ(!dev_err_set(derr, s), AMGPS_E_ARG, what);
 }
 
 // rowptr from per-row counts (prefix on the host); allocates col and val
@@ -1349,10 +1370,16 @@ DevCsr from_counts(DevScratch& B, const int32_t* dcnt, int64_t rows, int64_t col
 DevCsr dev_spgemm(amgps_ctx* c, DevScratch& B, const DevCsr& X, const DevCsr& Y, int* derr) {
   cudaStream_t s = c->stream;
   int32_t* cnt = B.alloc<int32_t>(X.n_rows);
-  launch_spgemm(X, Y, cnt, DevCsr{}, derr, false, c->nsm, s);
-  check_dev_err(derr, s, "sparse product: a row has more than 768 distinct columns");
+  // narrow form first; the wide form when some row exceeds its limit
+  bool wide = false;
+  launch_spgemm(X, Y, cnt, DevCsr{}, derr, false, false, c->nsm, s);
+  if (dev_err_set(derr, s)) {
+    wide = true;
+    launch_spgemm(X, Y, cnt, DevCsr{}, derr, false, true, c->nsm, s);
+    check_dev_err(derr, s, "sparse product: a row has more than 6144 distinct columns");
+  }
   DevCsr C = from_counts(B, cnt, X.n_rows, Y.n_cols, s);
-  launch_spgemm(X, Y, nullptr, C, derr, true, c->nsm, s);
+  launch_spgemm(X, Y, nullptr, C, derr, true, wide, c->nsm, s);
   check_dev_err(derr, s, "sparse product: numeric pass failed");
   return C;
 }
@@ -1367,8 +1394,11 @@ DevCsr dev_transpose(amgps_ctx* c, DevScratch& B, const DevCsr& M, int* derr) {
   int32_t* cursor = B.alloc<int32_t>(M.n_cols);
   CK(cudaMemcpyAsync(cursor, T.rowptr, M.n_cols * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   launch_transpose_fill(M, cursor, T, s);
-  launch_sort_rows(T, derr, c->nsm, s);
-  check_dev_err(derr, s, "transpose: a row has more than 768 entries");
+  launch_sort_rows(T, derr, false, c->nsm, s);
+  if (dev_err_set(derr, s)) {  // rows beyond the narrow limit were left unsorted
+    launch_sort_rows(T, derr, true, c->nsm, s);
+    check_dev_err(derr, s, "transpose: a row has more than 6144 entries");
+  }
   return T;
 }
 
@@ -1538,6 +1568,7 @@ amgps_status amgps_hierarchy_load(amgps_ctx* c, int n_levels, const amgps_csr* A
         if (l > 0) continue;
       }
       HostSell h = build_sell(A[l]);
+      L.split = split_for(h.stored, h.nslices);
       L.nslices = h.nslices;
       L.stored = h.stored;
       L.explicit_entries = h.explicit_entries;

@@ -24,22 +24,22 @@ __device__ __forceinline__ T absv(T v) { return v < T(0) ? -v : v; }
 // padding and clamped, in-range columns.  FP64 arithmetic is the scarce
 // resource on this GPU (its FP64 pipe issues about 2 FMAs per clock per SM),
 // so the row costs exactly one multiply-add per stored entry and nothing else.
+// Entries k in [k0, k1) of row `row` of slice s: init + SIGN * sum a_k u_{c_k}.
 template <int SIGN, class VT, class XT>
-__device__ __forceinline__ XT row_spmv(const DevMat<VT>& A, int64_t s, int lane, int64_t row,
-                                       const XT* __restrict__ u, XT init) {
+__device__ __forceinline__ XT row_spmv_range(const DevMat<VT>& A, int64_t s, int lane, int64_t row,
+                                             const XT* __restrict__ u, XT init, int k0, int k1) {
   const SliceDesc d = A.sd[s];
-  const int w = d.w;
   const int64_t nm1 = A.n - 1;
   XT t = init;
-  for (int k0 = 0; k0 < w; k0 += 8) {
+  for (int kb = k0; kb < k1; kb += 8) {
     XT a[8];
     int64_t c[8];
 #pragma unroll
     for (int kk = 0; kk < 8; ++kk) {
-      const int k = k0 + kk;
+      const int k = kb + kk;
       a[kk] = XT(0);
       c[kk] = 0;
-      if (k < w) {
+      if (k < k1) {
         const int64_t e = d.vbase + (int64_t)k * kSlice + lane;
         a[kk] = XT(ldval(A.val + e));
         if (d.cref >= 0) {
@@ -52,9 +52,16 @@ __device__ __forceinline__ XT row_spmv(const DevMat<VT>& A, int64_t s, int lane,
     }
 #pragma unroll
     for (int kk = 0; kk < 8; ++kk)
-      if (k0 + kk < w) t = fma(SIGN > 0 ? a[kk] : -a[kk], __ldg(u + c[kk]), t);
+      if (kb + kk < k1) t = fma(SIGN > 0 ? a[kk] : -a[kk], __ldg(u + c[kk]), t);
   }
   return t;
+}
+
+// The whole row: entries 0 .. w-1 of the slice.
+template <int SIGN, class VT, class XT>
+__device__ __forceinline__ XT row_spmv(const DevMat<VT>& A, int64_t s, int lane, int64_t row,
+                                       const XT* __restrict__ u, XT init) {
+  return row_spmv_range<SIGN, VT, XT>(A, s, lane, row, u, init, 0, A.sd[s].w);
 }
 
 // The SpMV of one smoother step is accumulated as init + SIGN * (A u):

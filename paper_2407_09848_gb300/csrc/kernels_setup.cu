@@ -11,20 +11,28 @@
 // k along row i of A, whatever the scheduling: the product is bitwise
 // reproducible.  A symbolic pass (FILL = false) counts the distinct columns
 // per row; the numeric pass (FILL = true) writes each row sorted by column.
-// Rows with more than kRowMax distinct columns set *err and are not written.
+// Two table sizes: the narrow form (1024 slots, rows up to kRowMaxNarrow,
+// two warps per block) and the wide form (8192 slots, rows up to
+// kRowMaxWide, one warp per block in opt-in shared memory) that the host
+// falls back to when a narrow pass reports an over-long row through *err.
 #include "kernels_common.cuh"
 #include "setup.h"
 
 namespace amgps {
 namespace {
 
-constexpr int kHash = 1024;     // hash slots per warp (power of two)
-constexpr int kGemmWarps = 2;   // warps per block
-static_assert(kRowMax < kHash, "hash table must exceed the row limit");
-
-__device__ __forceinline__ uint32_t slot_of(int32_t j) {
-  return ((uint32_t)j * 2654435761u) >> 22;  // top 10 bits: [0, 1024)
-}
+template <int HASH, int ROWMAX, int WARPS>
+struct GemmShape {
+  static constexpr int kHash = HASH, kRowMax = ROWMAX, kWarps = WARPS;
+  static constexpr int kLog2 = HASH == 1024 ? 10 : 13;
+  static_assert((1 << kLog2) == HASH, "hash size must be 1024 or 8192");
+  static_assert(ROWMAX < HASH, "hash table must exceed the row limit");
+  // per warp: vals[HASH], lval[ROWMAX] (doubles first), keys[HASH], lkey[ROWMAX]
+  static constexpr size_t kWarpBytes = (size_t)(HASH + ROWMAX) * 12;
+  static constexpr size_t kSmem = kWarpBytes * WARPS;
+};
+using Narrow = GemmShape<1024, kRowMaxNarrow, 2>;
+using Wide = GemmShape<8192, kRowMaxWide, 1>;
 
 __device__ __forceinline__ int warp_sum_int(int v) {
 #pragma unroll
@@ -32,20 +40,20 @@ __device__ __forceinline__ int warp_sum_int(int v) {
   return v;
 }
 
-template <bool FILL>
-__global__ void __launch_bounds__(32 * kGemmWarps) k_spgemm(const DevCsr A, const DevCsr B,
-                                                           int32_t* __restrict__ counts,
-                                                           const DevCsr C, int* err) {
-  __shared__ int32_t skey[kGemmWarps][kHash];
-  __shared__ double sval[kGemmWarps][kHash];
-  __shared__ int32_t lkey[kGemmWarps][kRowMax];
-  __shared__ double lval[kGemmWarps][kRowMax];
+template <class G, bool FILL>
+__global__ void __launch_bounds__(32 * G::kWarps) k_spgemm(const DevCsr A, const DevCsr B,
+                                                          int32_t* __restrict__ counts,
+                                                          const DevCsr C, int* err) {
+  extern __shared__ double smem_d[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int32_t* key = skey[w];
-  double* val = sval[w];
-  const int64_t stride = (int64_t)gridDim.x * kGemmWarps;
-  for (int64_t i = (int64_t)blockIdx.x * kGemmWarps + w; i < A.n_rows; i += stride) {
-    for (int h = lane; h < kHash; h += 32) {
+  double* val = smem_d + (size_t)w * (G::kHash + G::kRowMax);
+  double* lval = val + G::kHash;
+  int32_t* key = (int32_t*)(smem_d + (size_t)G::kWarps * (G::kHash + G::kRowMax)) +
+                 (size_t)w * (G::kHash + G::kRowMax);
+  int32_t* lkey = key + G::kHash;
+  const int64_t stride = (int64_t)gridDim.x * G::kWarps;
+  for (int64_t i = (int64_t)blockIdx.x * G::kWarps + w; i < A.n_rows; i += stride) {
+    for (int h = lane; h < G::kHash; h += 32) {
       key[h] = -1;
       if (FILL) val[h] = 0.0;
     }
@@ -56,13 +64,13 @@ __global__ void __launch_bounds__(32 * kGemmWarps) k_spgemm(const DevCsr A, cons
       const double a = A.val[e];
       for (int f = B.rowptr[k] + lane; f < B.rowptr[k + 1] && !over; f += 32) {
         const int32_t j = B.col[f];
-        uint32_t h = slot_of(j);
+        uint32_t h = ((uint32_t)j * 2654435761u) >> (32 - G::kLog2);
         int probes = 0;
         for (;;) {
           const int32_t prev = atomicCAS(&key[h], -1, j);
           if (prev == -1 || prev == j) break;
-          h = (h + 1) & (kHash - 1);
-          if (++probes == kHash) {
+          h = (h + 1) & (G::kHash - 1);
+          if (++probes == G::kHash) {
             over = true;
             break;
           }
@@ -72,9 +80,9 @@ __global__ void __launch_bounds__(32 * kGemmWarps) k_spgemm(const DevCsr A, cons
       __syncwarp();
     }
     int cnt = 0;
-    for (int h = lane; h < kHash; h += 32) cnt += key[h] >= 0;
+    for (int h = lane; h < G::kHash; h += 32) cnt += key[h] >= 0;
     cnt = warp_sum_int(cnt);
-    over = __any_sync(0xffffffffu, over) || cnt > kRowMax;
+    over = __any_sync(0xffffffffu, over) || cnt > G::kRowMax;
     if (over) {
       if (lane == 0) atomicExch(err, 1);
       __syncwarp();
@@ -92,25 +100,25 @@ __global__ void __launch_bounds__(32 * kGemmWarps) k_spgemm(const DevCsr A, cons
     }
     // compact the occupied slots, then place each entry by its rank in column order
     int base = 0;
-    for (int h0 = 0; h0 < kHash; h0 += 32) {
+    for (int h0 = 0; h0 < G::kHash; h0 += 32) {
       const int h = h0 + lane;
       const bool occ = key[h] >= 0;
       const unsigned m = __ballot_sync(0xffffffffu, occ);
       if (occ) {
         const int pos = base + __popc(m & ((1u << lane) - 1u));
-        lkey[w][pos] = key[h];
-        lval[w][pos] = val[h];
+        lkey[pos] = key[h];
+        lval[pos] = val[h];
       }
       base += __popc(m);
     }
     __syncwarp();
     const int64_t out0 = C.rowptr[i];
     for (int q = lane; q < cnt; q += 32) {
-      const int32_t kq = lkey[w][q];
+      const int32_t kq = lkey[q];
       int rank = 0;
-      for (int t = 0; t < cnt; ++t) rank += lkey[w][t] < kq;
+      for (int t = 0; t < cnt; ++t) rank += lkey[t] < kq;
       C.col[out0 + rank] = kq;
-      C.val[out0 + rank] = lval[w][q];
+      C.val[out0 + rank] = lval[q];
     }
     __syncwarp();
   }
@@ -174,49 +182,74 @@ __global__ void __launch_bounds__(kBlock) k_transpose_fill(const DevCsr M, int32
 }
 
 // transpose, step 3: sort every row by column (warp per row, rank placement;
-// the columns of a row are distinct) -- makes the transpose deterministic
-__global__ void __launch_bounds__(32 * kGemmWarps) k_sort_rows(const DevCsr T, int* err) {
-  __shared__ int32_t lkey[kGemmWarps][kRowMax];
-  __shared__ double lval[kGemmWarps][kRowMax];
+// the columns of a row are distinct) -- makes the transpose deterministic.
+// Rows longer than the form's limit set *err and are left as they are.
+template <class G>
+__global__ void __launch_bounds__(32 * G::kWarps) k_sort_rows(const DevCsr T, int* err) {
+  extern __shared__ double smem_d[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * kGemmWarps;
-  for (int64_t i = (int64_t)blockIdx.x * kGemmWarps + w; i < T.n_rows; i += stride) {
+  double* lval = smem_d + (size_t)w * G::kRowMax;
+  int32_t* lkey = (int32_t*)(smem_d + (size_t)G::kWarps * G::kRowMax) + (size_t)w * G::kRowMax;
+  const int64_t stride = (int64_t)gridDim.x * G::kWarps;
+  for (int64_t i = (int64_t)blockIdx.x * G::kWarps + w; i < T.n_rows; i += stride) {
     const int32_t r0 = T.rowptr[i];
     const int m = T.rowptr[i + 1] - r0;
-    if (m > kRowMax) {
+    if (m > G::kRowMax) {
       if (lane == 0) atomicExch(err, 1);
       continue;
     }
     for (int q = lane; q < m; q += 32) {
-      lkey[w][q] = T.col[r0 + q];
-      lval[w][q] = T.val[r0 + q];
+      lkey[q] = T.col[r0 + q];
+      lval[q] = T.val[r0 + q];
     }
     __syncwarp();
     for (int q = lane; q < m; q += 32) {
-      const int32_t kq = lkey[w][q];
+      const int32_t kq = lkey[q];
       int rank = 0;
-      for (int t = 0; t < m; ++t) rank += lkey[w][t] < kq;
+      for (int t = 0; t < m; ++t) rank += lkey[t] < kq;
       T.col[r0 + rank] = kq;
-      T.val[r0 + rank] = lval[w][q];
+      T.val[r0 + rank] = lval[q];
     }
     __syncwarp();
   }
 }
 
-int gemm_grid(int64_t rows, int nsm) {
-  int64_t g = (rows + kGemmWarps - 1) / kGemmWarps;
+int gemm_grid(int64_t rows, int warps, int nsm) {
+  int64_t g = (rows + warps - 1) / warps;
   const int64_t cap = (int64_t)nsm * 16;
   return (int)std::max<int64_t>(1, std::min(g, cap));
+}
+
+// the wide forms need more than the default 48 KB of dynamic shared memory
+void wide_smem_optin() {
+  static uint64_t done = 0;  // one bit per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && (done >> dev & 1u)) return;
+  cudaFuncSetAttribute(k_spgemm<Wide, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)Wide::kSmem);
+  cudaFuncSetAttribute(k_spgemm<Wide, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)Wide::kSmem);
+  cudaFuncSetAttribute(k_sort_rows<Wide>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(Wide::kRowMax * 12));
+  if (dev < 64) done |= uint64_t(1) << dev;
 }
 
 }  // namespace
 
 void launch_spgemm(const DevCsr& A, const DevCsr& B, int32_t* counts, const DevCsr& C, int* err,
-                   bool fill, int nsm, cudaStream_t s) {
+                   bool fill, bool wide, int nsm, cudaStream_t s) {
   if (A.n_rows == 0) return;
-  const int g = gemm_grid(A.n_rows, nsm);
-  if (fill) k_spgemm<true><<<g, 32 * kGemmWarps, 0, s>>>(A, B, counts, C, err);
-  else k_spgemm<false><<<g, 32 * kGemmWarps, 0, s>>>(A, B, counts, C, err);
+  if (wide) {
+    wide_smem_optin();
+    const int g = gemm_grid(A.n_rows, Wide::kWarps, nsm);
+    if (fill) k_spgemm<Wide, true><<<g, 32 * Wide::kWarps, Wide::kSmem, s>>>(A, B, counts, C, err);
+    else k_spgemm<Wide, false><<<g, 32 * Wide::kWarps, Wide::kSmem, s>>>(A, B, counts, C, err);
+  } else {
+    const int g = gemm_grid(A.n_rows, Narrow::kWarps, nsm);
+    if (fill) k_spgemm<Narrow, true><<<g, 32 * Narrow::kWarps, Narrow::kSmem, s>>>(A, B, counts, C, err);
+    else k_spgemm<Narrow, false><<<g, 32 * Narrow::kWarps, Narrow::kSmem, s>>>(A, B, counts, C, err);
+  }
   count_launch();
 }
 
@@ -248,9 +281,16 @@ void launch_transpose_fill(const DevCsr& M, int32_t* cursor, const DevCsr& T, cu
   count_launch();
 }
 
-void launch_sort_rows(const DevCsr& T, int* err, int nsm, cudaStream_t s) {
+void launch_sort_rows(const DevCsr& T, int* err, bool wide, int nsm, cudaStream_t s) {
   if (T.n_rows == 0) return;
-  k_sort_rows<<<gemm_grid(T.n_rows, nsm), 32 * kGemmWarps, 0, s>>>(T, err);
+  if (wide) {
+    wide_smem_optin();
+    k_sort_rows<Wide><<<gemm_grid(T.n_rows, Wide::kWarps, nsm), 32 * Wide::kWarps,
+                        Wide::kRowMax * 12, s>>>(T, err);
+  } else {
+    k_sort_rows<Narrow><<<gemm_grid(T.n_rows, Narrow::kWarps, nsm), 32 * Narrow::kWarps,
+                          Narrow::kWarps * Narrow::kRowMax * 12, s>>>(T, err);
+  }
   count_launch();
 }
 

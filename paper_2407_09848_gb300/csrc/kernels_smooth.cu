@@ -52,40 +52,81 @@ __global__ void __launch_bounds__(kBlock) k_step(const StepArgs<VT, XT> a) {
   step_finish<VT, XT, FAM, INIT, WR, ZOWN>(a, row, acc, rin, xin, di, zo);
 }
 
+// Split form for levels with wide rows: one block per slice, a.split warps;
+// warp g sums entries [g w / G, (g+1) w / G) of each row, warp 0 adds the
+// partials in warp order (deterministic) and finishes the rows.
+template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN>
+__global__ void __launch_bounds__(32 * kMaxSplit) k_step_split(const StepArgs<VT, XT> a) {
+  __shared__ XT part[kMaxSplit][32];
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5, G = blockDim.x >> 5;
+  int64_t s = blockIdx.x;
+  if (a.slices) {
+    if (s >= a.nlist) return;
+    s = a.slices[s];
+  } else if (s >= a.A.nslices) {
+    return;
+  }
+  const int64_t row = s * kSlice + lane;
+  const bool live = row < a.A.n;
+  using F = StepForm<FAM, INIT>;
+  const XT rin = (live && g == 0) ? a.rin[row] : XT(0);
+  const int w = a.A.sd[s].w;
+  const int k0 = (int)((int64_t)w * g / G), k1 = (int)((int64_t)w * (g + 1) / G);
+  part[g][lane] = row_spmv_range<F::kSign, VT, XT>(a.A, s, lane, row, a.u,
+                                                   (g == 0 && F::kResidual) ? rin : XT(0), k0, k1);
+  __syncthreads();
+  if (g != 0 || !live) return;
+  XT acc = part[0][lane];
+  for (int q = 1; q < G; ++q) acc += part[q][lane];
+  XT xin = XT(0), zo = XT(0), di = XT(0);
+  if (FAM != FAM_RES) {
+    xin = a.xin[row];
+    di = a.dinv[row];
+  }
+  if (ZOWN) zo = a.zown[row];
+  step_finish<VT, XT, FAM, INIT, WR, ZOWN>(a, row, acc, rin, xin, di, zo);
+}
+
+template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN>
+static void go(const StepArgs<VT, XT>& a, int64_t work, cudaStream_t s) {
+  if (a.split > 1)
+    k_step_split<VT, XT, FAM, INIT, WR, ZOWN><<<(unsigned)work, 32 * a.split, 0, s>>>(a);
+  else
+    k_step<VT, XT, FAM, INIT, WR, ZOWN>
+        <<<(unsigned)((work + kWarpsPerBlock - 1) / kWarpsPerBlock), kBlock, 0, s>>>(a);
+  count_launch();
+}
+
 template <class VT, class XT, int FAM, bool INIT>
-static void dispatch_wr(const StepArgs<VT, XT>& a, dim3 g, cudaStream_t s) {
+static void dispatch_wr(const StepArgs<VT, XT>& a, int64_t work, cudaStream_t s) {
   const bool z = a.zown != nullptr;
   if (a.write_r) {
-    if (z) k_step<VT, XT, FAM, INIT, true, true><<<g, kBlock, 0, s>>>(a);
-    else k_step<VT, XT, FAM, INIT, true, false><<<g, kBlock, 0, s>>>(a);
+    if (z) go<VT, XT, FAM, INIT, true, true>(a, work, s);
+    else go<VT, XT, FAM, INIT, true, false>(a, work, s);
   } else {
-    if (z) k_step<VT, XT, FAM, INIT, false, true><<<g, kBlock, 0, s>>>(a);
-    else k_step<VT, XT, FAM, INIT, false, false><<<g, kBlock, 0, s>>>(a);
+    if (z) go<VT, XT, FAM, INIT, false, true>(a, work, s);
+    else go<VT, XT, FAM, INIT, false, false>(a, work, s);
   }
-  count_launch();
 }
 
 template <class VT, class XT>
 void launch_step(const StepArgs<VT, XT>& a, cudaStream_t s) {
   const int64_t work = a.slices ? a.nlist : a.A.nslices;
   if (work == 0) return;
-  dim3 g((unsigned)((work + kWarpsPerBlock - 1) / kWarpsPerBlock));
   switch (a.fam) {
     case FAM_CHEB4:
-      if (a.init) dispatch_wr<VT, XT, FAM_CHEB4, true>(a, g, s);
-      else dispatch_wr<VT, XT, FAM_CHEB4, false>(a, g, s);
+      if (a.init) dispatch_wr<VT, XT, FAM_CHEB4, true>(a, work, s);
+      else dispatch_wr<VT, XT, FAM_CHEB4, false>(a, work, s);
       break;
     case FAM_CHEB1:
-      if (a.init) dispatch_wr<VT, XT, FAM_CHEB1, true>(a, g, s);
-      else dispatch_wr<VT, XT, FAM_CHEB1, false>(a, g, s);
+      if (a.init) dispatch_wr<VT, XT, FAM_CHEB1, true>(a, work, s);
+      else dispatch_wr<VT, XT, FAM_CHEB1, false>(a, work, s);
       break;
     case FAM_RES:
-      k_step<VT, XT, FAM_RES, true, false, false><<<g, kBlock, 0, s>>>(a);
-      count_launch();
+      go<VT, XT, FAM_RES, true, false, false>(a, work, s);
       break;
     default:
-      k_step<VT, XT, FAM_JAC, true, false, false><<<g, kBlock, 0, s>>>(a);
-      count_launch();
+      go<VT, XT, FAM_JAC, true, false, false>(a, work, s);
   }
 }
 
@@ -256,8 +297,10 @@ template void launch_convert<float, double>(int64_t, const float*, double*, cuda
 template void launch_convert<double, double>(int64_t, const double*, double*, cudaStream_t);
 
 // Transfers through a general prolongator (explicit SELL-32, FP64 values):
-// y = M u (add = 0) or y += M u (add = 1), one warp per slice.  M = R = P^T
-// restricts (b_c = P^T r), M = P prolongs (x += P x_c).
+// y = M u (add = 0) or y += M u (add = 1).  M = R = P^T restricts
+// (b_c = P^T r), M = P prolongs (x += P x_c).  One warp per slice, or with
+// split > 1 one block per slice whose warps share the row's entries (partials
+// added in warp order).
 template <class XT>
 __global__ void __launch_bounds__(kBlock) k_xfer(const DevMat<double> M, const XT* __restrict__ u,
                                                  XT* __restrict__ y, int add) {
@@ -271,13 +314,40 @@ __global__ void __launch_bounds__(kBlock) k_xfer(const DevMat<double> M, const X
 }
 
 template <class XT>
-void launch_xfer(const DevMat<double>& M, const XT* u, XT* y, int add, cudaStream_t s) {
+__global__ void __launch_bounds__(32 * kMaxSplit) k_xfer_split(const DevMat<double> M,
+                                                               const XT* __restrict__ u,
+                                                               XT* __restrict__ y, int add) {
+  __shared__ XT part[kMaxSplit][32];
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5, G = blockDim.x >> 5;
+  const int64_t s = blockIdx.x;
+  if (s >= M.nslices) return;
+  const int64_t row = s * kSlice + lane;
+  const bool live = row < M.n;
+  const XT init = (add && live && g == 0) ? y[row] : XT(0);
+  const int w = M.sd[s].w;
+  const int k0 = (int)((int64_t)w * g / G), k1 = (int)((int64_t)w * (g + 1) / G);
+  part[g][lane] = row_spmv_range<1, double, XT>(M, s, lane, row, u, init, k0, k1);
+  __syncthreads();
+  if (g != 0 || !live) return;
+  XT t = part[0][lane];
+  for (int q = 1; q < G; ++q) t += part[q][lane];
+  y[row] = t;
+}
+
+template <class XT>
+void launch_xfer(const DevMat<double>& M, const XT* u, XT* y, int add, int split, cudaStream_t s) {
   if (M.nslices == 0) return;
-  const unsigned grid = (unsigned)((M.nslices + kWarpsPerBlock - 1) / kWarpsPerBlock);
-  k_xfer<XT><<<grid, kBlock, 0, s>>>(M, u, y, add);
+  if (split > 1) {
+    k_xfer_split<XT><<<(unsigned)M.nslices, 32 * split, 0, s>>>(M, u, y, add);
+  } else {
+    const unsigned grid = (unsigned)((M.nslices + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    k_xfer<XT><<<grid, kBlock, 0, s>>>(M, u, y, add);
+  }
   count_launch();
 }
-template void launch_xfer<double>(const DevMat<double>&, const double*, double*, int, cudaStream_t);
-template void launch_xfer<float>(const DevMat<double>&, const float*, float*, int, cudaStream_t);
+template void launch_xfer<double>(const DevMat<double>&, const double*, double*, int, int,
+                                  cudaStream_t);
+template void launch_xfer<float>(const DevMat<double>&, const float*, float*, int, int,
+                                 cudaStream_t);
 
 }  // namespace amgps

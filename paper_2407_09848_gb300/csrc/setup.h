@@ -7,8 +7,10 @@
 
 namespace amgps {
 
-// Most distinct columns a row of a sparse product (or of a transpose) may have.
-constexpr int kRowMax = 768;
+// Most distinct columns a row of a sparse product (or of a transpose) may
+// have in the narrow and in the wide form of the kernels.
+constexpr int kRowMaxNarrow = 768;
+constexpr int kRowMaxWide = 6144;
 
 struct DevCsr {
   int64_t n_rows = 0, n_cols = 0, nnz = 0;
@@ -19,9 +21,10 @@ struct DevCsr {
 
 // C = A B.  fill = false: counts[i] = distinct columns of row i of C.
 // fill = true: C.rowptr set from those counts; writes C.col (ascending per
-// row) and C.val.  *err = 1 if a row exceeds kRowMax columns.
+// row) and C.val.  *err = 1 if a row exceeds the form's column limit
+// (kRowMaxNarrow, or kRowMaxWide with wide = true).
 void launch_spgemm(const DevCsr& A, const DevCsr& B, int32_t* counts, const DevCsr& C, int* err,
-                   bool fill, int nsm, cudaStream_t s);
+                   bool fill, bool wide, int nsm, cudaStream_t s);
 // diag[i] = a_ii and per-block maxima of sum_j |a_ij| / a_ii into part[];
 // returns the number of blocks (partials)
 int launch_rowstat(const DevCsr& A, double* diag, double* part, int nsm, cudaStream_t s);
@@ -32,6 +35,6 @@ void launch_sa_combine(const DevCsr& AP, const int32_t* agg, const double* diag,
 // (from the prefix sums of the counts), then sort each row of T by column
 void launch_col_count(int64_t nnz, const int32_t* col, int32_t* cnt, cudaStream_t s);
 void launch_transpose_fill(const DevCsr& M, int32_t* cursor, const DevCsr& T, cudaStream_t s);
-void launch_sort_rows(const DevCsr& T, int* err, int nsm, cudaStream_t s);
+void launch_sort_rows(const DevCsr& T, int* err, bool wide, int nsm, cudaStream_t s);
 
 }  // namespace amgps

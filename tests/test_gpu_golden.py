@@ -60,3 +60,33 @@ def test_iterations_equal_stored_oracle_counts(torch_cuda, grid):
             bad.append((r["kind"], r["degree"], it, r["iterations"]))
     S.close()
     assert not bad, bad
+
+
+GOLDEN_SA = os.path.join(os.path.dirname(__file__), "golden", "oracle_sa_pcg_iterations.json")
+
+
+@pytest.mark.parametrize("grid", [32, 64, 256])
+def test_sa_iterations_equal_stored_oracle_counts(torch_cuda, grid):
+    # smoothed-aggregation hierarchy built on the GPU (amgps_sa_level per
+    # level); the oracle's counts come from its own host-built hierarchy
+    torch = torch_cuda
+    from paper_2407_09848_gb300.amgps import Solver
+    with open(GOLDEN_SA) as f:
+        runs = [r for r in json.load(f)["runs"] if r["grid"] == grid]
+    assert runs, "no stored counts"
+    st = pr.poisson(grid)
+    builder = Solver()
+    As, Ps, _ = builder.sa_hierarchy(pr.to_csr(st), pr.geometric_aggregates(st.shape, 512))
+    builder.close()
+    assert [a.shape[0] for a in As] == runs[0]["levels"]
+    S = Solver().load(As, Ps)
+    b = torch.from_numpy(pr.rhs_uniform(As[0].shape[0], seed=0)).cuda()
+    x = torch.empty_like(b)
+    bad = []
+    for r in runs:
+        S.set_smoother(-1, r["kind"], r["degree"])
+        it, rel = S.pcg(b, x, rtol=1e-8, maxit=1000)
+        if it != r["iterations"] or rel > 1e-8:
+            bad.append((r["kind"], r["degree"], it, r["iterations"]))
+    S.close()
+    assert not bad, bad

@@ -88,16 +88,26 @@ def test_galerkin_generic_prolongator(solver):
     assert np.array_equal(Ac.data, Ac2.data)
 
 
-def test_galerkin_row_limit_is_an_error(solver):
-    # A P with P = I on a dense 800 x 800 SPD matrix: product rows of 800
-    # distinct columns exceed the 768 limit -> AMGPS_E_ARG, context still usable
+def test_galerkin_wide_rows_and_row_limit(solver):
+    # rows of 800 distinct columns take the wide form of the product kernels
     from paper_2407_09848_gb300.amgps import AmgpsError
     n = 800
     rng = np.random.default_rng(1)
     Q = rng.uniform(-1, 1, (n, n))
     A = sp.csr_matrix(Q @ Q.T + n * np.eye(n))
+    P = sp.csr_matrix(rng.uniform(-1, 1, (n, 40)))
+    Ac = solver.galerkin(A, P)
+    Aco = sa.galerkin(A, P)
+    assert max_abs_diff(Ac, Aco) <= 1e-13 * np.abs(Aco.data).max()
+    # P = I: both products have rows of 800 columns; I^T A I = A exactly
+    assert max_abs_diff(solver.galerkin(A, sp.identity(n, format="csr")), A) == 0.0
+    # a row of 7000 distinct columns exceeds the wide limit (6144): AMGPS_E_ARG,
+    # and the context stays usable
+    m = 7000
+    B = sp.identity(m, format="lil")
+    B[0, :] = 1.0
     with pytest.raises(AmgpsError) as ei:
-        solver.galerkin(A, sp.identity(n, format="csr"))
+        solver.galerkin(sp.csr_matrix(B), sp.identity(m, format="csr"))
     assert ei.value.name == "AMGPS_E_ARG"
     st = pr.poisson(6)
     (agg, nc, _), = pr.geometric_aggregates(st.shape, coarse_max=64)

@@ -452,13 +452,18 @@ def run_ours(a):
     clk = clk.summary() if hasattr(clk, "summary") else clk
     if a.prec == "f64" and a.kind in ("cheb4", "cheb4_opt", "weights") and n_step:
         # FP64 path: the step is bound by the FP64 pipe (ncu: ~83% busy vs
-        # DRAM ~62%).  Flops per launch averaged over a V-cycle's level-0 steps:
-        # (2k-2) steps of 2 nnz + 6 n (with the c1 z term) and one initial step
-        # of 2 nnz + 4 n.  Peak: 304 FP64 FMA thread-instructions per clock
-        # (152 SMs x 2, ncu peak_sustained) x 2 flops x the sampled SM clock.
+        # DRAM ~62%).  The 4th-kind steps run on the row-scaled matrix M^{-1}A
+        # with the residual kept scaled.  Flops per launch averaged over a
+        # V-cycle's 2k-1 level-0 steps: every step 2 nnz (the SpMV with the
+        # residual folded in); per row c2 r (1) and, with the c1 z term, one
+        # FMA (2), x += beta z (2), and 1 more where rin is still unscaled (the
+        # first step after the initial one, and the post-smoothing initial
+        # step, which has no c1 term): 2 nnz + 5 n per launch for k >= 2,
+        # 2 nnz + 4 n for k = 1.  Peak: 304 FP64 FMA thread-instructions per
+        # clock (152 SMs x 2, ncu peak_sustained) x 2 flops x the SM clock.
         k = a.degree
         nnz0 = float(H.levels[0].A.nnz)
-        fl = ((2 * k - 2) * (2 * nnz0 + 6 * n) + (2 * nnz0 + 4 * n)) / (2 * k - 1)
+        fl = 2 * nnz0 + (5 * n if k >= 2 else 4 * n)
         mhz = clk.get("sm_mhz") or 2070.0
         fpeak = 304 * 2 * mhz * 1e6 / 1e12
         fach = fl / (1e-3 * ms_step / n_step) / 1e12

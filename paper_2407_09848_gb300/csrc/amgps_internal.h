@@ -44,7 +44,16 @@ struct DevMat {
 
 // FAM_RES is not a smoother: it writes the true residual b - A x (rin = b,
 // u = x, result in zout) for the restriction of Eq. amg.
-enum Family { FAM_CHEB4 = 0, FAM_CHEB1 = 1, FAM_JAC = 2, FAM_RES = 3 };
+// FAM_CHEB4S / FAM_CHEB4SR are the 4th-kind step on FP64 levels in the
+// row-scaled form: A holds a_ij / M_i and the recurrence residual is kept as
+// M^{-1} r, so a row needs no 1/M product; in FAM_CHEB4SR rin is still
+// unscaled (b: the first step after the initial one, or an initial step) and
+// the accumulation starts from (1/M) rin.
+enum Family { FAM_CHEB4 = 0, FAM_CHEB1 = 1, FAM_JAC = 2, FAM_RES = 3, FAM_CHEB4S = 4,
+              FAM_CHEB4SR = 5 };
+constexpr bool is_cheb4(int fam) {
+  return fam == FAM_CHEB4 || fam == FAM_CHEB4S || fam == FAM_CHEB4SR;
+}
 
 // Arguments of one fused smoother step (see kernels_smooth.cu).
 template <class VT, class XT>
@@ -65,6 +74,8 @@ struct StepArgs {
   const int32_t* slices = nullptr;  // optional list of slices to process (null: all)
   int64_t nlist = 0;                // entries in `slices`
   int split = 1;  // > 1: one block of `split` warps per slice, entries split among them
+  // host hint for the scaled form: rin is still unscaled (b)
+  bool rin_raw = false;
 };
 
 // Warps per slice for a level whose rows are wide (the split form of the

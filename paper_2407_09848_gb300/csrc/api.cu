@@ -126,6 +126,9 @@ struct Level {
   int psplit = 1, rsplit = 1;
   int split = 1;  // warps per slice of the generic step kernel (wide rows)
   void* dinv = nullptr;   // 1 / M_i
+  // FP64 levels: the row-scaled values a_ij / M_i in the layout of `val`,
+  // used by the 4th-kind steps (their residual is kept scaled)
+  void* sval = nullptr;
   void *b = nullptr, *x = nullptr, *r = nullptr, *za = nullptr, *zb = nullptr, *xb = nullptr;
   double* ainv = nullptr;
   bool coarsest = false;
@@ -651,6 +654,10 @@ struct Engine {
   // direct kernel over the remaining slices, or the direct kernel alone.
   static void run_step(amgps_ctx* c, const Level& L, StepArgs<VT, XT> a, cudaStream_t s) {
     a.split = L.split;
+    if (L.sval && a.fam == FAM_CHEB4) {
+      a.A.val = (const VT*)L.sval;
+      a.fam = (a.rin_raw || a.init) ? FAM_CHEB4SR : FAM_CHEB4S;  // an initial step's rin is b
+    }
     if (c->use_tma && L.ntma > 0 &&
         launch_step_tma<VT, XT>(a, L.plan, L.tma_tiles, L.ntma, L.tma_grid, c->dscal + S_ERR, s)) {
       if (L.ngen > 0) {
@@ -753,7 +760,10 @@ struct Engine {
       a.rhoinv = XT(cf.rhoinv);
       a.fam = cf.fam;
       a.init = false;
-      ProfScope ps(c, profl, 0, step_bytes<VT, XT>(L, a.write_r ? 7 : 6));
+      a.rin_raw = (rin_next == b);  // first step after k_first: r_0 = b
+      // streams: z_j, r in(/out), z_{j+1}, x in/out, and 1/M unless scaled
+      const bool no_dinv = L.sval && cf.fam == FAM_CHEB4 && !a.rin_raw;
+      ProfScope ps(c, profl, 0, step_bytes<VT, XT>(L, (a.write_r ? 7 : 6) - (no_dinv ? 1 : 0)));
       run_step(c, L, a, s);
       ps.done();
       xcur = x;
@@ -869,6 +879,7 @@ struct Engine {
       a.c2 = XT(cf.c2[j + 1]);
       a.beta = XT(0);
       a.fam = FAM_CHEB4;
+      a.rin_raw = (rin_next == b);
       run_step(c, L, a, s);
       launch_dot(n, (const double*)gx, (const double*)zn, rw, c->ddots, slot0 + j, 0, s);
       rin_next = r;
@@ -1606,6 +1617,23 @@ amgps_status amgps_hierarchy_load(amgps_ctx* c, int n_levels, const amgps_csr* A
         L.val64 = dupload(c, h.val.data(), h.val.size());
       }
       if (L.coarsest) continue;  // single-level hierarchy: SELL for the PCG SpMV only
+      if (prec == AMGPS_F64) {
+        // row-scaled copy a_ij / M_i, M_i = sum_j |a_ij| (the l1 diagonal)
+        std::vector<double> m((size_t)L.n, 0.0);
+        for (int64_t i = 0; i < L.n; ++i)
+          for (int e = A[l].rowptr[i]; e < A[l].rowptr[i + 1]; ++e) m[i] += std::fabs(A[l].val[e]);
+        std::vector<double> sv(h.val.size(), 0.0);
+        for (int64_t sl = 0; sl < h.nslices; ++sl) {
+          const SliceDesc d = h.sd[sl];
+          for (int k = 0; k < d.w; ++k)
+            for (int ln = 0; ln < kSlice; ++ln) {
+              const int64_t row = sl * kSlice + ln;
+              const int64_t e = d.vbase + (int64_t)k * kSlice + ln;
+              if (row < L.n) sv[e] = h.val[e] / m[row];
+            }
+        }
+        L.sval = dupload(c, sv.data(), sv.size());
+      }
       L.dinv = dalloc(c, L.n * xs);
       L.r = dalloc(c, L.n * xs);
       L.za = dalloc(c, L.n * xs);

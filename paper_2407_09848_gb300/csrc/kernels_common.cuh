@@ -74,15 +74,33 @@ struct StepForm {
   static constexpr int kSign = kResidual ? -1 : 1;
 };
 
+// Whether a step reads 1/M: every step but the residual and the scaled
+// 4th-kind step with scaled rin.
+template <int FAM>
+__device__ __forceinline__ constexpr bool step_needs_dinv() {
+  return FAM != FAM_RES && FAM != FAM_CHEB4S;
+}
+
+// Starting value of the accumulation: rin for the residual forms ((1/M) rin
+// when a scaled step's rin is still unscaled), 0 otherwise.
+template <int FAM, bool RESID, class XT>
+__device__ __forceinline__ XT step_init(XT rin, XT di) {
+  if constexpr (!RESID) return XT(0);
+  else if constexpr (FAM == FAM_CHEB4SR) return rin * di;
+  else return rin;
+}
+
 // Epilogue of one smoother step for one row, given the accumulated SpMV and
 // the row's own vector entries (see kernels_smooth.cu for the recurrences).
 template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN>
 __device__ __forceinline__ void step_finish(const StepArgs<VT, XT>& a, int64_t row, XT acc, XT rin,
                                             XT xin, XT di, XT zo) {
-  if constexpr (FAM == FAM_CHEB4) {
-    const XT r = acc;
+  if constexpr (is_cheb4(FAM)) {
+    const XT r = acc;  // r_j, or M^{-1} r_j in the scaled forms
     if (WR) a.rout[row] = r;
-    XT z = a.c2 * (r * di);
+    XT z;
+    if constexpr (FAM == FAM_CHEB4) z = a.c2 * (r * di);
+    else z = a.c2 * r;
     if (ZOWN) z = fma(a.c1, zo, z);
     a.zout[row] = z;
     a.xout[row] = fma(a.beta, z, xin);

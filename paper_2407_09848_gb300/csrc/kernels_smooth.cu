@@ -40,14 +40,13 @@ __global__ void __launch_bounds__(kBlock) k_step(const StepArgs<VT, XT> a) {
   XT rin = XT(0), xin = XT(0), zo = XT(0), di = XT(0);
   if (live) {
     rin = a.rin[row];
-    if (FAM != FAM_RES) {
-      xin = a.xin[row];
-      di = a.dinv[row];
-    }
+    if (FAM != FAM_RES) xin = a.xin[row];
+    if (step_needs_dinv<FAM>()) di = a.dinv[row];
     if (ZOWN) zo = a.zown[row];
   }
   using F = StepForm<FAM, INIT>;
-  const XT acc = row_spmv<F::kSign, VT, XT>(a.A, s, lane, row, a.u, F::kResidual ? rin : XT(0));
+  const XT acc = row_spmv<F::kSign, VT, XT>(a.A, s, lane, row, a.u,
+                                             step_init<FAM, F::kResidual>(rin, di));
   if (!live) return;
   step_finish<VT, XT, FAM, INIT, WR, ZOWN>(a, row, acc, rin, xin, di, zo);
 }
@@ -70,19 +69,17 @@ __global__ void __launch_bounds__(32 * kMaxSplit) k_step_split(const StepArgs<VT
   const bool live = row < a.A.n;
   using F = StepForm<FAM, INIT>;
   const XT rin = (live && g == 0) ? a.rin[row] : XT(0);
+  const XT di = (live && g == 0 && step_needs_dinv<FAM>()) ? a.dinv[row] : XT(0);
   const int w = a.A.sd[s].w;
   const int k0 = (int)((int64_t)w * g / G), k1 = (int)((int64_t)w * (g + 1) / G);
-  part[g][lane] = row_spmv_range<F::kSign, VT, XT>(a.A, s, lane, row, a.u,
-                                                   (g == 0 && F::kResidual) ? rin : XT(0), k0, k1);
+  part[g][lane] = row_spmv_range<F::kSign, VT, XT>(
+      a.A, s, lane, row, a.u, g == 0 ? step_init<FAM, F::kResidual>(rin, di) : XT(0), k0, k1);
   __syncthreads();
   if (g != 0 || !live) return;
   XT acc = part[0][lane];
   for (int q = 1; q < G; ++q) acc += part[q][lane];
-  XT xin = XT(0), zo = XT(0), di = XT(0);
-  if (FAM != FAM_RES) {
-    xin = a.xin[row];
-    di = a.dinv[row];
-  }
+  XT xin = XT(0), zo = XT(0);
+  if (FAM != FAM_RES) xin = a.xin[row];
   if (ZOWN) zo = a.zown[row];
   step_finish<VT, XT, FAM, INIT, WR, ZOWN>(a, row, acc, rin, xin, di, zo);
 }
@@ -117,6 +114,13 @@ void launch_step(const StepArgs<VT, XT>& a, cudaStream_t s) {
     case FAM_CHEB4:
       if (a.init) dispatch_wr<VT, XT, FAM_CHEB4, true>(a, work, s);
       else dispatch_wr<VT, XT, FAM_CHEB4, false>(a, work, s);
+      break;
+    case FAM_CHEB4S:
+      dispatch_wr<VT, XT, FAM_CHEB4S, false>(a, work, s);
+      break;
+    case FAM_CHEB4SR:
+      if (a.init) dispatch_wr<VT, XT, FAM_CHEB4SR, true>(a, work, s);
+      else dispatch_wr<VT, XT, FAM_CHEB4SR, false>(a, work, s);
       break;
     case FAM_CHEB1:
       if (a.init) dispatch_wr<VT, XT, FAM_CHEB1, true>(a, work, s);

@@ -122,15 +122,15 @@ __global__ void __launch_bounds__((kTmaConsumers + 1) * 32, 1)
             unsigned char* base = stages + (size_t)st * p.stage_bytes;
             const int64_t r0 = rq;
             stage_r0[st] = rq;
-            constexpr int nvec = FAM == FAM_RES ? 1 : 3;  // the residual needs no x_in, 1/M
+            // the residual needs no x_in or 1/M; a scaled step with scaled rin no 1/M
+            constexpr bool wdi = step_needs_dinv<FAM>();
+            constexpr int nvec = FAM == FAM_RES ? 1 : (wdi ? 3 : 2);
             mbar_expect_tx(&full[st], (uint32_t)(p.vals_bytes + nvec * p.vec_bytes + p.win_bytes));
             bulk_g2s(base, a.A.val + vq, (uint32_t)p.vals_bytes, &full[st]);
             XT* sv = reinterpret_cast<XT*>(base + p.vals_bytes);
             bulk_g2s(sv, a.rin + r0, (uint32_t)p.vec_bytes, &full[st]);
-            if (FAM != FAM_RES) {
-              bulk_g2s(sv + p.rows, a.xin + r0, (uint32_t)p.vec_bytes, &full[st]);
-              bulk_g2s(sv + 2 * p.rows, a.dinv + r0, (uint32_t)p.vec_bytes, &full[st]);
-            }
+            if (FAM != FAM_RES) bulk_g2s(sv + p.rows, a.xin + r0, (uint32_t)p.vec_bytes, &full[st]);
+            if (wdi) bulk_g2s(sv + 2 * p.rows, a.dinv + r0, (uint32_t)p.vec_bytes, &full[st]);
             XT* sw = sv + 3 * p.rows;
             for (int g = 0; g < p.ngroups; ++g)
               bulk_g2s(sw + p.g_smem[g], a.u + r0 + p.g_start[g],
@@ -171,9 +171,9 @@ __global__ void __launch_bounds__((kTmaConsumers + 1) * 32, 1)
       const VT* svals = reinterpret_cast<const VT*>(base) + (size_t)cs * p.w * kSlice + lane;
       const XT rin = sv[it_row];
       const XT xin = FAM == FAM_RES ? XT(0) : sv[p.rows + it_row];
-      const XT di = FAM == FAM_RES ? XT(0) : sv[2 * p.rows + it_row];
+      const XT di = step_needs_dinv<FAM>() ? sv[2 * p.rows + it_row] : XT(0);
       const XT zo = ZOWN ? sw[p.d0 + it_row] : XT(0);
-      XT acc = F::kResidual ? rin : XT(0);
+      XT acc = step_init<FAM, F::kResidual>(rin, di);
 #pragma unroll
       for (int k = 0; k < kTmaMaxW; ++k) {
         if (k < p.w) {
@@ -235,6 +235,18 @@ void configure_all(int bytes) {
   set_smem_attr<VT, XT, FAM_CHEB1, false, true, false>(bytes);
   set_smem_attr<VT, XT, FAM_CHEB1, false, false, true>(bytes);
   set_smem_attr<VT, XT, FAM_CHEB1, false, false, false>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB4S, false, true, true>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB4S, false, true, false>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB4S, false, false, true>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB4S, false, false, false>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB4SR, true, true, true>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB4SR, true, true, false>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB4SR, true, false, true>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB4SR, true, false, false>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB4SR, false, true, true>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB4SR, false, true, false>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB4SR, false, false, true>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB4SR, false, false, false>(bytes);
   set_smem_attr<VT, XT, FAM_JAC, true, false, false>(bytes);
   set_smem_attr<VT, XT, FAM_RES, true, false, false>(bytes);
 }
@@ -260,6 +272,13 @@ bool launch_step_tma(const StepArgs<VT, XT>& a, const TmaPlan& p, const TmaTile*
     case FAM_CHEB4:
       if (a.init) launch_wr<VT, XT, FAM_CHEB4, true>(a, p, tiles, ntiles, grid, err, s);
       else launch_wr<VT, XT, FAM_CHEB4, false>(a, p, tiles, ntiles, grid, err, s);
+      break;
+    case FAM_CHEB4S:
+      launch_wr<VT, XT, FAM_CHEB4S, false>(a, p, tiles, ntiles, grid, err, s);
+      break;
+    case FAM_CHEB4SR:
+      if (a.init) launch_wr<VT, XT, FAM_CHEB4SR, true>(a, p, tiles, ntiles, grid, err, s);
+      else launch_wr<VT, XT, FAM_CHEB4SR, false>(a, p, tiles, ntiles, grid, err, s);
       break;
     case FAM_CHEB1:
       if (a.init) launch_wr<VT, XT, FAM_CHEB1, true>(a, p, tiles, ntiles, grid, err, s);

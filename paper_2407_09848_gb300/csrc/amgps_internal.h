@@ -51,7 +51,7 @@ struct DevMat {
 // the accumulation starts from (1/M) rin.
 enum Family { FAM_CHEB4 = 0, FAM_CHEB1 = 1, FAM_JAC = 2, FAM_RES = 3, FAM_CHEB4S = 4,
               FAM_CHEB4SR = 5 };
-constexpr bool is_cheb4(int fam) {
+__host__ __device__ constexpr bool is_cheb4(int fam) {
   return fam == FAM_CHEB4 || fam == FAM_CHEB4S || fam == FAM_CHEB4SR;
 }
 

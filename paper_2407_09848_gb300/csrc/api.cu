@@ -658,16 +658,15 @@ struct Engine {
       a.A.val = (const VT*)L.sval;
       a.fam = (a.rin_raw || a.init) ? FAM_CHEB4SR : FAM_CHEB4S;  // an initial step's rin is b
     }
-    if (c->use_tma && L.ntma > 0 &&
-        launch_step_tma<VT, XT>(a, L.plan, L.tma_tiles, L.ntma, L.tma_grid, c->dscal + S_ERR, s)) {
-      if (L.ngen > 0) {
-        a.slices = L.gen_slices;
-        a.nlist = L.ngen;
-        launch_step<VT, XT>(a, s);
-      }
-    } else {
-      launch_step<VT, XT>(a, s);
+    if (c->use_tma && L.ntma > 0) {
+      // the TMA kernel also runs the slices outside its plan (slice list)
+      StepArgs<VT, XT> t = a;
+      t.slices = L.ngen > 0 ? L.gen_slices : nullptr;
+      t.nlist = L.ngen;
+      if (launch_step_tma<VT, XT>(t, L.plan, L.tma_tiles, L.ntma, L.tma_grid, c->dscal + S_ERR, s))
+        return;
     }
+    launch_step<VT, XT>(a, s);
   }
 
   // One smoother application on level l: x <- S(b, x) (x = 0 when xzero).

@@ -120,6 +120,26 @@ __device__ __forceinline__ void step_finish(const StepArgs<VT, XT>& a, int64_t r
   }
 }
 
+// One smoother step on the 32 rows of slice s, one row per lane, operands
+// read from global memory (the direct form of the step).
+template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN>
+__device__ __forceinline__ void step_slice(const StepArgs<VT, XT>& a, int64_t s, int lane) {
+  const int64_t row = s * kSlice + lane;
+  const bool live = row < a.A.n;
+  XT rin = XT(0), xin = XT(0), zo = XT(0), di = XT(0);
+  if (live) {
+    rin = a.rin[row];
+    if (FAM != FAM_RES) xin = a.xin[row];
+    if (step_needs_dinv<FAM>()) di = a.dinv[row];
+    if (ZOWN) zo = a.zown[row];
+  }
+  using F = StepForm<FAM, INIT>;
+  const XT acc = row_spmv<F::kSign, VT, XT>(a.A, s, lane, row, a.u,
+                                             step_init<FAM, F::kResidual>(rin, di));
+  if (!live) return;
+  step_finish<VT, XT, FAM, INIT, WR, ZOWN>(a, row, acc, rin, xin, di, zo);
+}
+
 // Sum over a block (any blockDim multiple of 32, <= 1024); result valid in thread 0.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
 #pragma unroll

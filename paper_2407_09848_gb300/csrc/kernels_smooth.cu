@@ -35,20 +35,7 @@ __global__ void __launch_bounds__(kBlock) k_step(const StepArgs<VT, XT> a) {
   } else if (s >= a.A.nslices) {
     return;
   }
-  const int64_t row = s * kSlice + lane;
-  const bool live = row < a.A.n;
-  XT rin = XT(0), xin = XT(0), zo = XT(0), di = XT(0);
-  if (live) {
-    rin = a.rin[row];
-    if (FAM != FAM_RES) xin = a.xin[row];
-    if (step_needs_dinv<FAM>()) di = a.dinv[row];
-    if (ZOWN) zo = a.zown[row];
-  }
-  using F = StepForm<FAM, INIT>;
-  const XT acc = row_spmv<F::kSign, VT, XT>(a.A, s, lane, row, a.u,
-                                             step_init<FAM, F::kResidual>(rin, di));
-  if (!live) return;
-  step_finish<VT, XT, FAM, INIT, WR, ZOWN>(a, row, acc, rin, xin, di, zo);
+  step_slice<VT, XT, FAM, INIT, WR, ZOWN>(a, s, lane);
 }
 
 // Split form for levels with wide rows: one block per slice, a.split warps;

@@ -78,9 +78,9 @@ template <class XT>
 __device__ __forceinline__ XT widen(__nv_bfloat16 v) { return XT(__bfloat162float(v)); }
 
 template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN>
-__global__ void __launch_bounds__((kTmaConsumers + 1) * 32, 1)
+__global__ void __launch_bounds__((kTmaConsumers + 1) * 32, 2)
     k_step_tma(const StepArgs<VT, XT> a, const TmaPlan p, const TmaTile* __restrict__ tiles,
-               int ntiles, double* err) {
+               int ntiles, const int32_t* __restrict__ gen, int64_t ngen, double* err) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ volatile int abort_flag;
   __shared__ long long stage_r0[kTmaMaxStages];  // first row of the tile held by each stage
@@ -186,15 +186,24 @@ __global__ void __launch_bounds__((kTmaConsumers + 1) * 32, 1)
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[st]);
   }
-  if (abort_flag && lane == 0) *err = 1.0;
+  if (abort_flag) {
+    if (lane == 0) *err = 1.0;
+    return;
+  }
+  // the slices outside the plan (pattern changes, windows leaving [0, n)):
+  // direct loads, round-robin over all consumer warps; their rows are
+  // disjoint from the tiles' rows
+  for (int64_t q = (int64_t)blockIdx.x * kTmaConsumers + c; q < ngen;
+       q += (int64_t)gridDim.x * kTmaConsumers)
+    step_slice<VT, XT, FAM, INIT, WR, ZOWN>(a, gen[q], lane);
 }
 
 template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN>
 void launch_inst(const StepArgs<VT, XT>& a, const TmaPlan& p, const TmaTile* tiles, int ntiles,
                  int grid, double* err, cudaStream_t s) {
   const int smem = kBarrierBytes + p.nstages * p.stage_bytes;
-  k_step_tma<VT, XT, FAM, INIT, WR, ZOWN>
-      <<<grid, (kTmaConsumers + 1) * 32, smem, s>>>(a, p, tiles, ntiles, err);
+  k_step_tma<VT, XT, FAM, INIT, WR, ZOWN><<<grid, (kTmaConsumers + 1) * 32, smem, s>>>(
+      a, p, tiles, ntiles, a.slices, a.slices ? a.nlist : 0, err);
   count_launch();
 }
 

@@ -49,8 +49,10 @@ struct DevMat {
 // M^{-1} r, so a row needs no 1/M product; in FAM_CHEB4SR rin is still
 // unscaled (b: the first step after the initial one, or an initial step) and
 // the accumulation starts from (1/M) rin.
+// FAM_CHEB1S / FAM_CHEB1SR do the same for the 1st-kind steps, keeping the
+// residual as rho M^{-1} r (the 1/rho goes into the coefficient of r).
 enum Family { FAM_CHEB4 = 0, FAM_CHEB1 = 1, FAM_JAC = 2, FAM_RES = 3, FAM_CHEB4S = 4,
-              FAM_CHEB4SR = 5 };
+              FAM_CHEB4SR = 5, FAM_CHEB1S = 6, FAM_CHEB1SR = 7 };
 __host__ __device__ constexpr bool is_cheb4(int fam) {
   return fam == FAM_CHEB4 || fam == FAM_CHEB4S || fam == FAM_CHEB4SR;
 }

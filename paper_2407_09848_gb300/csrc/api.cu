@@ -657,6 +657,11 @@ struct Engine {
     if (L.sval && a.fam == FAM_CHEB4) {
       a.A.val = (const VT*)L.sval;
       a.fam = (a.rin_raw || a.init) ? FAM_CHEB4SR : FAM_CHEB4S;  // an initial step's rin is b
+    } else if (L.sval && a.fam == FAM_CHEB1) {
+      // residual kept as rho M^{-1} r: the 1/rho moves into the coefficient of r
+      a.A.val = (const VT*)L.sval;
+      a.fam = a.init ? FAM_CHEB1SR : FAM_CHEB1S;
+      a.c2 = a.c2 * a.rhoinv;
     }
     if (c->use_tma && L.ntma > 0) {
       // the TMA kernel also runs the slices outside its plan (slice list)
@@ -711,8 +716,13 @@ struct Engine {
     const XT* rin_next;
     XT* xcur = x;
     if (xzero) {
-      const double c2 = (cf.fam == FAM_CHEB4) ? cf.c2[1] : cf.c2[0];
-      launch_first<XT>(cf.fam, L.n, b, md, r, zc, x, XT(c2), XT(cf.beta[1]), XT(cf.rhoinv), s);
+      double c2 = (cf.fam == FAM_CHEB4) ? cf.c2[1] : cf.c2[0];
+      double rhoinv = cf.rhoinv;
+      if (L.sval && cf.fam == FAM_CHEB1) {  // scaled 1st-kind form: r = rho r^(0)
+        c2 *= rhoinv;
+        rhoinv = 1.0;
+      }
+      launch_first<XT>(cf.fam, L.n, b, md, r, zc, x, XT(c2), XT(cf.beta[1]), XT(rhoinv), s);
       rin_next = (cf.fam == FAM_CHEB4) ? b : r;
     } else {
       StepArgs<VT, XT> a;
@@ -761,7 +771,7 @@ struct Engine {
       a.init = false;
       a.rin_raw = (rin_next == b);  // first step after k_first: r_0 = b
       // streams: z_j, r in(/out), z_{j+1}, x in/out, and 1/M unless scaled
-      const bool no_dinv = L.sval && cf.fam == FAM_CHEB4 && !a.rin_raw;
+      const bool no_dinv = L.sval && ((cf.fam == FAM_CHEB4 && !a.rin_raw) || cf.fam == FAM_CHEB1);
       ProfScope ps(c, profl, 0, step_bytes<VT, XT>(L, (a.write_r ? 7 : 6) - (no_dinv ? 1 : 0)));
       run_step(c, L, a, s);
       ps.done();

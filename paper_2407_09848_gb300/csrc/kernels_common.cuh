@@ -78,7 +78,7 @@ struct StepForm {
 // 4th-kind step with scaled rin.
 template <int FAM>
 __device__ __forceinline__ constexpr bool step_needs_dinv() {
-  return FAM != FAM_RES && FAM != FAM_CHEB4S;
+  return FAM != FAM_RES && FAM != FAM_CHEB4S && FAM != FAM_CHEB1S;
 }
 
 // Starting value of the accumulation: rin for the residual forms ((1/M) rin
@@ -86,7 +86,7 @@ __device__ __forceinline__ constexpr bool step_needs_dinv() {
 template <int FAM, bool RESID, class XT>
 __device__ __forceinline__ XT step_init(XT rin, XT di) {
   if constexpr (!RESID) return XT(0);
-  else if constexpr (FAM == FAM_CHEB4SR) return rin * di;
+  else if constexpr (FAM == FAM_CHEB4SR || FAM == FAM_CHEB1SR) return rin * di;
   else return rin;
 }
 
@@ -110,6 +110,13 @@ __device__ __forceinline__ void step_finish(const StepArgs<VT, XT>& a, int64_t r
     else r = fma(-(a.rhoinv * di), acc, rin);
     if (WR) a.rout[row] = r;
     XT z = a.c2 * r;
+    if (ZOWN) z = fma(a.c1, zo, z);
+    a.zout[row] = z;
+    a.xout[row] = xin + z;
+  } else if constexpr (FAM == FAM_CHEB1S || FAM == FAM_CHEB1SR) {
+    const XT r = acc;  // rho M^{-1} r
+    if (WR) a.rout[row] = r;
+    XT z = a.c2 * r;  // c2 carries the 1/rho
     if (ZOWN) z = fma(a.c1, zo, z);
     a.zout[row] = z;
     a.xout[row] = xin + z;

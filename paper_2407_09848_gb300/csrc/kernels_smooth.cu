@@ -109,6 +109,12 @@ void launch_step(const StepArgs<VT, XT>& a, cudaStream_t s) {
       if (a.init) dispatch_wr<VT, XT, FAM_CHEB4SR, true>(a, work, s);
       else dispatch_wr<VT, XT, FAM_CHEB4SR, false>(a, work, s);
       break;
+    case FAM_CHEB1S:
+      dispatch_wr<VT, XT, FAM_CHEB1S, false>(a, work, s);
+      break;
+    case FAM_CHEB1SR:
+      dispatch_wr<VT, XT, FAM_CHEB1SR, true>(a, work, s);
+      break;
     case FAM_CHEB1:
       if (a.init) dispatch_wr<VT, XT, FAM_CHEB1, true>(a, work, s);
       else dispatch_wr<VT, XT, FAM_CHEB1, false>(a, work, s);

@@ -256,6 +256,14 @@ void configure_all(int bytes) {
   set_smem_attr<VT, XT, FAM_CHEB4SR, false, true, false>(bytes);
   set_smem_attr<VT, XT, FAM_CHEB4SR, false, false, true>(bytes);
   set_smem_attr<VT, XT, FAM_CHEB4SR, false, false, false>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB1S, false, true, true>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB1S, false, true, false>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB1S, false, false, true>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB1S, false, false, false>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB1SR, true, true, true>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB1SR, true, true, false>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB1SR, true, false, true>(bytes);
+  set_smem_attr<VT, XT, FAM_CHEB1SR, true, false, false>(bytes);
   set_smem_attr<VT, XT, FAM_JAC, true, false, false>(bytes);
   set_smem_attr<VT, XT, FAM_RES, true, false, false>(bytes);
 }
@@ -288,6 +296,12 @@ bool launch_step_tma(const StepArgs<VT, XT>& a, const TmaPlan& p, const TmaTile*
     case FAM_CHEB4SR:
       if (a.init) launch_wr<VT, XT, FAM_CHEB4SR, true>(a, p, tiles, ntiles, grid, err, s);
       else launch_wr<VT, XT, FAM_CHEB4SR, false>(a, p, tiles, ntiles, grid, err, s);
+      break;
+    case FAM_CHEB1S:
+      launch_wr<VT, XT, FAM_CHEB1S, false>(a, p, tiles, ntiles, grid, err, s);
+      break;
+    case FAM_CHEB1SR:
+      launch_wr<VT, XT, FAM_CHEB1SR, true>(a, p, tiles, ntiles, grid, err, s);
       break;
     case FAM_CHEB1:
       if (a.init) launch_wr<VT, XT, FAM_CHEB1, true>(a, p, tiles, ntiles, grid, err, s);

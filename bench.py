@@ -408,7 +408,7 @@ def run_ours(a):
 
     # ---- timed region: K solves, CUDA events on the caller's stream ----
     S.profile(True)
-    for c in (PROF_STEP, PROF_RESTRICT, PROF_SPMV, 3):
+    for c in (PROF_STEP, PROF_RESTRICT, PROF_SPMV, 3, 4):
         S.profile_read(c, reset=True)
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -429,6 +429,7 @@ def run_ours(a):
     n_step, ms_step, by_step = S.profile_read(PROF_STEP, reset=True)
     n_rr, ms_rr, _ = S.profile_read(PROF_RESTRICT, reset=True)
     n_sp, ms_sp, _ = S.profile_read(PROF_SPMV, reset=True)
+    _, ms_coarse, _ = S.profile_read(4, reset=True)
     launches, _, _ = S.profile_read(3, reset=True)
     ms_per = max_over_ranks(total_ms / a.steps, pg)
     true_res = float(np.linalg.norm(b - H.levels[0].A @ x.cpu().numpy()) / np.linalg.norm(b))
@@ -549,7 +550,7 @@ def run_ours(a):
            "gpu_launches": launches,
            "clocks": clk,
            "kernel_ms": {"k_step_level0": ms_step / a.steps, "k_resid_restrict_level0": ms_rr / a.steps,
-                         "k_spmv_dot": ms_sp / a.steps},
+                         "k_spmv_dot": ms_sp / a.steps, "coarse_levels": ms_coarse / a.steps},
            "sweep": sweep,
            "comparisons": extras}
     if rank == 0:

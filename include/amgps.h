@@ -324,7 +324,9 @@ amgps_status amgps_cheb1_astar(int degree, double* a_out);
  * bytes of the launches: matrix nonzeros and stored indices once, each vector
  * stream once) are returned.  Class 3 counts every kernel of this library
  * executed since the last reset (whether or not timing is enabled; a graph
- * replay counts its kernel nodes); its *total_ms and *bytes are 0.
+ * replay counts its kernel nodes); its *total_ms and *bytes are 0.  Class 4
+ * times the coarse part of each V-cycle (every level below the finest, one
+ * interval per cycle); its *bytes is 0.
  * reset != 0 clears the counters of the class.  Reading is synchronous. */
 amgps_status amgps_profile_enable(amgps_ctx* ctx, int on);
 amgps_status amgps_profile_read(amgps_ctx* ctx, int kernel_class, int reset,

@@ -24,7 +24,7 @@ PREC = {"f64": 0, "f32": 1, "bf16": 2}
 STATUS = {0: "AMGPS_OK", 1: "AMGPS_E_ARG", 2: "AMGPS_E_NOT_SPD", 3: "AMGPS_E_NOCONV",
           4: "AMGPS_E_NAN", 5: "AMGPS_E_CUDA", 6: "AMGPS_E_TIMEOUT", 7: "AMGPS_E_STATE",
           8: "AMGPS_E_NOMEM"}
-PROF_STEP, PROF_RESTRICT, PROF_SPMV = 0, 1, 2
+PROF_STEP, PROF_RESTRICT, PROF_SPMV, PROF_COUNT, PROF_COARSE = 0, 1, 2, 3, 4
 
 
 class AmgpsError(RuntimeError):

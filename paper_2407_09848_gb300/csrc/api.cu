@@ -475,9 +475,9 @@ struct amgps_ctx {
   };
   std::vector<Pair> pending;
   std::vector<cudaEvent_t> pool;
-  int64_t prof_launches[3] = {};
-  double prof_ms[3] = {};
-  double prof_bytes[3] = {};
+  int64_t prof_launches[5] = {};  // class 3 (kernel count) is kept apart
+  double prof_ms[5] = {};
+  double prof_bytes[5] = {};
 };
 
 namespace {
@@ -814,11 +814,16 @@ struct Engine {
       else launch_aggregate<XT>(L.cptr, L.cidx, L.nc, (const XT*)L.r, (XT*)C.b, s);
       ps.done();
     }
-    if (l + 1 == 1 && c->graph_ok && !record && !capturing(c)) {
-      CK(cudaGraphLaunch(c->gexec, s));
-      c->launch_adjust += c->graph_kernels;
-    } else {
-      vcycle_level(c, l + 1, (const XT*)C.b, (XT*)C.x, record);
+    {
+      // levels >= 1 of the cycle, timed as one class-4 interval from level 0
+      ProfScope ps(c, l == 0, 4, 0.0);
+      if (l + 1 == 1 && c->graph_ok && !record && !capturing(c)) {
+        CK(cudaGraphLaunch(c->gexec, s));
+        c->launch_adjust += c->graph_kernels;
+      } else {
+        vcycle_level(c, l + 1, (const XT*)C.b, (XT*)C.x, record);
+      }
+      ps.done();
     }
     if (L.xfer_general) launch_xfer<XT>(L.Pm, (const XT*)C.x, x, 1, L.psplit, s);
     else launch_prolong<XT>(L.n, L.agg, (const XT*)C.x, x, s);
@@ -2139,7 +2144,7 @@ amgps_status amgps_profile_read(amgps_ctx* c, int cls, int reset, int64_t* launc
                                 double* total_ms, double* bytes) {
   return guard(c, [&] {
     REQ(c, AMGPS_E_ARG, "null context");
-    REQ(cls >= 0 && cls <= 3, AMGPS_E_ARG, "kernel class out of range");
+    REQ(cls >= 0 && cls <= 4, AMGPS_E_ARG, "kernel class out of range");
     CK(cudaSetDevice(c->device));
     CK(cudaStreamSynchronize(c->stream));
     harvest(c);

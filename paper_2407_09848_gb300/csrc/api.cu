@@ -1618,6 +1618,9 @@ amgps_status amgps_hierarchy_load(amgps_ctx* c, int n_levels, const amgps_csr* A
         L.plan = hp.p;
         L.ntma = (int)hp.tiles.size();
         L.ngen = (int64_t)hp.gen.size();
+        // below two tiles per CTA the persistent pipeline cannot fill; the
+        // direct kernel (more, smaller blocks) is faster on such small levels
+        if (L.ntma < 4 * c->nsm) L.ntma = 0;
         if (L.ntma > 0) {
           L.tma_tiles = dupload(c, hp.tiles.data(), hp.tiles.size());
           L.tma_grid = std::min<int>(L.ntma, 2 * c->nsm);

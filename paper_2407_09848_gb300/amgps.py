@@ -424,8 +424,11 @@ class Solver:
         return C.c_void_p(a.ctypes.data)
 
     def set_tma(self, on):
-        """Use the TMA-fed step kernel where possible (default) or the direct one."""
-        self._check(lib().amgps_set_option(self._h, 1, 1 if on else 0))
+        """Step kernel choice: True (default: TMA-fed kernel on levels large
+        enough for it), False (direct kernel everywhere), "always" (TMA-fed
+        kernel wherever a level's layout allows it)."""
+        v = 2 if on == "always" else (1 if on else 0)
+        self._check(lib().amgps_set_option(self._h, 1, v))
 
     OUTER = {"cg": 0, "flexible": 1, "fcg1": 2}
 

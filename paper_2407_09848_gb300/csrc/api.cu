@@ -463,7 +463,7 @@ struct amgps_ctx {
   cudaGraphExec_t gexec = nullptr;
   bool graph_ok = false;
   int64_t graph_kernels = 0;   // kernel nodes in gexec
-  bool use_tma = true;         // TMA-fed step kernels (option AMGPS_OPT_TMA)
+  int use_tma = 1;             // TMA-fed step kernels (option AMGPS_OPT_TMA: 0 off, 1 auto, 2 always)
   int flexible = 0;            // AMGPS_OPT_FLEXIBLE: 0 standard, 1 Polak-Ribiere, 2 one-reduction
   int64_t launch_adjust = 0;   // captured (not run) launches removed, replays added
   int64_t launch_base = 0;     // reset point of the launch counter
@@ -663,7 +663,11 @@ struct Engine {
       a.fam = a.init ? FAM_CHEB1SR : FAM_CHEB1S;
       a.c2 = a.c2 * a.rhoinv;
     }
-    if (c->use_tma && L.ntma > 0) {
+    // TMA option 1 (auto): only where the level has two tiles per CTA or more;
+    // below that the persistent pipeline cannot fill and the direct kernel
+    // (more, smaller blocks) is faster.  Option 2 takes it wherever planned.
+    const bool tma = L.ntma > 0 && (c->use_tma == 2 || (c->use_tma == 1 && L.ntma >= 4 * c->nsm));
+    if (tma) {
       // the TMA kernel also runs the slices outside its plan (slice list)
       StepArgs<VT, XT> t = a;
       t.slices = L.ngen > 0 ? L.gen_slices : nullptr;
@@ -1618,9 +1622,6 @@ amgps_status amgps_hierarchy_load(amgps_ctx* c, int n_levels, const amgps_csr* A
         L.plan = hp.p;
         L.ntma = (int)hp.tiles.size();
         L.ngen = (int64_t)hp.gen.size();
-        // below two tiles per CTA the persistent pipeline cannot fill; the
-        // direct kernel (more, smaller blocks) is faster on such small levels
-        if (L.ntma < 4 * c->nsm) L.ntma = 0;
         if (L.ntma > 0) {
           L.tma_tiles = dupload(c, hp.tiles.data(), hp.tiles.size());
           L.tma_grid = std::min<int>(L.ntma, 2 * c->nsm);
@@ -2097,7 +2098,8 @@ amgps_status amgps_set_option(amgps_ctx* c, int option, int64_t value) {
     REQ(c, AMGPS_E_ARG, "null context");
     REQ(option == AMGPS_OPT_TMA || option == AMGPS_OPT_FLEXIBLE, AMGPS_E_ARG, "unknown option");
     if (option == AMGPS_OPT_TMA) {
-      c->use_tma = value != 0;
+      REQ(value >= 0 && value <= 2, AMGPS_E_ARG, "AMGPS_OPT_TMA takes 0, 1 or 2");
+      c->use_tma = (int)value;
       c->graph_ok = false;
     } else {
       REQ(value >= 0 && value <= 2, AMGPS_E_ARG, "AMGPS_OPT_FLEXIBLE takes 0, 1 or 2");

@@ -340,14 +340,14 @@ def test_tma_step_equals_direct_step(torch_cuda, prec):
                 S.set_smoother(level, "weights", 3, weights=[1.1, 0.9, 1.3])
             for zero in (True, False):
                 outs = []
-                for tma in (True, False):
+                for tma in ("always", False):
                     S.set_tma(tma)
                     x = x0.clone()
                     S.smooth(level, kind, k, b, x, x_is_zero=zero)
                     outs.append(x)
                 S.synchronize()
                 assert torch.equal(outs[0], outs[1]), (prec, level, kind, k, zero)
-    S.set_tma(True)
+    S.set_tma("always")
     z1 = torch.empty(H.levels[0].A.shape[0], dtype=torch.float64, device="cuda")
     z2 = torch.empty_like(z1)
     r = to_dev(torch, rng.uniform(-1, 1, H.levels[0].A.shape[0]))

@@ -112,7 +112,7 @@ def vcycle_backward(amg, b, gx, level=0):
 
     def rec(l, bl, xbar):
         if l == nl - 1:
-            y = amg.coarse_solve(xbar)            # A_c^{-1} is symmetric
+            y = amg.coarse_solve(xbar)            # the coarse operator is symmetric
             return y
         A, P, spec, M = amg.A[l], amg.P[l], amg.specs[l], amg.M[l]
         # forward (recomputed): pre, residual, restriction, coarse, prolongation

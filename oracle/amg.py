@@ -22,13 +22,18 @@ from .smoother import SmootherSpec, l1_diag, smooth
 class OracleAMG:
     """Hierarchy (A_l, P_l) plus one smoother spec per level."""
 
-    def __init__(self, A_list, P_list, specs):
+    def __init__(self, A_list, P_list, specs, coarse_sweeps=0):
+        """coarse_sweeps = 0: the coarsest level is solved by a dense Cholesky
+        factorisation; m > 0: by m l1-Jacobi sweeps from zero, the coarse
+        solver of the paper's experiments (Sec. 4, 30 sweeps)."""
         self.A = [sp.csr_matrix(A) for A in A_list]
         self.P = [sp.csr_matrix(P) for P in P_list]
         if isinstance(specs, SmootherSpec):
             specs = [specs] * (len(self.A) - 1)
         self.specs = list(specs)
         self.M = [l1_diag(A) for A in self.A[:-1]]
+        self.coarse_sweeps = int(coarse_sweeps)
+        self.Mc = l1_diag(self.A[-1])
         Ac = self.A[-1].toarray()
         # Cholesky of the coarsest matrix; raises LinAlgError if not SPD
         self.L = np.linalg.cholesky(Ac)
@@ -38,6 +43,9 @@ class OracleAMG:
         return len(self.A)
 
     def coarse_solve(self, b):
+        if self.coarse_sweeps > 0:
+            spec = SmootherSpec("l1jacobi", self.coarse_sweeps)
+            return smooth(self.A[-1], b, None, spec, M=self.Mc)
         y = sla.solve_triangular(self.L, b, lower=True)
         return sla.solve_triangular(self.L.T, y, lower=False)
 

@@ -193,3 +193,41 @@ def test_fcg1_textbook_cases():
     _, it_ok, _, _ = amg.fcg1(b, rtol=1e-10, precond=lambda r: M @ r)
     _, it_pcg, _, _ = amg.pcg(b, rtol=1e-10, precond=lambda r: M @ r)
     assert it_ok == it_pcg
+
+
+def test_coarse_l1jacobi_sweeps_dense_composition():
+    # coarsest level solved by m l1-Jacobi sweeps from zero (Sec. 4): the
+    # coarse operator is Q_m = sum_{j<m} (I - M^{-1}A_c)^j M^{-1}
+    A, Pl = hier(pr.varcoef(8, 1.0, 2.0, seed=5), 64)
+    assert len(A) == 2
+    spec = SmootherSpec("cheb4_opt", 2)
+    m = 7
+    amg = OracleAMG(A, Pl, spec, coarse_sweeps=m)
+    Ac = A[-1].toarray()
+    Minv = np.diag(1.0 / l1_diag(A[-1]))
+    E = np.eye(Ac.shape[0]) - Minv @ Ac
+    Q = sum(np.linalg.matrix_power(E, j) for j in range(m)) @ Minv
+    for i in range(Ac.shape[0]):
+        e = np.zeros(Ac.shape[0])
+        e[i] = 1.0
+        assert np.allclose(amg.coarse_solve(e), Q[:, i], rtol=0, atol=1e-14)
+    # two-level dense reference with Q_m in place of A_c^{-1}
+    n = A[0].shape[0]
+    B = dense_B(amg)
+    Ad, Pd = A[0].toarray(), Pl[0].toarray()
+    G = dense_G(A[0], spec)
+    Eref = G @ (np.eye(n) - Pd @ Q @ Pd.T @ Ad) @ G
+    assert np.max(np.abs(np.eye(n) - B @ Ad - Eref)) <= 1e-12
+    assert np.max(np.abs(B - B.T)) <= 1e-12 * np.abs(B).max()
+
+
+def test_coarse_sweeps_converge_to_exact_coarse_solve():
+    A, Pl = hier(pr.poisson(8), 8)
+    spec = SmootherSpec("cheb4", 2)
+    exact = OracleAMG(A, Pl, spec)
+    many = OracleAMG(A, Pl, spec, coarse_sweeps=3000)
+    r = pr.rhs_uniform(A[0].shape[0], seed=3)
+    assert np.allclose(many.vcycle(r), exact.vcycle(r), rtol=0, atol=1e-10)
+    b = pr.rhs_uniform(A[0].shape[0], seed=1)
+    _, it30, rel, _ = OracleAMG(A, Pl, spec, coarse_sweeps=30).pcg(b, rtol=1e-8)
+    assert rel <= 1e-8 and it30 < 100

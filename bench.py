@@ -301,6 +301,17 @@ def run_sa_c1(a, torch):
         out[f"{kind}_k{k}"] = {"iterations": it, "ms": round(ms, 3), "relres": rel,
                                "true_relres": true,
                                "oracle_iterations": gold.get((a.grid, kind, k))}
+    # the paper's solver setting (Sec. 4): 30 l1-Jacobi sweeps on the coarsest
+    # level, flexible CG with one reduction per iteration, tolerance 1e-7 (on
+    # the residual here; the paper states it on the error)
+    S.set_coarse_sweeps(30)
+    S.set_flexible("fcg1")
+    paper = {}
+    for kind, k in (("cheb4_opt", 4), ("cheb1_opt", 4), ("l1jacobi", 4)):
+        S.set_smoother(-1, kind, k)
+        it, ms, rel = timed_solve(S, bd, x, 1e-7, torch)
+        paper[f"{kind}_k{k}"] = {"iterations": it, "ms": round(ms, 3), "relres": rel}
+    out["paper_setting_coarse30_fcg1_rtol1e-7"] = paper
     S.close()
     return out
 

@@ -300,8 +300,12 @@ amgps_status amgps_synchronize(amgps_ctx* ctx);
  *      of Sec. 4: w = A z, then rho = z.r, gamma = z.q, delta = z.w in one
  *      reduction; beta = gamma / eta_old, p = z - beta p, q = w - beta q
  *      (q = A p kept by recurrence), eta = delta - beta gamma, alpha = rho/eta.
- *      Other values: AMGPS_E_ARG. */
-enum { AMGPS_OPT_TMA = 1, AMGPS_OPT_FLEXIBLE = 2 };
+ *      Other values: AMGPS_E_ARG.
+ * AMGPS_OPT_COARSE_SWEEPS (default 0): the coarsest level of the V-cycle is
+ * solved with the dense FP64 inverse (0), or by m = 1..1000 l1-Jacobi sweeps
+ * from zero, x <- x + M^{-1}(b - A_c x), the coarse solver of the paper's
+ * experiments (Sec. 4 uses 30); the V-cycle stays symmetric either way. */
+enum { AMGPS_OPT_TMA = 1, AMGPS_OPT_FLEXIBLE = 2, AMGPS_OPT_COARSE_SWEEPS = 3 };
 amgps_status amgps_set_option(amgps_ctx* ctx, int option, int64_t value);
 
 /* Host-only planning query (no device needed): how the TMA-fed step would

@@ -430,6 +430,11 @@ class Solver:
         v = 2 if on == "always" else (1 if on else 0)
         self._check(lib().amgps_set_option(self._h, 1, v))
 
+    def set_coarse_sweeps(self, m):
+        """Coarsest-level solve: 0 = dense inverse (default), m > 0 = m
+        l1-Jacobi sweeps from zero (the paper's coarse solver)."""
+        self._check(lib().amgps_set_option(self._h, 3, int(m)))
+
     OUTER = {"cg": 0, "flexible": 1, "fcg1": 2}
 
     def set_flexible(self, on):

@@ -465,6 +465,7 @@ struct amgps_ctx {
   int64_t graph_kernels = 0;   // kernel nodes in gexec
   int use_tma = 1;             // TMA-fed step kernels (option AMGPS_OPT_TMA: 0 off, 1 auto, 2 always)
   int flexible = 0;            // AMGPS_OPT_FLEXIBLE: 0 standard, 1 Polak-Ribiere, 2 one-reduction
+  int coarse_sweeps = 0;       // AMGPS_OPT_COARSE_SWEEPS: 0 dense Cholesky, m l1-Jacobi sweeps
   int64_t launch_adjust = 0;   // captured (not run) launches removed, replays added
   int64_t launch_base = 0;     // reset point of the launch counter
   bool prof = false;
@@ -787,13 +788,28 @@ struct Engine {
     check_launch();
   }
 
+  // Coarsest level: x = A_c^{-1} b (dense inverse), or with the coarse-sweeps
+  // option x = m l1-Jacobi sweeps from zero (the coarse solver of Sec. 4);
+  // both operators are symmetric.
+  static void coarse_solve(amgps_ctx* c, int l, const XT* b, XT* x) {
+    Level& L = c->lv[l];
+    if (c->coarse_sweeps > 0) {
+      Coefs cf;
+      cf.fam = FAM_JAC;
+      cf.k = c->coarse_sweeps;
+      smooth(c, l, cf, b, x, true);
+    } else {
+      launch_coarse_gemv<XT>((int)L.n, L.ainv, b, x, c->stream);
+      check_launch();
+    }
+  }
+
   // record: keep each level's post-smoother input (for the reverse pass)
   static void vcycle_level(amgps_ctx* c, int l, const XT* b, XT* x, bool record = false) {
     Level& L = c->lv[l];
     cudaStream_t s = c->stream;
     if (L.coarsest) {
-      launch_coarse_gemv<XT>((int)L.n, L.ainv, b, x, s);
-      check_launch();
+      coarse_solve(c, l, b, x);
       return;
     }
     const Coefs cf = make_coefs(L.spec.kind, L.spec.k, L.spec.w, L.spec.rho);
@@ -930,8 +946,7 @@ struct Engine {
     Level& L = c->lv[l];
     cudaStream_t s = c->stream;
     if (L.coarsest) {
-      launch_coarse_gemv<XT>((int)L.n, L.ainv, xbar, gbout, s);  // A_c^{-1} is symmetric
-      check_launch();
+      coarse_solve(c, l, xbar, gbout);  // the coarse operator is symmetric
       return;
     }
     const Coefs cf = make_coefs(L.spec.kind, L.spec.k, L.spec.w, L.spec.rho);
@@ -1595,8 +1610,8 @@ amgps_status amgps_hierarchy_load(amgps_ctx* c, int n_levels, const amgps_csr* A
         CK(cudaMemcpyAsync(&hstat, dstat, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
         REQ(hstat == 0, AMGPS_E_NOT_SPD, "coarsest matrix: Cholesky pivot not positive");
-        // a single-level hierarchy also needs the SELL form of A_0 for the PCG SpMV
-        if (l > 0) continue;
+        // the coarsest level also keeps its SELL form and 1/M: for the PCG
+        // SpMV of a single-level hierarchy and for l1-Jacobi coarse sweeps
       }
       HostSell h = build_sell(A[l]);
       L.split = split_for(h.stored, h.nslices);
@@ -1636,8 +1651,7 @@ amgps_status amgps_hierarchy_load(amgps_ctx* c, int n_levels, const amgps_csr* A
         L.col64 = L.col;
         L.val64 = dupload(c, h.val.data(), h.val.size());
       }
-      if (L.coarsest) continue;  // single-level hierarchy: SELL for the PCG SpMV only
-      if (prec == AMGPS_F64) {
+      if (prec == AMGPS_F64 && !L.coarsest) {
         // row-scaled copy a_ij / M_i, M_i = sum_j |a_ij| (the l1 diagonal)
         std::vector<double> m((size_t)L.n, 0.0);
         for (int64_t i = 0; i < L.n; ++i)
@@ -1663,6 +1677,7 @@ amgps_status amgps_hierarchy_load(amgps_ctx* c, int n_levels, const amgps_csr* A
       else if (prec == AMGPS_F32) launch_l1diag<float, float>(devmat<float>(L), (float*)L.dinv, c->stream);
       else launch_l1diag<__nv_bfloat16, float>(devmat<__nv_bfloat16>(L), (float*)L.dinv, c->stream);
       check_launch();
+      if (L.coarsest) continue;
       const amgps_csr& Pl = P[l];
       const int64_t nc = Pl.n_cols;
       L.nc = nc;
@@ -2098,14 +2113,19 @@ amgps_status amgps_synchronize(amgps_ctx* c) {
 amgps_status amgps_set_option(amgps_ctx* c, int option, int64_t value) {
   return guard(c, [&] {
     REQ(c, AMGPS_E_ARG, "null context");
-    REQ(option == AMGPS_OPT_TMA || option == AMGPS_OPT_FLEXIBLE, AMGPS_E_ARG, "unknown option");
+    REQ(option == AMGPS_OPT_TMA || option == AMGPS_OPT_FLEXIBLE || option == AMGPS_OPT_COARSE_SWEEPS,
+        AMGPS_E_ARG, "unknown option");
     if (option == AMGPS_OPT_TMA) {
       REQ(value >= 0 && value <= 2, AMGPS_E_ARG, "AMGPS_OPT_TMA takes 0, 1 or 2");
       c->use_tma = (int)value;
       c->graph_ok = false;
-    } else {
+    } else if (option == AMGPS_OPT_FLEXIBLE) {
       REQ(value >= 0 && value <= 2, AMGPS_E_ARG, "AMGPS_OPT_FLEXIBLE takes 0, 1 or 2");
       c->flexible = (int)value;
+    } else {
+      REQ(value >= 0 && value <= 1000, AMGPS_E_ARG, "AMGPS_OPT_COARSE_SWEEPS takes 0..1000");
+      c->coarse_sweeps = (int)value;
+      c->graph_ok = false;  // the coarse-level graph holds the coarse solve
     }
   });
 }

@@ -403,3 +403,38 @@ def test_fcg1_iterations_identical(torch_cuda, prec):
     S.set_flexible("cg")
     it_cg, _ = S.pcg(to_dev(torch, b), x, rtol=1e-9)
     assert abs(it_cg - it) <= 1
+
+
+def test_coarse_l1jacobi_sweeps(torch_cuda):
+    # the paper's coarse solver (m l1-Jacobi sweeps from zero) against the
+    # oracle: V-cycle, PCG counts, reverse mode; switching back restores the
+    # dense coarse solve (the coarse-level graph is rebuilt)
+    from oracle.adjoint import vcycle_backward
+    from paper_2407_09848_gb300.amgps import Solver
+    torch = torch_cuda
+    H = pr.build_hierarchy(pr.varcoef(20, 1.0, 4.0, seed=11, ny=18, nz=13), coarse_max=200)
+    S = Solver().load(H.A, H.P)
+    n = H.A[0].shape[0]
+    r = pr.vec_uniform(n, seed=4)
+    z = torch.empty(n, dtype=torch.float64, device="cuda")
+    z0 = torch.empty_like(z)
+    S.vcycle(to_dev(torch, r), z0)
+    for m in (1, 30):
+        S.set_coarse_sweeps(m)
+        ora = OracleAMG(H.A, H.P, SmootherSpec("cheb4_opt", 4), coarse_sweeps=m)
+        S.vcycle(to_dev(torch, r), z)
+        assert rel(to_np(z), ora.vcycle(r)) <= TOL
+        b = pr.rhs_uniform(n, seed=0)
+        x = torch.empty_like(z)
+        it, relres = S.pcg(to_dev(torch, b), x, rtol=1e-9)
+        _, ito, _, _ = ora.pcg(b, rtol=1e-9)
+        assert it == ito and relres <= 1e-9
+    gz = pr.vec_uniform(n, seed=8)
+    gr, _ = S.vcycle_backward(to_dev(torch, r), to_dev(torch, gz))
+    rr, _ = vcycle_backward(OracleAMG(H.A, H.P, SmootherSpec("cheb4_opt", 4), coarse_sweeps=30), r, gz)
+    assert rel(gr.cpu().numpy(), rr) <= TOL
+    S.set_coarse_sweeps(0)
+    S.vcycle(to_dev(torch, r), z)
+    S.synchronize()
+    assert torch.equal(z, z0)
+    S.close()

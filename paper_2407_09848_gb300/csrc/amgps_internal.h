@@ -80,10 +80,9 @@ struct StepArgs {
   bool rin_raw = false;
 };
 
-// Warps per slice for a level whose rows are wide (the split form of the
-// step and transfer kernels): 1 below 48 stored entries per row on average,
-// else the power of two nearest (avg / 32), at most kMaxSplit.
-constexpr int kMaxSplit = 16;
+// Most warps per slice in the split form of the step and transfer kernels
+// (levels with wide rows; the factor per level is chosen at load).
+constexpr int kMaxSplit = 32;
 
 // ---- TMA-fed step (kernels_tma.cu) ----
 // A tile is `rows` consecutive rows (a multiple of 32 slices' worth, up to

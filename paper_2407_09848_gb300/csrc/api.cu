@@ -170,16 +170,29 @@ void validate_csr(const amgps_csr& A, const char* what, bool square) {
   }
 }
 
-// Warps per slice for the split kernels: 1 while rows average under 48
-// stored entries, else the power of two nearest avg / 32, at most kMaxSplit.
+// Warps per slice for the split kernels (measured on the 256^3
+// smoothed-aggregation levels): 1 while rows average under 24 stored entries;
+// otherwise the larger of a width term (the power of two nearest avg / 32 once
+// avg >= 48) and a parallelism term (the power of two at or below
+// 24576 / slices, so small levels still field ~24k warps), capped at avg / 8
+// entries per warp and kMaxSplit.
 int split_for(int64_t stored, int64_t nslices) {
   if (nslices == 0) return 1;
   const double avg = (double)stored / ((double)nslices * kSlice);
-  if (avg < 48.0) return 1;
-  int g = 1;
-  while (g < kMaxSplit && 2.0 * g <= avg / 32.0 * 1.41421356) g *= 2;
-  return std::max(g, 2);
+  if (avg < 24.0) return 1;
+  int g1 = 1;
+  if (avg >= 48.0)
+    while (g1 < kMaxSplit && 2.0 * g1 <= avg / 32.0 * 1.41421356) g1 *= 2;
+  int g2 = 1;
+  while (g2 < kMaxSplit && 2.0 * g2 <= 24576.0 / (double)nslices) g2 *= 2;
+  int cap = 1;
+  while (cap < kMaxSplit && 2.0 * cap <= avg / 8.0) cap *= 2;
+  return std::max(1, std::min(std::max(g1, g2), cap));
 }
+
+// Most column offsets a uniform slice may list (the pattern of the widest
+// coarse operators of smoothed aggregation on a grid still fits).
+constexpr int64_t kUniformMax = 1024;
 
 // allow_uniform = false keeps every slice explicit (required for rectangular
 // matrices: a uniform slice's padding column row + off may fall outside n_cols)
@@ -219,7 +232,8 @@ HostSell build_sell(const amgps_csr& A, bool allow_uniform = true) {
       for (int e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e) offs.push_back((int64_t)A.col[e] - r);
     std::sort(offs.begin(), offs.end());
     offs.erase(std::unique(offs.begin(), offs.end()), offs.end());
-    const bool uniform = allow_uniform && (int64_t)offs.size() <= maxlen + 1 && offs.size() <= 64;
+    const bool uniform =
+        allow_uniform && (int64_t)offs.size() <= maxlen + 1 && (int64_t)offs.size() <= kUniformMax;
     if (uniform) {
       std::vector<int32_t> p(offs.begin(), offs.end());
       auto it = pats.find(p);
@@ -246,19 +260,20 @@ HostSell build_sell(const amgps_csr& A, bool allow_uniform = true) {
   h.val.assign(vbase, 0.0);
   if (h.any_explicit) h.col.assign(vbase, 0);
   std::vector<std::pair<int32_t, double>> rowbuf;
+  std::vector<uint8_t> filled(kUniformMax);
   for (int64_t s = 0; s < h.nslices; ++s) {
     const SliceDesc d = h.sd[s];
     const int64_t r0 = s * kSlice, r1 = std::min(n, r0 + kSlice);
     for (int64_t r = r0; r < r1; ++r) {
       const int lane = (int)(r - r0);
       if (d.cref >= 0) {
-        uint64_t filled = 0;
+        std::fill(filled.begin(), filled.begin() + d.w, uint8_t(0));
         for (int e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e) {
           const int32_t o = (int32_t)((int64_t)A.col[e] - r);
           const int32_t* p = h.off.data() + d.cref;
           const int k = (int)(std::lower_bound(p, p + d.w, o) - p);
-          REQ(!(filled >> k & 1u), AMGPS_E_ARG, "duplicate entry in CSR row");
-          filled |= uint64_t(1) << k;
+          REQ(!filled[k], AMGPS_E_ARG, "duplicate entry in CSR row");
+          filled[k] = 1;
           h.val[d.vbase + (int64_t)k * kSlice + lane] = A.val[e];
         }
       } else {

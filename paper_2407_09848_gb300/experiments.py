@@ -6,7 +6,11 @@ b = A 1) when the preconditioner is one application of the optimised
 alone, on A = Q D Q^T with equispaced, boundary-clustered and gapped spectra,
 for several sizes and degrees.  The paper shows these counts only as images.
 
+sa_solve: PCG on a smoothed-aggregation hierarchy built on the GPU (a short
+fixed command for profiling that path).
+
 CLI:  python -m paper_2407_09848_gb300.experiments smoother_only
+      python -m paper_2407_09848_gb300.experiments sa_solve [grid]
 """
 from __future__ import annotations
 
@@ -41,13 +45,43 @@ def smoother_only(sizes=(128, 256, 512, 1024), degrees=(1, 2, 3, 4, 5, 6, 8, 10,
     return out
 
 
+def sa_solve(grid=256, kind="cheb4_opt", degree=4, solves=2, rtol=1e-8):
+    """Smoothed-aggregation hierarchy of the grid^3 Poisson problem built on
+    the GPU, then `solves` PCG solves (the first one warms up): iterations and
+    the last solve's time.  A fixed, short command for profiling the SA path."""
+    import time
+    import torch
+    from .amgps import Solver
+    st = pr.poisson(grid)
+    builder = Solver()
+    As, Ps, _ = builder.sa_hierarchy(pr.to_csr(st), pr.geometric_aggregates(st.shape, 512))
+    builder.close()
+    S = Solver().load(As, Ps)
+    S.set_smoother(-1, kind, degree)
+    b = torch.from_numpy(pr.rhs_uniform(As[0].shape[0], seed=0)).cuda()
+    x = torch.empty_like(b)
+    out = {}
+    for _ in range(solves):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        it, rel = S.pcg(b, x, rtol=rtol)
+        torch.cuda.synchronize()
+        out = {"grid": grid, "kind": kind, "degree": degree, "iterations": it, "relres": rel,
+               "ms": 1e3 * (time.perf_counter() - t)}
+    S.close()
+    return out
+
+
 def main(argv):
-    if len(argv) < 1 or argv[0] != "smoother_only":
-        print(__doc__)
-        return 2
-    rows = smoother_only()
-    print(json.dumps(rows))
-    return 0
+    if len(argv) >= 1 and argv[0] == "smoother_only":
+        print(json.dumps(smoother_only()))
+        return 0
+    if len(argv) >= 1 and argv[0] == "sa_solve":
+        grid = int(argv[1]) if len(argv) > 1 else 256
+        print(json.dumps(sa_solve(grid)))
+        return 0
+    print(__doc__)
+    return 2
 
 
 if __name__ == "__main__":

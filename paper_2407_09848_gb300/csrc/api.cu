@@ -1231,7 +1231,8 @@ void pcg_impl(amgps_ctx* c, const double* b, double* x, double rtol, int maxit, 
       launch_spmv_dot(A, c->pp, c->pq, rw_spmv, c->dscal, s);
       ps.done();
     }
-    launch_cg_update(n, c->pp, c->pq, x, c->pr, rw_upd, c->dscal, s);
+    // r -= alpha q now; x += alpha p is deferred to the direction update
+    launch_r_update(n, c->pq, c->pr, rw_upd, c->dscal, s);
     check_launch();
     CK(cudaMemcpyAsync(c->hscal, c->dscal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaEventRecord(c->ev_sync, s));
@@ -1245,13 +1246,16 @@ void pcg_impl(amgps_ctx* c, const double* b, double* x, double rtol, int maxit, 
     REQ(std::isfinite(pq) && std::isfinite(rr), AMGPS_E_NAN, "NaN/Inf in PCG scalars");
     REQ(pq > 0.0, AMGPS_E_NOT_SPD, "p^T A p <= 0 in PCG");
     rel = std::sqrt(rr) / bnorm;
-    if (rel <= rtol) break;
-    if (it == maxit) break;
+    if (rel <= rtol || it == maxit) {
+      launch_xpay_x(n, z, c->pp, x, c->dscal, 0, s);  // the last x update
+      check_launch();
+      break;
+    }
     std::swap(z, zo);
     M(c->pr, z);
     if (c->flexible == 1) launch_dot(n, c->pr, zo, rw_dot, c->dscal, S_RZP, 0, s);
     launch_dot(n, c->pr, z, rw_dot, c->dscal, S_RZ, c->flexible == 1 ? 2 : 1, s);
-    launch_xpay(n, z, c->pp, c->dscal, s);
+    launch_xpay_x(n, z, c->pp, x, c->dscal, 1, s);  // x += alpha p; p = z + beta p
     check_launch();
   }
   *iters = std::min(it, maxit);

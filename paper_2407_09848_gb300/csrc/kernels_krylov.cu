@@ -187,6 +187,48 @@ void launch_fcg_update(int64_t n, const double* z, const double* w, double* p, d
   count_launch();
 }
 
+// r -= alpha q ; r.r (S_RR).  The x update of the same iteration is deferred
+// to k_xpay_x, which reads p anyway.
+__global__ void __launch_bounds__(kBlock) k_r_update(int64_t n, const double* __restrict__ q,
+                                                     double* __restrict__ r, const RedWork w,
+                                                     double* scal) {
+  const double alpha = scal[S_ALPHA];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kBlock) {
+    const double ri = fma(-alpha, q[i], r[i]);
+    r[i] = ri;
+    acc = fma(ri, ri, acc);
+  }
+  grid_sum(acc, w, [&](double tot) { scal[S_RR] = tot; });
+}
+
+void launch_r_update(int64_t n, const double* q, double* r, const RedWork& w, double* scal,
+                     cudaStream_t s) {
+  k_r_update<<<w.grid, kBlock, 0, s>>>(n, q, r, w, scal);
+  count_launch();
+}
+
+// x += alpha p with the previous alpha, then p = z + beta p (x_beta = 1), or
+// only x += alpha p (x_beta = 0: the last iteration)
+__global__ void __launch_bounds__(kBlock) k_xpay_x(int64_t n, const double* __restrict__ z,
+                                                   double* __restrict__ p, double* __restrict__ x,
+                                                   const double* __restrict__ scal, int with_p) {
+  const double alpha = scal[S_ALPHA], beta = scal[S_BETA];
+  const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (i >= n) return;
+  const double pi = p[i];
+  x[i] = fma(alpha, pi, x[i]);
+  if (with_p) p[i] = fma(beta, pi, z[i]);
+}
+
+void launch_xpay_x(int64_t n, const double* z, double* p, double* x, const double* scal,
+                   int with_p, cudaStream_t s) {
+  if (n == 0) return;
+  k_xpay_x<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, z, p, x, scal, with_p);
+  count_launch();
+}
+
 __global__ void __launch_bounds__(kBlock) k_dot(int64_t n, const double* __restrict__ a,
                                                 const double* __restrict__ b, const RedWork w,
                                                 double* scal, int slot, int rz_shift) {

@@ -36,6 +36,12 @@ void launch_fcg_update(int64_t n, const double* z, const double* w, double* p, d
                        cudaStream_t s);
 void launch_cg_update(int64_t n, const double* p, const double* q, double* x, double* r,
                       const RedWork& w, double* scal, cudaStream_t s);
+// standard PCG with the x update deferred: r -= alpha q and r.r; later
+// x += alpha p together with p = z + beta p (with_p = 0: x only)
+void launch_r_update(int64_t n, const double* q, double* r, const RedWork& w, double* scal,
+                     cudaStream_t s);
+void launch_xpay_x(int64_t n, const double* z, double* p, double* x, const double* scal,
+                   int with_p, cudaStream_t s);
 // rz_mode 0: scal[out_slot] = a.b.  1: scal[S_RZOLD] <- scal[S_RZ], scal[S_RZ] = a.b,
 // scal[S_BETA] = S_RZ / S_RZOLD.  2: as 1 with the flexible (Polak-Ribiere)
 // beta = (S_RZ - S_RZP) / S_RZOLD.

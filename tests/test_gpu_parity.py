@@ -438,3 +438,48 @@ def test_coarse_l1jacobi_sweeps(torch_cuda):
     S.synchronize()
     assert torch.equal(z, z0)
     S.close()
+
+
+def test_more_input_and_option_errors(torch_cuda):
+    # every case is rejected on the host before a launch (no device fault)
+    from paper_2407_09848_gb300.amgps import AmgpsError, Solver, lib
+    torch = torch_cuda
+    H = pr.build_hierarchy(pr.poisson(8), coarse_max=64)
+    S = Solver().load(H.A, H.P)
+    n = H.A[0].shape[0]
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    bn = to_dev(torch, pr.rhs_uniform(n, seed=0))
+    bn[3] = float("nan")
+    with pytest.raises(AmgpsError) as e:
+        S.pcg(bn, x)
+    assert e.value.name == "AMGPS_E_NAN"
+    for opt, val in ((1, 3), (2, 3), (3, -1), (3, 1001), (9, 0)):
+        assert lib().amgps_set_option(S._h, opt, val) == 1  # AMGPS_E_ARG
+    # zero right-hand side through every outer CG form
+    bz = torch.zeros(n, dtype=torch.float64, device="cuda")
+    for form in ("cg", "flexible", "fcg1"):
+        S.set_flexible(form)
+        it, rr = S.pcg(bz, x)
+        assert it == 0 and torch.count_nonzero(x) == 0
+    S.set_flexible("cg")
+    # smoothed aggregation: aggregate index out of range, empty aggregate
+    A0 = pr.to_csr(pr.poisson(6))
+    (agg, nc, _), = pr.geometric_aggregates((6, 6, 6), coarse_max=64)
+    bad = agg.copy()
+    bad[0] = nc
+    with pytest.raises(AmgpsError) as e:
+        S.sa_level(A0, bad, nc)
+    assert e.value.name == "AMGPS_E_ARG"
+    with pytest.raises(AmgpsError) as e:
+        S.sa_level(A0, agg, nc + 1)  # coarse index nc has no fine point
+    assert e.value.name == "AMGPS_E_ARG"
+    # smoother-only PCG needs a level with a smoother
+    H1 = pr.build_hierarchy(pr.poisson(3), coarse_max=512)
+    S1 = Solver().load(H1.A, H1.P)
+    b1 = to_dev(torch, pr.rhs_uniform(27, seed=1))
+    x1 = torch.zeros(27, dtype=torch.float64, device="cuda")
+    with pytest.raises(AmgpsError) as e:
+        S1.pcg_smoother("cheb4_opt", 2, b1, x1)
+    assert e.value.name == "AMGPS_E_ARG"
+    S1.close()
+    S.close()

@@ -126,8 +126,8 @@ struct Level {
   int psplit = 1, rsplit = 1;
   int split = 1;  // warps per slice of the generic step kernel (wide rows)
   void* dinv = nullptr;   // 1 / M_i
-  // FP64 levels: the row-scaled values a_ij / M_i in the layout of `val`,
-  // used by the 4th-kind steps (their residual is kept scaled)
+  // FP64 and FP32 levels: the row-scaled values a_ij / M_i in the layout and
+  // type of `val`, used by the polynomial steps (their residual is kept scaled)
   void* sval = nullptr;
   void *b = nullptr, *x = nullptr, *r = nullptr, *za = nullptr, *zb = nullptr, *xb = nullptr;
   double* ainv = nullptr;
@@ -1670,8 +1670,10 @@ amgps_status amgps_hierarchy_load(amgps_ctx* c, int n_levels, const amgps_csr* A
         L.col64 = L.col;
         L.val64 = dupload(c, h.val.data(), h.val.size());
       }
-      if (prec == AMGPS_F64 && !L.coarsest) {
-        // row-scaled copy a_ij / M_i, M_i = sum_j |a_ij| (the l1 diagonal)
+      if ((prec == AMGPS_F64 || prec == AMGPS_F32) && !L.coarsest) {
+        // row-scaled copy a_ij / M_i, M_i = sum_j |a_ij| (the l1 diagonal), in
+        // the level's value type (BF16 levels keep A: a_ij / M_i is rarely exact
+        // in BF16 where a_ij is)
         std::vector<double> m((size_t)L.n, 0.0);
         for (int64_t i = 0; i < L.n; ++i)
           for (int e = A[l].rowptr[i]; e < A[l].rowptr[i + 1]; ++e) m[i] += std::fabs(A[l].val[e]);
@@ -1685,7 +1687,13 @@ amgps_status amgps_hierarchy_load(amgps_ctx* c, int n_levels, const amgps_csr* A
               if (row < L.n) sv[e] = h.val[e] / m[row];
             }
         }
-        L.sval = dupload(c, sv.data(), sv.size());
+        if (prec == AMGPS_F64) {
+          L.sval = dupload(c, sv.data(), sv.size());
+        } else {
+          std::vector<float> svf(sv.size());
+          for (size_t i = 0; i < sv.size(); ++i) svf[i] = (float)sv[i];
+          L.sval = dupload(c, svf.data(), svf.size());
+        }
       }
       L.dinv = dalloc(c, L.n * xs);
       L.r = dalloc(c, L.n * xs);

@@ -2,15 +2,18 @@
 // solve, and the power-iteration estimate.  All reductions are deterministic
 // (fixed grid, fixed summation tree: see grid_sum), so a solve repeated on
 // the same input performs the same iterations bit for bit.
+#include <atomic>
+
 #include "kernels_common.cuh"
 
 namespace amgps {
 
 namespace {
-int64_t g_launches = 0;
+// kernels enqueued by this process (all contexts, all host threads)
+std::atomic<int64_t> g_launches{0};
 }
-int64_t launches_enqueued() { return g_launches; }
-void count_launch() { ++g_launches; }
+int64_t launches_enqueued() { return g_launches.load(std::memory_order_relaxed); }
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 int reduction_grid(int64_t work_items, int nsm) {
   int64_t g = (work_items + kBlock - 1) / kBlock;

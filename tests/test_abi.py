@@ -109,3 +109,28 @@ def test_tma_plan_rejects_bad_csr(lib):
     A.indices[0] = 5  # column out of range
     with pytest.raises(amgps.AmgpsError):
         amgps.tma_plan_stats(A, "f64")
+
+
+def test_layout_of_wide_smoothed_aggregation_levels(lib):
+    # host-only: a smoothed-aggregation coarse level (the oracle's product, up to
+    # 168 offsets per row) goes through the SELL builder's wide uniform path;
+    # stencils wider than the TMA window limit are left to the direct kernel
+    import scipy.sparse as sp
+    from oracle import sa
+    from paper_2407_09848_gb300 import problems as pr
+    st = pr.poisson(32)
+    levels = pr.geometric_aggregates(st.shape, coarse_max=512)
+    As, _, _ = sa.sa_hierarchy(pr.to_csr(st), [a for a, _, _ in levels],
+                               [nc for _, nc, _ in levels])
+    for A in As[1:]:
+        A = sp.csr_matrix(A)
+        assert np.diff(A.indptr).max() > 8
+        tiles, gen, _, _ = amgps.tma_plan_stats(A, "f64")
+        assert tiles == 0 and gen == (A.shape[0] + 31) // 32
+    # a duplicated entry in a wide row is rejected
+    A = sp.csr_matrix(As[1]).sorted_indices()
+    r0 = A.indptr[100]
+    dup = A.copy()
+    dup.indices[r0 + 1] = dup.indices[r0]
+    with pytest.raises(amgps.AmgpsError):
+        amgps.tma_plan_stats(dup, "f64")

@@ -200,3 +200,29 @@ def test_device_built_sa_hierarchy_pcg(solver, grid):
     _, ito, _, _ = OracleAMG(Aso, Pso, SmootherSpec("cheb4_opt", 4)).pcg(b, rtol=1e-8)
     assert it == ito and rel <= 1e-8
     S.close()
+
+
+@pytest.mark.parametrize("grid", [32, 64])
+def test_paper_setting_iterations_match_oracle(solver, grid):
+    # Sec. 4's solver setting on the device-built SA hierarchy: 30 l1-Jacobi
+    # coarse sweeps, one-reduction flexible CG, tolerance 1e-7; counts equal
+    # the oracle's on its own host-built hierarchy
+    torch = pytest.importorskip("torch")
+    from paper_2407_09848_gb300.amgps import Solver
+    st = pr.poisson(grid)
+    levels = pr.geometric_aggregates(st.shape, coarse_max=512)
+    As, Ps, _ = solver.sa_hierarchy(pr.to_csr(st), levels)
+    Aso, Pso, _ = sa.sa_hierarchy(pr.to_csr(st), [a for a, _, _ in levels],
+                                  [nc for _, nc, _ in levels])
+    S = Solver().load(As, Ps)
+    S.set_coarse_sweeps(30)
+    S.set_flexible("fcg1")
+    b = pr.rhs_uniform(As[0].shape[0], seed=0)
+    x = torch.empty(As[0].shape[0], dtype=torch.float64, device="cuda")
+    for kind, k in (("cheb4_opt", 4), ("cheb1_opt", 4), ("l1jacobi", 4)):
+        S.set_smoother(-1, kind, k)
+        it, rel = S.pcg(dev(torch, b), x, rtol=1e-7)
+        xo, ito, _, _ = OracleAMG(Aso, Pso, SmootherSpec(kind, k), coarse_sweeps=30).fcg1(b, rtol=1e-7)
+        assert it == ito and rel <= 1e-7, (kind, it, ito)
+        assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-6 * np.linalg.norm(xo)
+    S.close()

@@ -93,7 +93,8 @@ def _jacobi_backward(A, b, x0, k, M, gx):
 
 
 def smooth_backward(A, b, x0, spec: SmootherSpec, gx, M=None):
-    """(dL/db, dL/dx0, dL/dbeta or None) of one application x = S(b, x0)."""
+    """(dL/db, dL/dx0, dL/dbeta or None) of one application x = S(b, x0) of the
+    smoothers of Sec. 2.1-2.2 (Eq. polsmoother, Eq. polsmootheropt, Algorithm 1)."""
     M = l1_diag(A) if M is None else M
     kd = spec.kind
     if kd == "l1jacobi":
@@ -142,8 +143,9 @@ def vcycle_backward(amg, b, gx, level=0):
 
 def error_reduction_loss(amg, E0):
     """Mean over the columns e0 of E0 of ||E e0||_A^2 / ||e0||_A^2 with
-    E = I - B A (one V-cycle), and its gradient with respect to every level's
-    weights.  Returns (loss, [dL/dbeta_l])."""
+    E = I - B A (one V-cycle of Eq. amg), and its gradient with respect to every
+    level's weights (the loss has no counterpart in the paper; it drives the
+    learned weights).  Returns (loss, [dL/dbeta_l])."""
     A = amg.A[0]
     m = E0.shape[1]
     loss = 0.0

@@ -20,7 +20,7 @@ from .smoother import SmootherSpec, l1_diag, smooth
 
 
 class OracleAMG:
-    """Hierarchy (A_l, P_l) plus one smoother spec per level."""
+    """Hierarchy (A_l, P_l) of Sec. 2 plus one smoother spec per level (Eq. amg)."""
 
     def __init__(self, A_list, P_list, specs, coarse_sweeps=0):
         """coarse_sweeps = 0: the coarsest level is solved by a dense Cholesky
@@ -43,6 +43,8 @@ class OracleAMG:
         return len(self.A)
 
     def coarse_solve(self, b):
+        """Coarsest level of Eq. amg: exact (Cholesky), or the l1-Jacobi sweeps
+        of Sec. 4 when coarse_sweeps > 0."""
         if self.coarse_sweeps > 0:
             spec = SmootherSpec("l1jacobi", self.coarse_sweeps)
             return smooth(self.A[-1], b, None, spec, M=self.Mc)

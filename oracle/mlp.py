@@ -32,7 +32,8 @@ def unpack(theta):
 
 
 def forward(theta, F, beta_ref):
-    """F: (B, 8) features.  Returns beta (B, 4) and the cache for backward."""
+    """F: (B, 8) features.  Returns beta (B, 4) and the cache for backward (no
+    counterpart in the paper)."""
     P = unpack(theta)
     a1 = F @ P["W1"].T + P["b1"]
     h1 = np.maximum(a1, 0.0)
@@ -45,7 +46,8 @@ def forward(theta, F, beta_ref):
 
 
 def backward(theta, cache, gbeta):
-    """dL/dtheta given dL/dbeta (B, 4), by the chain rule through the layers."""
+    """dL/dtheta given dL/dbeta (B, 4), by the chain rule through the layers (no
+    counterpart in the paper)."""
     P = unpack(theta)
     F, a1, h1, a2, h2, t, beta = cache
     go = gbeta * beta * 0.5 * (1.0 - t * t)          # d beta / d o
@@ -63,7 +65,7 @@ def backward(theta, cache, gbeta):
 
 
 def adam(theta, grad, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
-    """One Adam step (step counts from 1).  Returns new (theta, m, v)."""
+    """One textbook Adam step (step counts from 1).  Returns new (theta, m, v)."""
     m = b1 * m + (1 - b1) * grad
     v = b2 * v + (1 - b2) * grad * grad
     mh = m / (1 - b1 ** step)

@@ -286,5 +286,6 @@ def _interior_maxima(beta, k):
 
 
 def gamma_opt4(beta):
-    """gamma of the optimised 4th-kind polynomial with weights ``beta``."""
+    """gamma of the optimised 4th-kind polynomial with weights ``beta``: the
+    objective of Eq. prob1 (Sec. 2.1)."""
     return gamma_sup(lambda x: p_opt4(beta, x), opt4_pprime0(beta))

@@ -22,20 +22,21 @@ import scipy.sparse as sp
 
 
 def tentative(agg, n_coarse):
-    """P_hat: one unit entry per fine row, in column agg[i]."""
+    """P_hat of Sec. 4: one unit entry per fine row, in column agg[i]."""
     agg = np.asarray(agg, dtype=np.int64)
     n = agg.size
     return sp.csr_matrix((np.ones(n), (np.arange(n), agg)), shape=(n, n_coarse))
 
 
 def lambda_bound(A):
-    """max_i sum_j |a_ij| / a_ii  (>= every eigenvalue of D^{-1} A)."""
+    """max_i sum_j |a_ij| / a_ii  (>= every eigenvalue of D^{-1} A): the estimate of
+    lambda_max of D^{-1} A in omega = 4/(3 lambda_max), Sec. 4."""
     A = sp.csr_matrix(A)
     return float(np.max(np.asarray(abs(A).sum(axis=1)).ravel() / A.diagonal()))
 
 
 def sa_prolongator(A, agg, n_coarse):
-    """Returns (P, omega): P = (I - omega D^{-1} A) P_hat."""
+    """Returns (P, omega): P = (I - omega D^{-1} A) P_hat (Sec. 4)."""
     A = sp.csr_matrix(A)
     omega = 4.0 / (3.0 * lambda_bound(A))
     Ph = tentative(agg, n_coarse)
@@ -44,13 +45,14 @@ def sa_prolongator(A, agg, n_coarse):
 
 
 def galerkin(A, P):
-    """A_c = P^T A P."""
+    """A_c = P^T A P, the Galerkin product of Sec. 2."""
     P = sp.csr_matrix(P)
     return sp.csr_matrix(P.T @ (sp.csr_matrix(A) @ P))
 
 
 def sa_hierarchy(A0, aggs, n_coarse):
-    """Levels A_0..A_L and prolongators P_0..P_{L-1} from per-level aggregates."""
+    """Levels A_0..A_L and prolongators P_0..P_{L-1} from per-level aggregates
+    (smoothed aggregation of Sec. 4, Galerkin products of Sec. 2)."""
     As, Ps, omegas = [sp.csr_matrix(A0)], [], []
     for agg, nc in zip(aggs, n_coarse):
         P, om = sa_prolongator(As[-1], agg, nc)

@@ -34,7 +34,8 @@ def l1_diag(A):
 
 
 def power_lambda(A, v0, iters=10, M=None):
-    """Spectral estimate of M^{-1}A by ``iters`` power steps.
+    """Spectral estimate of M^{-1}A by ``iters`` power steps (the rho of kind
+    CHEB1; Sec. 3 replaces rho(M^{-1}A) by 1 for the other kinds).
 
     v_0 = v0/||v0||_2; for i = 1..iters: w = M^{-1} A v_{i-1},
     lambda_i = ||w||_2, v_i = w / lambda_i.  Returns lambda_iters.  (The paper
@@ -127,7 +128,8 @@ def l1jacobi(A, b, x0, k, M=None):
 
 
 class SmootherSpec:
-    """Kind, degree and the scalars a kind needs on one level."""
+    """Kind, degree and the scalars a kind needs on one level (the smoothers of
+    Sec. 2.1-2.2 and the l1-Jacobi baseline of Eq. l1smooth)."""
 
     def __init__(self, kind, k, beta=None, rho=1.0, a=None):
         if kind not in KINDS:
@@ -154,7 +156,8 @@ def opt4_table(k):
 
 
 def smooth(A, b, x0, spec: SmootherSpec, M=None):
-    """One smoother application: returns x after ``spec.k`` steps from x0
+    """One smoother application (Eq. polsmoother, Eq. polsmootheropt,
+    Algorithm 1 or Eq. l1smooth by kind): returns x after ``spec.k`` steps from x0
     (x0 None means the zero vector)."""
     kd = spec.kind
     if kd == "l1jacobi":

@@ -1357,10 +1357,14 @@ amgps_status amgps_hierarchy_load(amgps_ctx* c, int n_levels, const amgps_csr* A
         // the level's value type (BF16 levels keep A: a_ij / M_i is rarely exact
         // in BF16 where a_ij is)
         std::vector<double> m((size_t)L.n, 0.0);
-        for (int64_t i = 0; i < L.n; ++i)
-          for (int e = A[l].rowptr[i]; e < A[l].rowptr[i + 1]; ++e) m[i] += std::fabs(A[l].val[e]);
+        const amgps_csr& Al = A[l];
+        parallel_for(L.n, [&](int64_t i, int) {
+          double acc = 0.0;
+          for (int e = Al.rowptr[i]; e < Al.rowptr[i + 1]; ++e) acc += std::fabs(Al.val[e]);
+          m[i] = acc;
+        });
         std::vector<double> sv(h.val.size(), 0.0);
-        for (int64_t sl = 0; sl < h.nslices; ++sl) {
+        parallel_for(h.nslices, [&](int64_t sl, int) {
           const SliceDesc d = h.sd[sl];
           for (int k = 0; k < d.w; ++k)
             for (int ln = 0; ln < kSlice; ++ln) {
@@ -1368,7 +1372,7 @@ amgps_status amgps_hierarchy_load(amgps_ctx* c, int n_levels, const amgps_csr* A
               const int64_t e = d.vbase + (int64_t)k * kSlice + ln;
               if (row < L.n) sv[e] = h.val[e] / m[row];
             }
-        }
+        });
         if (prec == AMGPS_F64) {
           L.sval = dupload(c, sv.data(), sv.size());
         } else {

@@ -2,8 +2,11 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <exception>
+#include <functional>
 #include <map>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "host_check.h"
@@ -16,6 +19,34 @@ int64_t floor_to(int64_t x, int64_t a) { return x >= 0 ? x / a * a : -((-x + a -
 int64_t ceil_to(int64_t x, int64_t a) { return -floor_to(-x, a); }
 
 }  // namespace
+
+int parallel_threads(int64_t count) {
+  if (count < 4096) return 1;
+  const unsigned hw = std::thread::hardware_concurrency();
+  return (int)std::max(1u, std::min(hw == 0 ? 1u : hw, 32u));
+}
+
+void parallel_for(int64_t count, const std::function<void(int64_t, int)>& f) {
+  const int nt = parallel_threads(count);
+  if (nt == 1) {
+    for (int64_t i = 0; i < count; ++i) f(i, 0);
+    return;
+  }
+  std::vector<std::thread> th;
+  std::vector<std::exception_ptr> errs(nt);
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([&, t] {
+      try {
+        const int64_t i0 = count * t / nt, i1 = count * (t + 1) / nt;
+        for (int64_t i = i0; i < i1; ++i) f(i, t);
+      } catch (...) {
+        errs[t] = std::current_exception();
+      }
+    });
+  for (auto& x : th) x.join();
+  for (auto& e : errs)
+    if (e) std::rethrow_exception(e);
+}
 
 void validate_csr(const amgps_csr& A, const char* what, bool square) {
   std::string w(what);
@@ -57,6 +88,13 @@ int split_for(int64_t stored, int64_t nslices) {
 
 // allow_uniform = false keeps every slice explicit (required for rectangular
 // matrices: a uniform slice's padding column row + off may fall outside n_cols)
+// Three passes: (1) in parallel, each slice's longest row and its sorted set
+// of column offsets; (2) in slice order, the layout decision (a slice whose
+// offsets all lie in the previous uniform pattern reuses it, so boundary
+// slices keep the interior pattern; else its own offsets if uniform; else
+// explicit) and the prefix of value bases; (3) in parallel, the values (and
+// explicit columns).  Each slice's output depends on its rows alone, so the
+// result does not depend on the thread count.
 HostSell build_sell(const amgps_csr& A, bool allow_uniform) {
   HostSell h;
   const int64_t n = A.n_rows;
@@ -64,74 +102,77 @@ HostSell build_sell(const amgps_csr& A, bool allow_uniform) {
   h.nnz = A.nnz;
   h.nslices = (n + kSlice - 1) / kSlice;
   h.sd.resize(h.nslices);
+  std::vector<int32_t> maxlen(h.nslices, 0);
+  std::vector<std::vector<int32_t>> own(allow_uniform ? h.nslices : 0);
+  parallel_for(h.nslices, [&](int64_t s, int) {
+    const int64_t r0 = s * kSlice, r1 = std::min(n, r0 + kSlice);
+    int ml = 0;
+    for (int64_t r = r0; r < r1; ++r) ml = std::max(ml, A.rowptr[r + 1] - A.rowptr[r]);
+    maxlen[s] = ml;
+    if (!allow_uniform) return;
+    std::vector<int32_t>& o = own[s];
+    for (int64_t r = r0; r < r1; ++r)
+      for (int e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e)
+        o.push_back((int32_t)((int64_t)A.col[e] - r));
+    std::sort(o.begin(), o.end());
+    o.erase(std::unique(o.begin(), o.end()), o.end());
+  });
   std::map<std::vector<int32_t>, int32_t> pats;
-  std::vector<int32_t> prev;
+  const std::vector<int32_t>* prev = nullptr;
   int32_t prev_ref = -1;
-  std::vector<int64_t> offs;
   int64_t vbase = 0;
   for (int64_t s = 0; s < h.nslices; ++s) {
-    const int64_t r0 = s * kSlice, r1 = std::min(n, r0 + kSlice);
-    int maxlen = 0;
-    for (int64_t r = r0; r < r1; ++r) maxlen = std::max(maxlen, A.rowptr[r + 1] - A.rowptr[r]);
-    // fast path: every offset of the slice already in the previous pattern
-    bool reuse = allow_uniform && prev_ref >= 0 && (int64_t)prev.size() <= maxlen + 1;
-    for (int64_t r = r0; r < r1 && reuse; ++r)
-      for (int e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e) {
-        const int32_t o = (int32_t)((int64_t)A.col[e] - r);
-        if (!std::binary_search(prev.begin(), prev.end(), o)) {
-          reuse = false;
-          break;
-        }
-      }
-    if (reuse) {
-      h.sd[s] = SliceDesc{vbase, (int32_t)prev.size(), prev_ref};
-      vbase += (int64_t)prev.size() * kSlice;
+    const int ml = maxlen[s];
+    if (allow_uniform && prev_ref >= 0 && (int64_t)prev->size() <= ml + 1 &&
+        std::includes(prev->begin(), prev->end(), own[s].begin(), own[s].end())) {
+      h.sd[s] = SliceDesc{vbase, (int32_t)prev->size(), prev_ref};
+      vbase += (int64_t)prev->size() * kSlice;
       continue;
     }
-    offs.clear();
-    for (int64_t r = r0; r < r1; ++r)
-      for (int e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e) offs.push_back((int64_t)A.col[e] - r);
-    std::sort(offs.begin(), offs.end());
-    offs.erase(std::unique(offs.begin(), offs.end()), offs.end());
-    const bool uniform =
-        allow_uniform && (int64_t)offs.size() <= maxlen + 1 && (int64_t)offs.size() <= kUniformMax;
+    const bool uniform = allow_uniform && (int64_t)own[s].size() <= ml + 1 &&
+                         (int64_t)own[s].size() <= kUniformMax;
     if (uniform) {
-      std::vector<int32_t> p(offs.begin(), offs.end());
-      auto it = pats.find(p);
+      auto it = pats.find(own[s]);
       int32_t ref;
       if (it == pats.end()) {
         ref = (int32_t)h.off.size();
-        h.off.insert(h.off.end(), p.begin(), p.end());
-        pats.emplace(p, ref);
+        h.off.insert(h.off.end(), own[s].begin(), own[s].end());
+        it = pats.emplace(own[s], ref).first;
       } else {
         ref = it->second;
       }
-      prev = p;
+      prev = &it->first;
       prev_ref = ref;
-      h.sd[s] = SliceDesc{vbase, (int32_t)p.size(), ref};
-      vbase += (int64_t)p.size() * kSlice;
+      h.sd[s] = SliceDesc{vbase, (int32_t)own[s].size(), ref};
+      vbase += (int64_t)own[s].size() * kSlice;
     } else {
-      h.sd[s] = SliceDesc{vbase, (int32_t)maxlen, -1};
-      vbase += (int64_t)maxlen * kSlice;
+      h.sd[s] = SliceDesc{vbase, (int32_t)ml, -1};
+      vbase += (int64_t)ml * kSlice;
       h.any_explicit = true;
-      h.explicit_entries += (int64_t)maxlen * kSlice;
+      h.explicit_entries += (int64_t)ml * kSlice;
     }
   }
+  own.clear();
+  own.shrink_to_fit();
   h.stored = vbase;
   h.val.assign(vbase, 0.0);
   if (h.any_explicit) h.col.assign(vbase, 0);
-  std::vector<std::pair<int32_t, double>> rowbuf;
-  std::vector<uint8_t> filled(kUniformMax);
-  for (int64_t s = 0; s < h.nslices; ++s) {
+  const int nt = parallel_threads(h.nslices);
+  std::vector<std::vector<std::pair<int32_t, double>>> rowbufs(nt);
+  std::vector<std::vector<uint8_t>> filleds(nt);
+  parallel_for(h.nslices, [&](int64_t s, int t) {
+    std::vector<std::pair<int32_t, double>>& rowbuf = rowbufs[t];
+    std::vector<uint8_t>& filled = filleds[t];
     const SliceDesc d = h.sd[s];
     const int64_t r0 = s * kSlice, r1 = std::min(n, r0 + kSlice);
     for (int64_t r = r0; r < r1; ++r) {
       const int lane = (int)(r - r0);
       if (d.cref >= 0) {
+        if ((int)filled.size() < d.w) filled.resize(d.w);
         std::fill(filled.begin(), filled.begin() + d.w, uint8_t(0));
+        const int32_t* p = h.off.data() + d.cref;
         for (int e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e) {
           const int32_t o = (int32_t)((int64_t)A.col[e] - r);
-          const int32_t* p = h.off.data() + d.cref;
           const int k = (int)(std::lower_bound(p, p + d.w, o) - p);
           REQ(!filled[k], AMGPS_E_ARG, "duplicate entry in CSR row");
           filled[k] = 1;
@@ -151,7 +192,7 @@ HostSell build_sell(const amgps_csr& A, bool allow_uniform) {
           h.col[d.vbase + (int64_t)k * kSlice + lane] = (int32_t)std::min<int64_t>(r, A.n_cols - 1);
       }
     }
-  }
+  });
   return h;
 }
 

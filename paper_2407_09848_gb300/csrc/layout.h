@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cstdint>
+#include <functional>
 #include <vector>
 
 #include "amgps_internal.h"
@@ -33,6 +34,12 @@ struct HostPlan {
   std::vector<TmaTile> tiles;
   std::vector<int32_t> gen;  // slices the TMA kernel does not cover
 };
+
+// Host threads for `count` independent items (1 below 4096 items, else the
+// hardware concurrency, at most 32); parallel_for calls f(i, thread) for
+// i in [0, count) in contiguous chunks and rethrows the first failure.
+int parallel_threads(int64_t count);
+void parallel_for(int64_t count, const std::function<void(int64_t, int)>& f);
 
 // AMGPS_E_ARG (through Fail) unless A is a well-formed CSR (square if asked)
 void validate_csr(const amgps_csr& A, const char* what, bool square);

@@ -1265,15 +1265,7 @@ amgps_status amgps_hierarchy_load(amgps_ctx* c, int n_levels, const amgps_csr* A
     for (int l = 0; l < n_levels; ++l) {
       validate_csr(A[l], "A", true);
       // SPD needs a positive diagonal; M_i = sum |a_ij| then bounds rho(M^{-1}A) <= 1
-      for (int64_t i = 0; i < A[l].n_rows; ++i) {
-        bool found = false;
-        for (int e = A[l].rowptr[i]; e < A[l].rowptr[i + 1]; ++e)
-          if (A[l].col[e] == i) {
-            REQ(A[l].val[e] > 0.0, AMGPS_E_NOT_SPD, "non-positive diagonal entry");
-            found = true;
-          }
-        REQ(found, AMGPS_E_NOT_SPD, "missing diagonal entry");
-      }
+      require_positive_diagonal(A[l]);
     }
     for (int l = 0; l + 1 < n_levels; ++l) {
       validate_csr(P[l], "P", false);
@@ -1940,15 +1932,7 @@ amgps_status amgps_sa_level(amgps_ctx* c, const amgps_csr* A, const int32_t* agg
     REQ(c && A && agg && omega && P_out && Ac_out, AMGPS_E_ARG, "null argument");
     validate_csr(*A, "A", true);
     REQ(n_coarse >= 1 && n_coarse <= A->n_rows, AMGPS_E_ARG, "n_coarse out of range");
-    for (int64_t i = 0; i < A->n_rows; ++i) {
-      bool found = false;
-      for (int e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e)
-        if (A->col[e] == i) {
-          REQ(A->val[e] > 0.0, AMGPS_E_NOT_SPD, "non-positive diagonal entry");
-          found = true;
-        }
-      REQ(found, AMGPS_E_NOT_SPD, "missing diagonal entry");
-    }
+    require_positive_diagonal(*A);
     std::vector<int32_t> used((size_t)n_coarse, 0);
     for (int64_t i = 0; i < A->n_rows; ++i) {
       REQ(agg[i] >= 0 && agg[i] < n_coarse, AMGPS_E_ARG, "aggregate index out of range");

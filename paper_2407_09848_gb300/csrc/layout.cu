@@ -49,19 +49,35 @@ void parallel_for(int64_t count, const std::function<void(int64_t, int)>& f) {
 }
 
 void validate_csr(const amgps_csr& A, const char* what, bool square) {
-  std::string w(what);
+  const std::string w(what);
   REQ(A.rowptr && A.col && A.val, AMGPS_E_ARG, w + ": null array");
   REQ(A.n_rows >= 1 && A.n_cols >= 1, AMGPS_E_ARG, w + ": empty matrix");
   REQ(A.n_rows < (int64_t(1) << 31) && A.n_cols < (int64_t(1) << 31), AMGPS_E_ARG,
       w + ": dimension exceeds int32");
   REQ(!square || A.n_rows == A.n_cols, AMGPS_E_ARG, w + ": not square");
   REQ(A.rowptr[0] == 0 && A.rowptr[A.n_rows] == A.nnz, AMGPS_E_ARG, w + ": bad rowptr ends");
-  for (int64_t i = 0; i < A.n_rows; ++i)
+  parallel_for(A.n_rows, [&](int64_t i, int) {
     REQ(A.rowptr[i + 1] >= A.rowptr[i], AMGPS_E_ARG, w + ": rowptr not monotone");
-  for (int64_t e = 0; e < A.nnz; ++e) {
-    REQ(A.col[e] >= 0 && A.col[e] < A.n_cols, AMGPS_E_ARG, w + ": column index out of range");
-    REQ(std::isfinite(A.val[e]), AMGPS_E_ARG, w + ": non-finite value");
-  }
+  });
+  // rowptr is monotone from 0 to nnz, so the rows cover every entry once
+  parallel_for(A.n_rows, [&](int64_t i, int) {
+    for (int e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e) {
+      REQ(A.col[e] >= 0 && A.col[e] < A.n_cols, AMGPS_E_ARG, w + ": column index out of range");
+      REQ(std::isfinite(A.val[e]), AMGPS_E_ARG, w + ": non-finite value");
+    }
+  });
+}
+
+void require_positive_diagonal(const amgps_csr& A) {
+  parallel_for(A.n_rows, [&](int64_t i, int) {
+    bool found = false;
+    for (int e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e)
+      if (A.col[e] == i) {
+        REQ(A.val[e] > 0.0, AMGPS_E_NOT_SPD, "non-positive diagonal entry");
+        found = true;
+      }
+    REQ(found, AMGPS_E_NOT_SPD, "missing diagonal entry");
+  });
 }
 
 // Warps per slice for the split kernels (measured on the 256^3

@@ -43,6 +43,9 @@ void parallel_for(int64_t count, const std::function<void(int64_t, int)>& f);
 
 // AMGPS_E_ARG (through Fail) unless A is a well-formed CSR (square if asked)
 void validate_csr(const amgps_csr& A, const char* what, bool square);
+// AMGPS_E_NOT_SPD unless every row holds a positive diagonal entry (a
+// validated square CSR)
+void require_positive_diagonal(const amgps_csr& A);
 // Warps per slice for the split kernels of a level (1: no split)
 int split_for(int64_t stored, int64_t nslices);
 // SELL-32 form of A; allow_uniform = false keeps every slice explicit

@@ -177,6 +177,13 @@ def test_mixed_precision_general_p_converges(sa_case, prec):
     it, rel = S.pcg(dev(torch, b), x, rtol=1e-9)
     true = np.linalg.norm(b - As[0] @ x.cpu().numpy()) / np.linalg.norm(b)
     assert rel <= 1e-9 and true <= 2e-9
+    # with the paper's setting: coarse l1-Jacobi sweeps run in the mixed
+    # engine, one-reduction flexible CG outside
+    S.set_coarse_sweeps(30)
+    S.set_flexible("fcg1")
+    it2, rel2 = S.pcg(dev(torch, b), x, rtol=1e-9)
+    true2 = np.linalg.norm(b - As[0] @ x.cpu().numpy()) / np.linalg.norm(b)
+    assert rel2 <= 1e-9 and true2 <= 2e-9 and it2 <= 2 * it
     S.close()
 
 

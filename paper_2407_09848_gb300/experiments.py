@@ -9,8 +9,12 @@ for several sizes and degrees.  The paper shows these counts only as images.
 sa_solve: PCG on a smoothed-aggregation hierarchy built on the GPU (a short
 fixed command for profiling that path).
 
+degree_sweep: PCG iterations and time per iteration against the degree
+(k = 1..12, five kinds) on the grid^3 Poisson problem.
+
 CLI:  python -m paper_2407_09848_gb300.experiments smoother_only
       python -m paper_2407_09848_gb300.experiments sa_solve [grid]
+      python -m paper_2407_09848_gb300.experiments degree_sweep [grid]
 """
 from __future__ import annotations
 
@@ -72,9 +76,47 @@ def sa_solve(grid=256, kind="cheb4_opt", degree=4, solves=2, rtol=1e-8):
     return out
 
 
+def degree_sweep(grid=256, degrees=(1, 2, 3, 4, 5, 6, 8, 10, 12),
+                 kinds=("cheb4_opt", "cheb1_opt", "cheb4", "cheb1", "l1jacobi"), rtol=1e-8):
+    """The supplementary trend of the paper (Sec. 4 and its supplement):
+    PCG iterations and time per iteration against the polynomial degree, on
+    the grid^3 Poisson problem with unsmoothed aggregation, FP64.  CHEB1 uses
+    rho = 1.1 x the 10-step power estimate of each level."""
+    import time
+    import torch
+    from .amgps import Solver
+    H = pr.build_hierarchy(pr.poisson(grid), coarse_max=512)
+    S = Solver().load(H.A, H.P)
+    b = torch.from_numpy(pr.rhs_uniform(H.A[0].shape[0], seed=0)).cuda()
+    x = torch.empty_like(b)
+    rows = []
+    for kind in kinds:
+        for k in degrees:
+            if kind == "cheb1":
+                for l in range(H.n_levels - 1):
+                    v0 = torch.from_numpy(pr.vec_uniform(H.A[l].shape[0], seed=0)).cuda()
+                    S.set_smoother(l, "cheb1", k, rho=1.1 * S.estimate_lambda(l, v0, iters=10))
+            else:
+                S.set_smoother(-1, kind, k)
+            S.pcg(b, x, rtol=rtol, maxit=2000)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            it, rel = S.pcg(b, x, rtol=rtol, maxit=2000)
+            torch.cuda.synchronize()
+            ms = 1e3 * (time.perf_counter() - t)
+            rows.append({"kind": kind, "degree": k, "iterations": it, "ms": round(ms, 3),
+                         "ms_per_iteration": round(ms / max(it, 1), 4)})
+    S.close()
+    return rows
+
+
 def main(argv):
     if len(argv) >= 1 and argv[0] == "smoother_only":
         print(json.dumps(smoother_only()))
+        return 0
+    if len(argv) >= 1 and argv[0] == "degree_sweep":
+        grid = int(argv[1]) if len(argv) > 1 else 256
+        print(json.dumps(degree_sweep(grid)))
         return 0
     if len(argv) >= 1 and argv[0] == "sa_solve":
         grid = int(argv[1]) if len(argv) > 1 else 256

@@ -1115,6 +1115,14 @@ DevCsr from_counts(DevScratch& B, const int32_t* dcnt, int64_t rows, int64_t col
 DevCsr dev_spgemm(amgps_ctx* c, DevScratch& B, const DevCsr& X, const DevCsr& Y, int* derr) {
   cudaStream_t s = c->stream;
   int32_t* cnt = B.alloc<int32_t>(X.n_rows);
+  if (Y.n_cols <= kDenseMaxCols) {  // few columns: dense row accumulator
+    launch_spgemm_dense(X, Y, cnt, DevCsr{}, derr, false, c->nsm, s);
+    check_dev_err(derr, s, "sparse product: symbolic pass failed");
+    DevCsr C = from_counts(B, cnt, X.n_rows, Y.n_cols, s);
+    launch_spgemm_dense(X, Y, nullptr, C, derr, true, c->nsm, s);
+    check_dev_err(derr, s, "sparse product: numeric pass failed");
+    return C;
+  }
   // narrow form first; the wide form when some row exceeds its limit
   bool wide = false;
   launch_spgemm(X, Y, cnt, DevCsr{}, derr, false, false, c->nsm, s);

@@ -124,6 +124,77 @@ __global__ void __launch_bounds__(32 * G::kWarps) k_spgemm(const DevCsr A, const
   }
 }
 
+// Dense form for products with at most kDenseMaxCols columns (the coarse
+// levels): one warp per block owns a dense row accumulator (values and touch
+// flags for every column) in shared memory.  Rounds add in the same order as
+// the hashed forms, so the result is bitwise the same; one ordered scan per
+// row emits the columns already sorted (no sort) and clears what it touched.
+// No row limit applies.
+__global__ void __launch_bounds__(32) k_spgemm_dense(const DevCsr A, const DevCsr B,
+                                                    int32_t* __restrict__ counts,
+                                                    const DevCsr C, int fill, int* err) {
+  extern __shared__ double dval[];
+  const int ncols = (int)B.n_cols;
+  uint8_t* flag = reinterpret_cast<uint8_t*>(dval + ncols);
+  const int lane = threadIdx.x & 31;
+  for (int j = lane; j < ncols; j += 32) {
+    dval[j] = 0.0;
+    flag[j] = 0;
+  }
+  __syncwarp();
+  for (int64_t i = blockIdx.x; i < A.n_rows; i += gridDim.x) {
+    for (int e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e) {
+      const int32_t k = A.col[e];
+      const double a = A.val[e];
+      for (int f = B.rowptr[k] + lane; f < B.rowptr[k + 1]; f += 32) {
+        const int32_t j = B.col[f];
+        if (fill) {
+          if (flag[j]) {
+            dval[j] += a * B.val[f];
+          } else {
+            flag[j] = 1;
+            dval[j] = 0.0;
+            dval[j] += a * B.val[f];
+          }
+        } else {
+          flag[j] = 1;
+        }
+      }
+      __syncwarp();
+    }
+    // the row's column count first: the numeric pass writes only when it
+    // equals the slot the symbolic pass reserved
+    int total = 0;
+    if (fill) {
+      for (int j0 = 0; j0 < ncols; j0 += 32) {
+        const int j = j0 + lane;
+        total += __popc(__ballot_sync(0xffffffffu, j < ncols && flag[j]));
+      }
+    }
+    const bool write = fill && (C.rowptr[i + 1] - C.rowptr[i] == total);
+    if (fill && !write && lane == 0) atomicExch(err, 2);
+    const int64_t out0 = fill ? C.rowptr[i] : 0;
+    int base = 0;
+    for (int j0 = 0; j0 < ncols; j0 += 32) {
+      const int j = j0 + lane;
+      const bool on = j < ncols && flag[j];
+      const unsigned m = __ballot_sync(0xffffffffu, on);
+      if (on) {
+        if (write) {
+          const int pos = base + __popc(m & ((1u << lane) - 1u));
+          C.col[out0 + pos] = j;
+          C.val[out0 + pos] = dval[j];
+        }
+        dval[j] = 0.0;
+        flag[j] = 0;
+      }
+      base += __popc(m);
+    }
+    if (!fill && lane == 0) counts[i] = base;
+    __syncwarp();
+  }
+}
+
 // diag[i] = a_ii, part[block] = max over its rows of sum_j |a_ij| / a_ii
 __global__ void __launch_bounds__(kBlock) k_rowstat(const DevCsr A, double* __restrict__ diag,
                                                     double* __restrict__ part) {
@@ -250,6 +321,23 @@ void launch_spgemm(const DevCsr& A, const DevCsr& B, int32_t* counts, const DevC
     if (fill) k_spgemm<Narrow, true><<<g, 32 * Narrow::kWarps, Narrow::kSmem, s>>>(A, B, counts, C, err);
     else k_spgemm<Narrow, false><<<g, 32 * Narrow::kWarps, Narrow::kSmem, s>>>(A, B, counts, C, err);
   }
+  count_launch();
+}
+
+void launch_spgemm_dense(const DevCsr& A, const DevCsr& B, int32_t* counts, const DevCsr& C,
+                         int* err, bool fill, int nsm, cudaStream_t s) {
+  if (A.n_rows == 0) return;
+  const size_t smem = (size_t)B.n_cols * 9;
+  static uint64_t done = 0;  // opt-in once per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && !(done >> dev & 1u)) {
+    cudaFuncSetAttribute(k_spgemm_dense, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)((size_t)kDenseMaxCols * 9));
+    done |= uint64_t(1) << dev;
+  }
+  const int g = gemm_grid(A.n_rows, 1, nsm);
+  k_spgemm_dense<<<g, 32, smem, s>>>(A, B, counts, C, fill ? 1 : 0, err);
   count_launch();
 }
 

@@ -25,6 +25,11 @@ struct DevCsr {
 // (kRowMaxNarrow, or kRowMaxWide with wide = true).
 void launch_spgemm(const DevCsr& A, const DevCsr& B, int32_t* counts, const DevCsr& C, int* err,
                    bool fill, bool wide, int nsm, cudaStream_t s);
+// Dense form of C = A B for B.n_cols <= kDenseMaxCols: same results as the
+// hashed forms (bitwise), no row limit.
+constexpr int64_t kDenseMaxCols = 16384;
+void launch_spgemm_dense(const DevCsr& A, const DevCsr& B, int32_t* counts, const DevCsr& C,
+                         int* err, bool fill, int nsm, cudaStream_t s);
 // diag[i] = a_ii and per-block maxima of sum_j |a_ij| / a_ii into part[];
 // returns the number of blocks (partials)
 int launch_rowstat(const DevCsr& A, double* diag, double* part, int nsm, cudaStream_t s);

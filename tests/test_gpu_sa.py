@@ -101,9 +101,16 @@ def test_galerkin_wide_rows_and_row_limit(solver):
     assert max_abs_diff(Ac, Aco) <= 1e-13 * np.abs(Aco.data).max()
     # P = I: both products have rows of 800 columns; I^T A I = A exactly
     assert max_abs_diff(solver.galerkin(A, sp.identity(n, format="csr")), A) == 0.0
-    # a row of 7000 distinct columns exceeds the wide limit (6144): AMGPS_E_ARG,
-    # and the context stays usable
+    # products with at most 16384 columns take the dense-accumulator form: a
+    # row of 7000 columns is fine there (I^T B I = B exactly)
     m = 7000
+    B = sp.identity(m, format="lil")
+    B[0, :] = 1.0
+    B = sp.csr_matrix(B)
+    assert max_abs_diff(solver.galerkin(B, sp.identity(m, format="csr")), B) == 0.0
+    # wider products use the hashed forms: a row of 20000 distinct columns
+    # exceeds their limit (6144): AMGPS_E_ARG, and the context stays usable
+    m = 20000
     B = sp.identity(m, format="lil")
     B[0, :] = 1.0
     with pytest.raises(AmgpsError) as ei:

@@ -18,7 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libamgps.so")
 SOURCES = ["api.cu", "kernels_smooth.cu", "kernels_krylov.cu", "kernels_tma.cu", "kernels_mlp.cu",
-           "kernels_setup.cu", "layout.cu"]
+           "kernels_setup.cu", "layout.cu",
+           "setup_host.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -16,6 +16,13 @@ struct Fail {
   std::string msg;
 };
 
+// the last kernel launch on this thread failed -> AMGPS_E_CUDA
+inline void check_launch() {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    throw Fail{AMGPS_E_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e)};
+}
+
 }  // namespace amgps
 
 #define CK(call)                                                                         \

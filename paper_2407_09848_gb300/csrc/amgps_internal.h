@@ -8,7 +8,9 @@
 //     (col = row + off[k]); then no per-entry column index is stored and
 //     entries absent from a row hold 0 (their clamped column is a valid
 //     address).  Every level of a 7-point operator with geometric
-//     aggregation is uniform, so the index stream disappears.
+//     aggregation is uniform, so the index stream disappears; so are the
+//     wide coarse levels of smoothed aggregation (patterns up to 1024
+//     offsets).
 //   * "explicit" otherwise: col[vbase + 32 k + lane] as in plain SELL.
 #pragma once
 

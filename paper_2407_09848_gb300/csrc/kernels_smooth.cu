@@ -14,13 +14,16 @@
 //     d^(j) = rho_j rho_{j-1} d^(j-1) + (2 rho_j/delta) r^(j) ; x += d^(j)
 //   l1-Jacobi sweep: x_new = x + M^{-1}(b - A x)
 //
-// D^{-1} = 1/M (Eq. l1smooth) is formed once per level and streamed as one
-// vector: on this GPU the FP64 pipe, not HBM, is the tighter limit of the FP64
-// path, and re-deriving M_i from the row plus an IEEE division every step would
-// cost about four times the FP64 instructions of the whole step.  The row's
-// own vectors are loaded before the SpMV so their latency overlaps it.  z
-// ping-pongs between two buffers because neighbouring rows gather z_j in the
-// same launch that writes z_{j+1}.
+// D^{-1} = 1/M (Eq. l1smooth) is formed once per level (re-deriving M_i from
+// the row plus an IEEE division every step would cost about four times the
+// FP64 instructions of the whole step).  On FP64 and FP32 levels the
+// polynomial steps go further and run on the row-scaled values a_ij / M_i with
+// the residual kept as M^{-1} r (rho M^{-1} r for the 1st kind): the families
+// FAM_CHEB4S/SR and FAM_CHEB1S/SR, which need no 1/M product or stream except
+// where rin is still b.  The row's own vectors are loaded before the SpMV so
+// their latency overlaps it.  z ping-pongs between two buffers because
+// neighbouring rows gather z_j in the same launch that writes z_{j+1}.  Levels
+// with wide rows use the split form (several warps per slice).
 #include "kernels_common.cuh"
 
 namespace amgps {

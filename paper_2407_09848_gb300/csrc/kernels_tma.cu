@@ -1,17 +1,20 @@
 // TMA-fed fused smoother step: the k_step recurrences (Sec. 2.1, 2.2) with
 // every global read staged by the Tensor Memory Accelerator.
 //
-// A persistent grid walks a list of 256-row tiles round-robin, so the tiles in
-// flight at any moment form one contiguous band and the vector windows that
-// neighbouring tiles share are read from HBM once and then from L2.  Warp 0 of
-// each CTA is the producer: one lane issues cp.async.bulk copies of a tile's
-// values, of its rows of r_in, x_in and 1/M, and of the contiguous windows of
-// the multiplied vector u (one per group of nearby column offsets) into a
-// shared-memory stage, completing on that stage's "full" mbarrier.  Warps
-// 1..8 are consumers, one 32-row slice each: they wait on "full", evaluate
-// the row from shared memory, store r/z/x to global memory, and arrive on the
-// stage's "empty" mbarrier so the producer may refill it.  The arithmetic and
-// its order are those of k_step, so both paths give the same bits.
+// A persistent grid (two CTAs per SM) walks a list of tiles round-robin --
+// 512 rows for FP64 vectors, 1024 for FP32 -- so the tiles in flight at any
+// moment form one contiguous band and the vector windows that neighbouring
+// tiles share are read from HBM once and then from L2.  Warp 0 of each CTA is
+// the producer: one lane issues cp.async.bulk copies of a tile's values, of
+// its rows of r_in, x_in and (when the step needs it) 1/M, and of the
+// contiguous windows of the multiplied vector u (one per group of nearby
+// column offsets) into a shared-memory stage, completing on that stage's
+// "full" mbarrier.  Warps 1..16 are consumers, taking the tile's 32-row slices
+// in turn: they wait on "full", evaluate the rows from shared memory, store
+// r/z/x to global memory, and arrive on the stage's "empty" mbarrier so the
+// producer may refill it.  After the tiles, the consumers also run the slices
+// outside the plan with direct loads.  The arithmetic and its order are those
+// of k_step, so both paths give the same bits.
 //
 // Every wait is bounded (kWaitSpins polls).  A wait that gives up sets the
 // solver's error slot and makes all warps leave their loops; the producer

@@ -1,5 +1,6 @@
 """The C-ABI library builds, loads and exports every declared entry point;
 its host-only table calls agree with the oracle and the paper (no GPU)."""
+import os
 import numpy as np
 import pytest
 
@@ -134,3 +135,33 @@ def test_layout_of_wide_smoothed_aggregation_levels(lib):
     dup.indices[r0 + 1] = dup.indices[r0]
     with pytest.raises(amgps.AmgpsError):
         amgps.tma_plan_stats(dup, "f64")
+
+
+def test_header_compiles_as_c(tmp_path):
+    # the boundary is a C ABI: include/amgps.h must stay valid C11, and the
+    # quick-start calls must type-check against it
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "quick.c"
+    src.write_text(
+        '#include "amgps.h"\n#include <stddef.h>\n'
+        "int quick(int nl, const amgps_csr* A, const amgps_csr* P, const double* b, double* x) {\n"
+        "  amgps_ctx* ctx;\n"
+        "  if (amgps_create(&ctx, 0, NULL) != AMGPS_OK) return -1;\n"
+        "  amgps_hierarchy_load(ctx, nl, A, P, AMGPS_F64);\n"
+        "  amgps_set_smoother(ctx, -1, AMGPS_CHEB4_OPT, 4, NULL, 0.0);\n"
+        "  amgps_set_option(ctx, AMGPS_OPT_FLEXIBLE, 2);\n"
+        "  int it; double rel;\n"
+        "  amgps_pcg(ctx, b, x, 1e-8, 1000, &it, &rel);\n"
+        "  amgps_csr_buf Ac = {0};\n"
+        "  amgps_galerkin(ctx, A, P, &Ac);\n"
+        "  amgps_csr_buf_free(&Ac);\n"
+        "  amgps_destroy(ctx);\n"
+        "  return it;\n}\n")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    r = subprocess.run([gcc, "-std=c11", "-Wall", "-Werror", "-c", "-I", inc, str(src), "-o",
+                        str(tmp_path / "quick.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr

@@ -165,3 +165,41 @@ def test_header_compiles_as_c(tmp_path):
     r = subprocess.run([gcc, "-std=c11", "-Wall", "-Werror", "-c", "-I", inc, str(src), "-o",
                         str(tmp_path / "quick.o")], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_malformed_csr_rejected_on_host(lib):
+    # host-only: every malformed CSR form returns AMGPS_E_ARG from the validator
+    # that hierarchy_load shares, before any layout or device work
+    import ctypes as C
+
+    def plan(n_rows, n_cols, rowptr, col, val):
+        rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+        ci = np.ascontiguousarray(col, dtype=np.int32)
+        vv = np.ascontiguousarray(val, dtype=np.float64)
+        nnz = int(len(ci))
+        csr = amgps.CSR(n_rows, n_cols, nnz, rp.ctypes.data, ci.ctypes.data, vv.ctypes.data)
+        t, g, sb, ns = C.c_int64(), C.c_int64(), C.c_int(), C.c_int()
+        st = lib.amgps_tma_plan_stats(C.byref(csr), 0, C.byref(t), C.byref(g), C.byref(sb),
+                                      C.byref(ns))
+        return st, lib.amgps_last_error(None).decode()
+
+    good = ([0, 2, 4], [0, 1, 0, 1], [2.0, -1.0, -1.0, 2.0])
+    assert plan(2, 2, *good)[0] == 0
+    cases = {
+        "empty matrix": (0, 0, [0], [0], [0.0]),
+        "not square": (2, 3, *good),
+        "bad rowptr ends": (2, 2, [0, 2, 3], *good[1:]),
+        "rowptr not monotone": (3, 3, [0, 3, 1, 4], [0, 1, 2, 2], [2.0, -1.0, -1.0, 2.0]),
+        "duplicate entry": (2, 2, [0, 3, 4], [0, 1, 0, 1], [2.0, -1.0, -1.0, 2.0]),
+        "column index out of range": (2, 2, [0, 2, 4], [0, 2, 0, 1], good[2]),
+        "negative column": (2, 2, [0, 2, 4], [0, -1, 0, 1], good[2]),
+        "non-finite value": (2, 2, [0, 2, 4], good[1], [2.0, np.nan, -1.0, 2.0]),
+        "infinite value": (2, 2, [0, 2, 4], good[1], [2.0, -1.0, np.inf, 2.0]),
+    }
+    for name, args in cases.items():
+        st, msg = plan(*args)
+        assert st == 1, (name, st, msg)  # AMGPS_E_ARG
+        assert msg, name
+    assert lib.amgps_tma_plan_stats(None, 0, None, None, None, None) == 1
+    assert plan(2, 2, *good)[0] == 0 and lib.amgps_tma_plan_stats(
+        C.byref(amgps.CSR(2, 2, 4, 0, 0, 0)), 0, None, None, None, None) == 1  # null arrays

@@ -87,15 +87,40 @@ struct StepArgs {
 constexpr int kMaxSplit = 32;
 
 // ---- TMA-fed step (kernels_tma.cu) ----
-// A tile is `rows` consecutive rows (a multiple of 32 slices' worth, up to
-// kTmaMaxRows) of one uniform pattern.  For each tile the producer warp copies
-// into shared memory, with cp.async.bulk: the tile's values, its rows of r_in,
-// x_in and 1/M, and for each group of nearby column offsets the contiguous
-// window of the multiplied vector that the group reads.  Consumer warps then
-// work from shared memory only.  Fewer, larger copies keep the TMA unit
-// streaming: tiles are 512 rows for FP64 and 1024 rows for FP32/BF16 vectors.
-constexpr int kTmaMaxRows = 1024;
-constexpr int kTmaConsumers = 16;
+// A tile is `rows` consecutive rows (whole 32-row slices) of one uniform
+// pattern.  For each tile the producer warp copies into shared memory, with
+// cp.async.bulk: the tile's values, its rows of r_in, x_in and 1/M, and for
+// each group of nearby column offsets the contiguous window of the multiplied
+// vector that the group reads.  Consumer warps then work from shared memory
+// only; a group's warps split each tile's slices between them.  Fewer, larger
+// copies keep the TMA unit streaming.  The launch shape depends on the vector
+// type:
+//   FP64: 480-row tiles (15 slices), one CTA per SM of 1 producer warp and two
+//     groups of 15 consumer warps taking alternate tiles (992 threads), with
+//     up to 225 KB of stages -- four in flight, so a tile's copies are issued
+//     three tiles ahead of the FP64-bound consumers;
+//   FP32/BF16: 1024-row tiles (32 slices), two CTAs per SM, each 1 producer
+//     warp and one group of 16 consumer warps, up to 112.5 KB of stages.
+template <class XT>
+struct TmaShape {  // FP32 vectors (FP32 and BF16 levels)
+  static constexpr int kRows = 1024, kGroups = 1, kConsumers = 16, kCtasPerSm = 2;
+  static constexpr int kSmemBudget = 115200;
+};
+template <>
+struct TmaShape<double> {
+  static constexpr int kRows = 480, kGroups = 2, kConsumers = 15, kCtasPerSm = 1;
+  static constexpr int kSmemBudget = 230400;
+};
+// the same figures by vector size, for the host-side planner
+inline int tma_rows(size_t xsize) {
+  return xsize == 8 ? TmaShape<double>::kRows : TmaShape<float>::kRows;
+}
+inline int tma_ctas_per_sm(size_t xsize) {
+  return xsize == 8 ? TmaShape<double>::kCtasPerSm : TmaShape<float>::kCtasPerSm;
+}
+inline int tma_smem_budget(size_t xsize) {
+  return xsize == 8 ? TmaShape<double>::kSmemBudget : TmaShape<float>::kSmemBudget;
+}
 constexpr int kTmaMaxW = 8;
 constexpr int kTmaMaxGroups = 4;
 constexpr int kTmaMaxStages = 8;
@@ -158,7 +183,7 @@ void launch_l1diag(const DevMat<VT>& A, XT* dinv, cudaStream_t s);
 template <class A, class B>
 void launch_convert(int64_t n, const A* in, B* out, cudaStream_t s);
 
-void tma_configure(int max_dynamic_smem);
+void tma_configure();
 
 // Kernels enqueued through the launchers above (graph captures included; the
 // host driver corrects for captures and adds graph replays).

@@ -1116,7 +1116,7 @@ amgps_status amgps_hierarchy_load(amgps_ctx* c, int n_levels, const amgps_csr* A
     enter(c);
     CK(cudaStreamSynchronize(c->stream));
     free_hierarchy(c);
-    tma_configure(kTmaSmemBudget + 2 * kTmaMaxStages * 8);
+    tma_configure();
     check_launch();
     c->prec = prec;
     c->lv.resize(n_levels);
@@ -1168,13 +1168,13 @@ amgps_status amgps_hierarchy_load(amgps_ctx* c, int n_levels, const amgps_csr* A
       }
       {
         const size_t vsz = prec == AMGPS_F64 ? 8 : (prec == AMGPS_F32 ? 4 : 2);
-        HostPlan hp = build_tma_plan(h, vsz, xs, kTmaSmemBudget);
+        HostPlan hp = build_tma_plan(h, vsz, xs, tma_smem_budget(xs));
         L.plan = hp.p;
         L.ntma = (int)hp.tiles.size();
         L.ngen = (int64_t)hp.gen.size();
         if (L.ntma > 0) {
           L.tma_tiles = dupload(c, hp.tiles.data(), hp.tiles.size());
-          L.tma_grid = std::min<int>(L.ntma, 2 * c->nsm);
+          L.tma_grid = std::min<int>(L.ntma, tma_ctas_per_sm(xs) * c->nsm);
         }
         if (L.ngen > 0) L.gen_slices = dupload(c, hp.gen.data(), hp.gen.size());
       }
@@ -1685,7 +1685,7 @@ amgps_status amgps_tma_plan_stats(const amgps_csr* A, amgps_prec prec, int64_t* 
     HostSell h = build_sell(*A);
     const size_t vsz = prec == AMGPS_F64 ? 8 : (prec == AMGPS_F32 ? 4 : 2);
     const size_t xsz = prec == AMGPS_F64 ? 8 : 4;
-    HostPlan hp = build_tma_plan(h, vsz, xsz, kTmaSmemBudget);
+    HostPlan hp = build_tma_plan(h, vsz, xsz, tma_smem_budget(xsz));
     if (tiles) *tiles = (int64_t)hp.tiles.size();
     if (generic_slices) *generic_slices = (int64_t)hp.gen.size();
     if (stage_bytes) *stage_bytes = hp.p.stage_bytes;

@@ -1,20 +1,23 @@
 // TMA-fed fused smoother step: the k_step recurrences (Sec. 2.1, 2.2) with
 // every global read staged by the Tensor Memory Accelerator.
 //
-// A persistent grid (two CTAs per SM) walks a list of tiles round-robin --
-// 512 rows for FP64 vectors, 1024 for FP32 -- so the tiles in flight at any
-// moment form one contiguous band and the vector windows that neighbouring
-// tiles share are read from HBM once and then from L2.  Warp 0 of each CTA is
-// the producer: one lane issues cp.async.bulk copies of a tile's values, of
-// its rows of r_in, x_in and (when the step needs it) 1/M, and of the
-// contiguous windows of the multiplied vector u (one per group of nearby
+// A persistent grid walks a list of tiles round-robin, so the tiles in flight
+// at any moment form one contiguous band and the vector windows that
+// neighbouring tiles share are read from HBM once and then from L2.  Warp 0 of
+// each CTA is the producer: one lane issues cp.async.bulk copies of a tile's
+// values, of its rows of r_in, x_in and (when the step needs it) 1/M, and of
+// the contiguous windows of the multiplied vector u (one per group of nearby
 // column offsets) into a shared-memory stage, completing on that stage's
-// "full" mbarrier.  Warps 1..16 are consumers, taking the tile's 32-row slices
-// in turn: they wait on "full", evaluate the rows from shared memory, store
-// r/z/x to global memory, and arrive on the stage's "empty" mbarrier so the
-// producer may refill it.  After the tiles, the consumers also run the slices
-// outside the plan with direct loads.  The arithmetic and its order are those
-// of k_step, so both paths give the same bits.
+// "full" mbarrier.  The other warps are consumers, in groups that take
+// alternate tiles; a group's warps split the tile's 32-row slices: they wait
+// on "full", evaluate the rows from shared memory, store r/z/x to global
+// memory, and arrive on the stage's "empty" mbarrier so the producer may
+// refill it.  After the tiles, all consumers also run the slices outside the
+// plan with direct loads.  The arithmetic and its order are those of k_step,
+// so both paths give the same bits.  Tile height, groups and CTAs per SM come
+// from TmaShape<XT>: for FP64 one CTA per SM with two groups of 15 warps and
+// four 480-row stages in flight (the FP64-bound consumers then never wait for
+// a copy), for FP32 vectors two CTAs per SM of 16 consumers on 1024-row tiles.
 //
 // Every wait is bounded (kWaitSpins polls).  A wait that gives up sets the
 // solver's error slot and makes all warps leave their loops; the producer
@@ -80,8 +83,14 @@ __device__ __forceinline__ XT widen(float v) { return XT(v); }
 template <class XT>
 __device__ __forceinline__ XT widen(__nv_bfloat16 v) { return XT(__bfloat162float(v)); }
 
+// consumer warps per CTA
+template <class XT>
+__host__ __device__ constexpr int tma_warps() {
+  return TmaShape<XT>::kGroups * TmaShape<XT>::kConsumers;
+}
+
 template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN>
-__global__ void __launch_bounds__((kTmaConsumers + 1) * 32, 2)
+__global__ void __launch_bounds__((tma_warps<XT>() + 1) * 32, TmaShape<XT>::kCtasPerSm)
     k_step_tma(const StepArgs<VT, XT> a, const TmaPlan p, const TmaTile* __restrict__ tiles,
                int ntiles, const int32_t* __restrict__ gen, int64_t ngen, double* err) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -96,7 +105,7 @@ __global__ void __launch_bounds__((kTmaConsumers + 1) * 32, 2)
   if (threadIdx.x == 0) {
     for (int i = 0; i < ns; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], kTmaConsumers);
+      mbar_init(&empty[i], TmaShape<XT>::kConsumers);  // one group consumes a tile
     }
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -155,10 +164,17 @@ __global__ void __launch_bounds__((kTmaConsumers + 1) * 32, 2)
   }
 
   const int c = warp - 1;
+  constexpr int kGroups = TmaShape<XT>::kGroups, kCons = TmaShape<XT>::kConsumers;
+  const int grp = c / kCons, cw = c % kCons;
   const int spt = p.rows / kSlice;  // slices per tile
   using F = StepForm<FAM, INIT>;
-  int it = 0;
-  for (int j = blockIdx.x; j < ntiles; j += gridDim.x, ++it) {
+  // group g takes this CTA's tiles g, g + kGroups, ...  The producer fills
+  // tiles in order, and a group waits for a tile only after finishing its
+  // previous one, so the stage's previous fill (kGroups <= nstages tiles
+  // earlier) has landed and the parity wait cannot match a stale phase.
+  for (int it = grp;; it += kGroups) {
+    const int j = blockIdx.x + it * (int)gridDim.x;
+    if (j >= ntiles) break;
     const int st = it % ns;
     const uint32_t ph = (uint32_t)(it / ns) & 1u;
     if (abort_flag || !mbar_wait(&full[st], ph)) {
@@ -169,7 +185,7 @@ __global__ void __launch_bounds__((kTmaConsumers + 1) * 32, 2)
     const XT* sv = reinterpret_cast<const XT*>(base + p.vals_bytes);
     const XT* sw = sv + 3 * p.rows;
     const int64_t r0 = stage_r0[st];
-    for (int cs = c; cs < spt; cs += kTmaConsumers) {
+    for (int cs = cw; cs < spt; cs += kCons) {
       const int it_row = cs * kSlice + lane;  // row inside the tile
       const VT* svals = reinterpret_cast<const VT*>(base) + (size_t)cs * p.w * kSlice + lane;
       const XT rin = sv[it_row];
@@ -196,8 +212,8 @@ __global__ void __launch_bounds__((kTmaConsumers + 1) * 32, 2)
   // the slices outside the plan (pattern changes, windows leaving [0, n)):
   // direct loads, round-robin over all consumer warps; their rows are
   // disjoint from the tiles' rows
-  for (int64_t q = (int64_t)blockIdx.x * kTmaConsumers + c; q < ngen;
-       q += (int64_t)gridDim.x * kTmaConsumers)
+  for (int64_t q = (int64_t)blockIdx.x * tma_warps<XT>() + c; q < ngen;
+       q += (int64_t)gridDim.x * tma_warps<XT>())
     step_slice<VT, XT, FAM, INIT, WR, ZOWN>(a, gen[q], lane);
 }
 
@@ -205,7 +221,7 @@ template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN>
 void launch_inst(const StepArgs<VT, XT>& a, const TmaPlan& p, const TmaTile* tiles, int ntiles,
                  int grid, double* err, cudaStream_t s) {
   const int smem = kBarrierBytes + p.nstages * p.stage_bytes;
-  k_step_tma<VT, XT, FAM, INIT, WR, ZOWN><<<grid, (kTmaConsumers + 1) * 32, smem, s>>>(
+  k_step_tma<VT, XT, FAM, INIT, WR, ZOWN><<<grid, (tma_warps<XT>() + 1) * 32, smem, s>>>(
       a, p, tiles, ntiles, a.slices, a.slices ? a.nlist : 0, err);
   count_launch();
 }
@@ -275,16 +291,16 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 }  // namespace
 
-void tma_configure(int max_dynamic_smem) {
-  configure_all<double, double>(max_dynamic_smem);
-  configure_all<float, float>(max_dynamic_smem);
-  configure_all<__nv_bfloat16, float>(max_dynamic_smem);
+void tma_configure() {
+  configure_all<double, double>(TmaShape<double>::kSmemBudget + kBarrierBytes);
+  configure_all<float, float>(TmaShape<float>::kSmemBudget + kBarrierBytes);
+  configure_all<__nv_bfloat16, float>(TmaShape<float>::kSmemBudget + kBarrierBytes);
 }
 
 template <class VT, class XT>
 bool launch_step_tma(const StepArgs<VT, XT>& a, const TmaPlan& p, const TmaTile* tiles,
                      int ntiles, int grid, double* err, cudaStream_t s) {
-  if (ntiles <= 0 || p.nstages < 2) return false;
+  if (ntiles <= 0 || p.nstages < 2 || p.nstages < TmaShape<XT>::kGroups) return false;
   if (!aligned16(a.A.val) || !aligned16(a.u) || !aligned16(a.rin)) return false;
   if (a.fam != FAM_RES && (!aligned16(a.xin) || !aligned16(a.dinv))) return false;
   if (a.zown && a.zown != a.u) return false;  // z_j at the row is read from u's window

@@ -251,7 +251,7 @@ uint16_t dbl_to_bf16(double x) {
 HostPlan build_tma_plan(const HostSell& h, size_t vsize, size_t xsize, int smem_budget) {
   HostPlan hp;
   const int64_t n = h.n;
-  const int rows = xsize == 8 ? 512 : kTmaMaxRows;  // FP64 vectors: two 512-row stages per CTA
+  const int rows = tma_rows(xsize);
   const int64_t ntf = n / rows;
   const int spt = rows / kSlice;
   hp.p.rows = rows;

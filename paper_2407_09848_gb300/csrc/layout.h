@@ -16,9 +16,6 @@ namespace amgps {
 // coarse operators of smoothed aggregation on a grid still fits).
 constexpr int64_t kUniformMax = 1024;
 
-// Dynamic shared memory per CTA of the TMA-fed step: two CTAs fit one SM
-// (2 x (115200 B + 1 KB driver reserve + static) <= 228 KB).
-constexpr int kTmaSmemBudget = 115200;
 
 struct HostSell {
   int64_t n = 0, nnz = 0, nslices = 0, stored = 0, explicit_entries = 0;

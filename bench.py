@@ -463,8 +463,8 @@ def run_ours(a):
     roof = hbm
     clk = clk.summary() if hasattr(clk, "summary") else clk
     if a.prec == "f64" and a.kind in ("cheb4", "cheb4_opt", "weights") and n_step:
-        # FP64 path: the step is bound by the FP64 pipe (ncu: ~83% busy vs
-        # DRAM ~62%).  The 4th-kind steps run on the row-scaled matrix M^{-1}A
+        # FP64 path: the step is bound by the FP64 pipe (ncu: ~85% busy vs
+        # DRAM ~60%).  The 4th-kind steps run on the row-scaled matrix M^{-1}A
         # with the residual kept scaled.  Flops per launch averaged over a
         # V-cycle's 2k-1 level-0 steps: every step 2 nnz (the SpMV with the
         # residual folded in); per row c2 r (1) and, with the c1 z term, one

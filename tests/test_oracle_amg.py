@@ -231,3 +231,47 @@ def test_coarse_sweeps_converge_to_exact_coarse_solve():
     b = pr.rhs_uniform(A[0].shape[0], seed=1)
     _, it30, rel, _ = OracleAMG(A, Pl, spec, coarse_sweeps=30).pcg(b, rtol=1e-8)
     assert rel <= 1e-8 and it30 < 100
+
+
+@pytest.mark.parametrize("flexible", [True, False])
+def test_conjugacy_defect_under_a_variable_preconditioner(flexible):
+    # With exact line searches r_{k+1} is orthogonal to p_k, and A p_k =
+    # (r_k - r_{k+1}) / alpha_k, p_k.A p_k = r_k.z_k / alpha_k.  Hence for any
+    # preconditioners B_k (z_k = B_k r_k) the local conjugacy defect is fixed
+    # by the direction update alone:
+    #   flexible (Polak-Ribiere):  alpha_k p_{k+1}.A p_k = z_{k+1}.r_k - r_{k+1}.z_k
+    #   standard (Fletcher-Reeves): alpha_k p_{k+1}.A p_k = z_{k+1}.r_k
+    # (the first is the local relation of inexact-preconditioned CG, Golub-Ye;
+    # both vanish for a fixed symmetric B).  Steps s_k = x_{k+1} - x_k =
+    # alpha_k p_k are read from runs stopped after 1, 2, ... iterations with the
+    # same preconditioner sequence, and alpha_{k+1} = s.A s / (r_{k+1}.z_{k+1}).
+    A, Pl = hier(pr.varcoef(6, 1.0, 3.0, seed=7), 30)
+    amg = OracleAMG(A, Pl, SmootherSpec("cheb4", 1))
+    A0 = A[0]
+    n = A0.shape[0]
+    b = pr.rhs_uniform(n, seed=5)
+    D = np.random.default_rng(9).uniform(0.5, 2.0, (8, n))   # B_k = diag(D[k]), SPD, varying
+
+    def run(m):
+        calls = [0]
+
+        def prec(r):
+            d = D[calls[0]]
+            calls[0] += 1
+            return d * r
+        x, it, _, _ = amg.pcg(b, rtol=0.0, maxit=m, flexible=flexible, precond=prec)
+        assert it == m
+        return x
+    xs = [np.zeros(n)] + [run(m) for m in range(1, 6)]
+    r = [b - A0 @ x for x in xs]
+    z = [D[k] * r[k] for k in range(len(xs))]
+    s = [xs[k + 1] - xs[k] for k in range(len(xs) - 1)]
+    for k in range(len(s) - 1):
+        alpha1 = (s[k + 1] @ (A0 @ s[k + 1])) / (r[k + 1] @ z[k + 1])
+        lhs = s[k + 1] @ (A0 @ s[k])                     # alpha_{k+1} alpha_k p_{k+1}.A p_k
+        defect = z[k + 1] @ r[k] - (r[k + 1] @ z[k] if flexible else 0.0)
+        rhs = alpha1 * defect
+        scale = abs(alpha1) * np.linalg.norm(z[k + 1]) * np.linalg.norm(r[k])
+        assert abs(lhs - rhs) <= 1e-10 * scale, (k, lhs, rhs)
+        if k >= 1:
+            assert abs(rhs) > 1e-6 * scale               # the preconditioner change matters

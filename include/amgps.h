@@ -286,7 +286,7 @@ amgps_status amgps_synchronize(amgps_ctx* ctx);
 /* Context options.  AMGPS_OPT_TMA selects the kernel of the fused smoother
  * step: 0 the direct-load kernel everywhere; 1 (default) the TMA-fed
  * pipelined kernel on levels whose layout allows it and that hold at least
- * two tiles per CTA (4 x the SM count), the direct one elsewhere; 2 the
+ * 4 tiles per SM, the direct one elsewhere; 2 the
  * TMA-fed kernel wherever the layout allows it.  Results are identical
  * across the three.  Other values: AMGPS_E_ARG.
  * AMGPS_OPT_FLEXIBLE (default 0) selects the outer CG form of amgps_pcg and

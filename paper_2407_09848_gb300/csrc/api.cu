@@ -356,9 +356,10 @@ struct Engine {
       a.fam = a.init ? FAM_CHEB1SR : FAM_CHEB1S;
       a.c2 = a.c2 * a.rhoinv;
     }
-    // TMA option 1 (auto): only where the level has two tiles per CTA or more;
-    // below that the persistent pipeline cannot fill and the direct kernel
-    // (more, smaller blocks) is faster.  Option 2 takes it wherever planned.
+    // TMA option 1 (auto): only where the level has at least 4 tiles per SM
+    // (two per CTA for FP32 vectors, four per CTA for FP64); below that the
+    // persistent pipeline cannot fill and the direct kernel (more, smaller
+    // blocks) is faster.  Option 2 takes it wherever planned.
     const bool tma = L.ntma > 0 && (c->use_tma == 2 || (c->use_tma == 1 && L.ntma >= 4 * c->nsm));
     if (tma) {
       // the TMA kernel also runs the slices outside its plan (slice list)

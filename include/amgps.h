@@ -45,7 +45,7 @@ typedef enum {
   AMGPS_E_NOCONV = 3,   /* PCG reached maxit without meeting rtol (x holds the last iterate) */
   AMGPS_E_NAN = 4,      /* a NaN/Inf appeared in a PCG scalar */
   AMGPS_E_CUDA = 5,     /* a CUDA runtime call failed (message has cudaGetErrorString) */
-  AMGPS_E_TIMEOUT = 6,  /* reserved: a bounded device wait gave up */
+  AMGPS_E_TIMEOUT = 6,  /* a bounded wait inside a pipelined kernel gave up */
   AMGPS_E_STATE = 7,    /* call out of order (e.g. smooth before hierarchy_load) */
   AMGPS_E_NOMEM = 8     /* device or pinned host allocation failed */
 } amgps_status;

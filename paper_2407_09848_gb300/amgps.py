@@ -25,6 +25,7 @@ STATUS = {0: "AMGPS_OK", 1: "AMGPS_E_ARG", 2: "AMGPS_E_NOT_SPD", 3: "AMGPS_E_NOC
           4: "AMGPS_E_NAN", 5: "AMGPS_E_CUDA", 6: "AMGPS_E_TIMEOUT", 7: "AMGPS_E_STATE",
           8: "AMGPS_E_NOMEM"}
 PROF_STEP, PROF_RESTRICT, PROF_SPMV, PROF_COUNT, PROF_COARSE = 0, 1, 2, 3, 4
+OPT_TMA, OPT_FLEXIBLE, OPT_COARSE_SWEEPS = 1, 2, 3
 
 
 class AmgpsError(RuntimeError):
@@ -428,12 +429,12 @@ class Solver:
         enough for it), False (direct kernel everywhere), "always" (TMA-fed
         kernel wherever a level's layout allows it)."""
         v = 2 if on == "always" else (1 if on else 0)
-        self._check(lib().amgps_set_option(self._h, 1, v))
+        self._check(lib().amgps_set_option(self._h, OPT_TMA, v))
 
     def set_coarse_sweeps(self, m):
         """Coarsest-level solve: 0 = dense inverse (default), m > 0 = m
         l1-Jacobi sweeps from zero (the paper's coarse solver)."""
-        self._check(lib().amgps_set_option(self._h, 3, int(m)))
+        self._check(lib().amgps_set_option(self._h, OPT_COARSE_SWEEPS, int(m)))
 
     OUTER = {"cg": 0, "flexible": 1, "fcg1": 2}
 
@@ -442,7 +443,7 @@ class Solver:
         True or "flexible" (Polak-Ribiere beta), "fcg1" (flexible CG with one
         reduction per iteration)."""
         v = self.OUTER[on] if isinstance(on, str) else (1 if on else 0)
-        self._check(lib().amgps_set_option(self._h, 2, v))
+        self._check(lib().amgps_set_option(self._h, OPT_FLEXIBLE, v))
 
     def synchronize(self):
         self._check(lib().amgps_synchronize(self._h))

@@ -204,3 +204,22 @@ def test_malformed_csr_rejected_on_host(lib):
     assert lib.amgps_tma_plan_stats(None, 0, None, None, None, None) == 1
     assert plan(2, 2, *good)[0] == 0 and lib.amgps_tma_plan_stats(
         C.byref(amgps.CSR(2, 2, 4, 0, 0, 0)), 0, None, None, None, None) == 1  # null arrays
+
+
+def test_binding_constants_match_header():
+    # the Python binding's status, kind, precision and option numbers are the
+    # enumerators of include/amgps.h
+    import re
+    txt = open(amgps.HEADER).read()
+    enum = {m.group(1): int(m.group(2))
+            for m in re.finditer(r"\b(AMGPS_[A-Z0-9_]+)\s*=\s*(\d+)", txt)}
+    for code, name in amgps.STATUS.items():
+        assert enum[name] == code, name
+    assert {n for n in enum if n.startswith("AMGPS_E_") or n == "AMGPS_OK"} == set(
+        amgps.STATUS.values())
+    for kind, v in amgps.KIND.items():
+        assert enum["AMGPS_" + kind.upper()] == v, kind
+    for prec, v in amgps.PREC.items():
+        assert enum["AMGPS_" + prec.upper()] == v, prec
+    assert (enum["AMGPS_OPT_TMA"], enum["AMGPS_OPT_FLEXIBLE"], enum["AMGPS_OPT_COARSE_SWEEPS"]) == (
+        amgps.OPT_TMA, amgps.OPT_FLEXIBLE, amgps.OPT_COARSE_SWEEPS)

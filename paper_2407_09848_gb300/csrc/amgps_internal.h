@@ -121,6 +121,14 @@ inline int tma_ctas_per_sm(size_t xsize) {
 inline int tma_smem_budget(size_t xsize) {
   return xsize == 8 ? TmaShape<double>::kSmemBudget : TmaShape<float>::kSmemBudget;
 }
+// The stage count of a plan is a multiple of the group count: then the
+// previous fill of the stage a group waits on is a tile of the same group,
+// already consumed, so the parity wait cannot pass on a stale phase.  (With
+// two groups and an odd count, a group could reach a stage whose previous
+// tile -- the other group's -- had not landed yet.)
+inline int tma_groups(size_t xsize) {
+  return xsize == 8 ? TmaShape<double>::kGroups : TmaShape<float>::kGroups;
+}
 constexpr int kTmaMaxW = 8;
 constexpr int kTmaMaxGroups = 4;
 constexpr int kTmaMaxStages = 8;

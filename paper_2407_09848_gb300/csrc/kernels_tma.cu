@@ -168,10 +168,10 @@ __global__ void __launch_bounds__((tma_warps<XT>() + 1) * 32, TmaShape<XT>::kCta
   const int grp = c / kCons, cw = c % kCons;
   const int spt = p.rows / kSlice;  // slices per tile
   using F = StepForm<FAM, INIT>;
-  // group g takes this CTA's tiles g, g + kGroups, ...  The producer fills
-  // tiles in order, and a group waits for a tile only after finishing its
-  // previous one, so the stage's previous fill (kGroups <= nstages tiles
-  // earlier) has landed and the parity wait cannot match a stale phase.
+  // group g takes this CTA's tiles g, g + kGroups, ...  The stage of tile it
+  // last held tile it - nstages; nstages is a multiple of kGroups, so that
+  // tile belongs to this group and was consumed before this wait, and the
+  // parity wait cannot pass on a stale phase (copies may land out of order).
   for (int it = grp;; it += kGroups) {
     const int j = blockIdx.x + it * (int)gridDim.x;
     if (j >= ntiles) break;
@@ -300,7 +300,7 @@ void tma_configure() {
 template <class VT, class XT>
 bool launch_step_tma(const StepArgs<VT, XT>& a, const TmaPlan& p, const TmaTile* tiles,
                      int ntiles, int grid, double* err, cudaStream_t s) {
-  if (ntiles <= 0 || p.nstages < 2 || p.nstages < TmaShape<XT>::kGroups) return false;
+  if (ntiles <= 0 || p.nstages < 2 || p.nstages % TmaShape<XT>::kGroups != 0) return false;
   if (!aligned16(a.A.val) || !aligned16(a.u) || !aligned16(a.rin)) return false;
   if (a.fam != FAM_RES && (!aligned16(a.xin) || !aligned16(a.dinv))) return false;
   if (a.zown && a.zown != a.u) return false;  // z_j at the row is read from u's window

@@ -328,6 +328,7 @@ HostPlan build_tma_plan(const HostSell& h, size_t vsize, size_t xsize, int smem_
   P.win_bytes = (int)(acc * (int64_t)xsize);
   P.stage_bytes = (int)ceil_to(P.vals_bytes + 3 * P.vec_bytes + P.win_bytes, 128);
   P.nstages = std::min<int>(kTmaMaxStages, (smem_budget - 2 * kTmaMaxStages * 8) / P.stage_bytes);
+  P.nstages -= P.nstages % tma_groups(xsize);  // see tma_groups()
   if (P.nstages < 2) {
     P.nstages = 0;
     return finish();

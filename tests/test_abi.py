@@ -96,6 +96,7 @@ def test_tma_plan_covers_and_checks_copies(lib, prec):
             if tiles:
                 budget = 230400 if prec == "f64" else 115200  # one CTA per SM for FP64, two otherwise
                 assert 2 <= nst <= 8 and nst * stage + 128 <= budget and stage % 128 == 0
+                assert prec != "f64" or nst % 2 == 0  # a multiple of the two consumer groups
     # 64^3: (almost) every tile whose +-4096-row windows stay inside the vector
     # qualifies; the exceptions are tiles where the slice pattern changes
     H = pr.build_hierarchy(pr.poisson(64))
@@ -223,3 +224,13 @@ def test_binding_constants_match_header():
         assert enum["AMGPS_" + prec.upper()] == v, prec
     assert (enum["AMGPS_OPT_TMA"], enum["AMGPS_OPT_FLEXIBLE"], enum["AMGPS_OPT_COARSE_SWEEPS"]) == (
         amgps.OPT_TMA, amgps.OPT_FLEXIBLE, amgps.OPT_COARSE_SWEEPS)
+
+
+def test_fp64_stage_count_is_even(lib):
+    # a 480-wide grid leaves room for three 57.6 KB FP64 stages; the planner
+    # keeps two, a multiple of the FP64 shape's two consumer groups
+    from paper_2407_09848_gb300 import problems as pr
+    tiles, gen, stage, nst = amgps.tma_plan_stats(pr.to_csr(pr.poisson(480, 8, 8)), "f64")
+    assert tiles > 0 and stage == 57600 and nst == 2
+    tiles, gen, stage, nst = amgps.tma_plan_stats(pr.to_csr(pr.poisson(256, 8, 8)), "f64")
+    assert nst == 4

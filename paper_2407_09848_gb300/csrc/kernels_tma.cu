@@ -147,14 +147,17 @@ __global__ void __launch_bounds__((tma_warps<XT>() + 1) * 32, TmaShape<XT>::kCta
             for (int g = 0; g < p.ngroups; ++g)
               bulk_g2s(sw + p.g_smem[g], a.u + r0 + p.g_start[g],
                        (uint32_t)(p.g_elems[g] * (int)sizeof(XT)), &full[st]);
+            ++it;  // lane 0 counts issued tiles only: the drain waits for these
           }
         }
-        ++it;
         if (__shfl_sync(0xffffffffu, (int)abort_flag, 0)) break;
       }
     }
     if (lane == 0) {
-      // the last fill of each stage must have landed before this CTA exits
+      // the last fill of each stage must have landed before this CTA exits:
+      // wait for the last ns issued tiles (a tile given up on was not issued;
+      // counting it would wait on its stage's stale phase and miss the copy
+      // of that stage's previous tile)
       const int first = it > ns ? it - ns : 0;
       for (int q = first; q < it; ++q)
         if (!mbar_wait(&full[q % ns], (uint32_t)(q / ns) & 1u)) abort_flag = 1;

@@ -18,7 +18,11 @@ The planner makes the stage count a multiple of the group count, and the
 launcher rejects any other plan: with two groups and an odd count a group can
 reach a stage whose previous tile, the other group's, has not landed yet.
 The model must find that hazard (and the one of more groups than stages),
-which shows it can see a stale phase.
+which shows it can see a stale phase.  With bounded waits that give up, the
+producer stops issuing and, before the CTA exits, waits for the last fill of
+every stage -- the last `ns` tiles it issued; counting the tile it gave up on
+as issued would let that drain pass on a stale phase while the stage's
+previous copy is still in flight, which the model also finds.
 """
 import random
 
@@ -50,24 +54,29 @@ class Hazard(AssertionError):
     pass
 
 
-def run_cta(ntiles, ns, groups, consumers, seed, check_stale=True):
+def run_cta(ntiles, ns, groups, consumers, seed, check_stale=True, timeouts=0.0,
+            drain_counts_unissued=False):
     """One CTA: `ntiles` tiles, `ns` stages, `groups` x `consumers` consumer
-    warps.  Returns the number of scheduling steps taken."""
+    warps.  With `timeouts`, any blocked wait may give up (the kernel's bounded
+    waits): the warp sets the abort flag and leaves, the others leave at their
+    next wait, the producer stops issuing and drains the copies it issued
+    (`timeouts` is the chance per scheduling step that blocked waits may give up).
+    `drain_counts_unissued` counts the tile the producer gave up on as issued.
+    Returns the number of scheduling steps taken."""
     rng = random.Random(seed)
     full = [MBarrier(1) for _ in range(ns)]                 # producer's copy lands
     empty = [MBarrier(consumers) for _ in range(ns)]        # one group consumes a tile
     stage_tile = [None] * ns                                # which tile a stage holds
     readers_left = [0] * ns                                 # warps still to read it
-    # producer state
-    prod = {"it": 0, "inflight": []}                        # copies issued, not landed
-    # consumer warp state: next tile index of its group, and whether it waits
-    warps = [{"g": g, "it": g} for g in range(groups) for _ in range(consumers)]
+    prod = {"it": 0, "issued": 0, "inflight": [], "drain": None, "done": False}
+    warps = [{"g": g, "it": g, "out": False} for g in range(groups) for _ in range(consumers)]
     consumed = {}
+    state = {"abort": False}
     steps = 0
 
     def producer_enabled():
         it = prod["it"]
-        if it >= ntiles:
+        if prod["drain"] is not None or it >= ntiles or state["abort"]:
             return False
         st, k = it % ns, it // ns
         return empty[st].try_wait_parity((k & 1) ^ 1)
@@ -83,6 +92,21 @@ def run_cta(ntiles, ns, groups, consumers, seed, check_stale=True):
         stage_tile[st] = None                               # copy in flight
         prod["inflight"].append(it)
         prod["it"] += 1
+        prod["issued"] += 1
+
+    def producer_stops():
+        # loop left (all issued, or abort seen / own wait gave up): drain the
+        # last fill of every stage, i.e. the last ns issued tiles
+        if prod["it"] < ntiles and drain_counts_unissued:
+            prod["it"] += 1                                 # the tile it gave up on
+            last = prod["it"]
+        else:
+            last = prod["issued"]
+        prod["drain"] = list(range(max(0, last - ns), last))
+
+    def drain_enabled():
+        q = prod["drain"][0]
+        return full[q % ns].try_wait_parity((q // ns) & 1)
 
     def land_step():
         it = prod["inflight"].pop(rng.randrange(len(prod["inflight"])))
@@ -92,10 +116,11 @@ def run_cta(ntiles, ns, groups, consumers, seed, check_stale=True):
         readers_left[st] = consumers
         full[st].arrive()
 
+    def warp_live(w):
+        return not w["out"] and w["it"] < ntiles
+
     def warp_enabled(w):
         it = w["it"]
-        if it >= ntiles:
-            return False
         st, k = it % ns, it // ns
         return full[st].try_wait_parity(k & 1)
 
@@ -113,27 +138,65 @@ def run_cta(ntiles, ns, groups, consumers, seed, check_stale=True):
 
     while True:
         moves = []
-        if producer_enabled():
-            moves.append(("p", None))
+        giveup = timeouts > 0 and rng.random() < timeouts
+        if not prod["done"]:
+            if prod["drain"] is None:
+                if producer_enabled():
+                    moves.append(("p", None))
+                elif prod["it"] >= ntiles or state["abort"]:
+                    moves.append(("stop", None))
+                elif giveup:
+                    moves.append(("ptimeout", None))
+            elif not prod["drain"]:
+                moves.append(("exit", None))
+            elif drain_enabled():
+                moves.append(("drain", None))
+            elif prod["drain"][0] >= prod["issued"]:
+                # waiting for a copy that was never issued: the bounded wait
+                # gives up (copies that were issued always land in this model)
+                moves.append(("drain", None))
         if prod["inflight"]:
             moves.append(("l", None))
         for w in warps:
-            if warp_enabled(w):
-                moves.append(("w", w))
+            if warp_live(w):
+                if state["abort"]:
+                    moves.append(("leave", w))
+                elif warp_enabled(w):
+                    moves.append(("w", w))
+                elif giveup:
+                    moves.append(("wtimeout", w))
         if not moves:
             break
         kind, w = rng.choice(moves)
         if kind == "p":
             producer_step()
+        elif kind == "stop":
+            producer_stops()
+        elif kind == "ptimeout":
+            state["abort"] = True
+            producer_stops()
+        elif kind == "drain":
+            prod["drain"].pop(0)
+        elif kind == "exit":
+            prod["done"] = True
+            if prod["inflight"]:
+                raise Hazard(f"producer left with copies of tiles {prod['inflight']} in flight")
         elif kind == "l":
             land_step()
-        else:
+        elif kind == "w":
             warp_step(w)
+        elif kind == "wtimeout":
+            state["abort"] = True
+            w["out"] = True
+        else:                                               # leave after an abort
+            w["out"] = True
         steps += 1
-    # no deadlock: everything issued, landed and consumed
-    assert prod["it"] == ntiles and not prod["inflight"], "producer stalled"
-    assert all(w["it"] >= ntiles for w in warps), "a consumer warp stalled"
-    assert consumed == {t: consumers for t in range(ntiles)}
+    # no deadlock: the producer drained and left, every warp finished or left
+    assert prod["done"] and not prod["inflight"], "producer stalled"
+    assert all(not warp_live(w) for w in warps), "a consumer warp stalled"
+    if not state["abort"]:
+        assert prod["issued"] == ntiles
+        assert consumed == {t: consumers for t in range(ntiles)}
     return steps
 
 
@@ -163,6 +226,30 @@ def test_stage_count_not_a_multiple_of_groups_is_unsafe(ns, groups):
     for seed in range(400):
         try:
             run_cta(4 * ns + 3, ns, groups, consumers=2, seed=seed)
+        except Hazard:
+            seen = True
+            break
+    assert seen
+
+
+@pytest.mark.parametrize("ns,groups", [(2, 1), (3, 1), (5, 1), (2, 2), (4, 2)])
+def test_abort_path_drains_every_copy(ns, groups):
+    # any wait may give up; the producer still leaves only after every copy it
+    # issued has landed, and no warp waits forever
+    for ntiles in (1, ns, 2 * ns + 1, 17):
+        for seed in range(150):
+            run_cta(ntiles, ns, groups, consumers=2, seed=seed, timeouts=0.3)
+
+
+def test_counting_the_unissued_tile_in_the_drain_is_unsafe():
+    # if the tile the producer gave up on were counted as issued, the drain
+    # would wait on that stage's phase, see the stale phase of the stage's
+    # previous tile as complete and leave while that copy is still in flight
+    seen = False
+    for seed in range(5000):
+        try:
+            run_cta(9, 2, 1, consumers=2, seed=seed, timeouts=0.05,
+                    drain_counts_unissued=True)
         except Hazard:
             seen = True
             break

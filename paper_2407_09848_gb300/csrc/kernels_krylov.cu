@@ -52,30 +52,6 @@ void launch_spmv_dot(const DevMat<double>& A, const double* p, double* q, const 
   count_launch();
 }
 
-// x += alpha p ; r -= alpha q ; r.r (S_RR), alpha = rz / pq from k_spmv_dot
-__global__ void __launch_bounds__(kBlock) k_cg_update(int64_t n, const double* __restrict__ p,
-                                                      const double* __restrict__ q,
-                                                      double* __restrict__ x,
-                                                      double* __restrict__ r, const RedWork w,
-                                                      double* scal) {
-  const double alpha = scal[S_ALPHA];
-  double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * kBlock) {
-    x[i] = fma(alpha, p[i], x[i]);
-    const double ri = fma(-alpha, q[i], r[i]);
-    r[i] = ri;
-    acc = fma(ri, ri, acc);
-  }
-  grid_sum(acc, w, [&](double tot) { scal[S_RR] = tot; });
-}
-
-void launch_cg_update(int64_t n, const double* p, const double* q, double* x, double* r,
-                      const RedWork& w, double* scal, cudaStream_t s) {
-  k_cg_update<<<w.grid, kBlock, 0, s>>>(n, p, q, x, r, w, scal);
-  count_launch();
-}
-
 // Three sums in one pass (the one-reduction flexible CG): partials are laid
 // out [v0 of every block | v1 ... | v2 ...] in w.part (3 x grid doubles); the
 // last block adds each column in index order and calls fin(t0, t1, t2).
@@ -253,21 +229,6 @@ __global__ void __launch_bounds__(kBlock) k_dot(int64_t n, const double* __restr
 void launch_dot(int64_t n, const double* a, const double* b, const RedWork& w, double* scal,
                 int out_slot, int rz_mode, cudaStream_t s) {
   k_dot<<<w.grid, kBlock, 0, s>>>(n, a, b, w, scal, out_slot, rz_mode);
-  count_launch();
-}
-
-// p = z + beta p, beta = rz / rz_old from the last block of k_dot
-__global__ void __launch_bounds__(kBlock) k_xpay(int64_t n, const double* __restrict__ z,
-                                                 double* __restrict__ p,
-                                                 const double* __restrict__ scal) {
-  const double beta = scal[S_BETA];
-  const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
-  if (i < n) p[i] = fma(beta, p[i], z[i]);
-}
-
-void launch_xpay(int64_t n, const double* z, double* p, const double* scal, cudaStream_t s) {
-  if (n == 0) return;
-  k_xpay<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, z, p, scal);
   count_launch();
 }
 

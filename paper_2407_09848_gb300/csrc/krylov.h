@@ -34,8 +34,6 @@ void launch_spmv_dot3(const DevMat<double>& A, const double* z, double* w, const
 void launch_fcg_update(int64_t n, const double* z, const double* w, double* p, double* q,
                        double* x, double* r, int first, const RedWork& rw, double* scal,
                        cudaStream_t s);
-void launch_cg_update(int64_t n, const double* p, const double* q, double* x, double* r,
-                      const RedWork& w, double* scal, cudaStream_t s);
 // standard PCG with the x update deferred: r -= alpha q and r.r; later
 // x += alpha p together with p = z + beta p (with_p = 0: x only)
 void launch_r_update(int64_t n, const double* q, double* r, const RedWork& w, double* scal,
@@ -47,7 +45,6 @@ void launch_xpay_x(int64_t n, const double* z, double* p, double* x, const doubl
 // beta = (S_RZ - S_RZP) / S_RZOLD.
 void launch_dot(int64_t n, const double* a, const double* b, const RedWork& w, double* scal,
                 int out_slot, int rz_mode, cudaStream_t s);
-void launch_xpay(int64_t n, const double* z, double* p, const double* scal, cudaStream_t s);
 template <class XT>
 void launch_coarse_gemv(int nc, const double* ainv, const XT* b, XT* x, cudaStream_t s);
 void launch_chol_inverse(int n, double* work, double* ainv, int* status, cudaStream_t s);

@@ -21,8 +21,6 @@ from __future__ import annotations
 import json
 import sys
 
-import numpy as np
-
 from . import problems as pr
 
 

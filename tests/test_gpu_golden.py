@@ -6,7 +6,6 @@ launch configuration)."""
 import json
 import os
 
-import numpy as np
 import pytest
 
 from paper_2407_09848_gb300 import problems as pr

@@ -309,12 +309,27 @@ enum { AMGPS_OPT_TMA = 1, AMGPS_OPT_FLEXIBLE = 2, AMGPS_OPT_COARSE_SWEEPS = 3 };
 amgps_status amgps_set_option(amgps_ctx* ctx, int option, int64_t value);
 
 /* Host-only planning query (no device needed): how the TMA-fed step would
- * cover matrix A at precision `prec` -- 256-row tiles it takes, slices left to
- * the direct kernel, bytes per shared-memory stage and stages per CTA.  Every
- * bulk copy of the plan is checked on the host for bounds and 16-byte
- * alignment; a violation returns AMGPS_E_ARG. */
+ * cover matrix A at precision `prec` -- tiles it takes (480 rows for FP64
+ * vectors, 1024 for FP32 ones), 32-row slices left to the direct kernel, bytes
+ * per shared-memory stage and stages per CTA.  Every bulk copy of the plan is
+ * checked on the host for bounds and 16-byte alignment; a violation returns
+ * AMGPS_E_ARG. */
 amgps_status amgps_tma_plan_stats(const amgps_csr* A, amgps_prec prec, int64_t* tiles,
                                   int64_t* generic_slices, int* stage_bytes, int* nstages);
+
+/* Host-only inspection (no device needed): the SELL-32 layout that
+ * amgps_hierarchy_load uploads for the square matrix A.  Slice s holds rows
+ * 32s .. 32s+31; entry k of its lane l (row 32s+l) sits at index
+ * vbase[s] + 32k + l of val (and of col), k < width[s].  A uniform slice
+ * (cref[s] >= 0) stores no columns: its entry k is column row + off[cref[s]+k],
+ * clamped to [0, n-1], and an entry absent from a row holds 0.  An explicit
+ * slice (cref[s] < 0) stores the columns in col (row-sorted; padding holds 0
+ * and an in-range column).  Call once with null arrays for the sizes
+ * (*nslices, *stored, *noff), then with arrays of those lengths (col entries of
+ * uniform slices are written as -1).  AMGPS_E_ARG for a malformed A. */
+amgps_status amgps_sell_layout(const amgps_csr* A, int64_t* nslices, int64_t* stored,
+                               int64_t* noff, int64_t* vbase, int32_t* width, int32_t* cref,
+                               double* val, int32_t* col, int32_t* off);
 
 /* The library's tabulated optimal 4th-kind weights beta_{1..degree} for
  * Eq. polsmootheropt (degree 1..16), written to beta_out (host). */

@@ -83,6 +83,9 @@ _SIGS = {
                             C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "amgps_mlp_adam": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_float, C.c_float,
                         C.c_float, C.c_float, C.c_void_p], C.c_int),
+    "amgps_sell_layout": ([C.POINTER(CSR), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                           C.POINTER(C.c_int64), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                           C.c_void_p, C.c_void_p], C.c_int),
     "amgps_opt4_weights": ([C.c_int, C.c_void_p], C.c_int),
     "amgps_cheb1_astar": ([C.c_int, C.POINTER(C.c_double)], C.c_int),
     "amgps_profile_enable": ([C.c_void_p, C.c_int], C.c_int),
@@ -187,6 +190,30 @@ def tma_plan_stats(A, prec="f64"):
     if st:
         raise AmgpsError(st, lib().amgps_last_error(None).decode())
     return t.value, g.value, sb.value, ns.value
+
+
+def sell_layout(A):
+    """Host-only: the SELL-32 layout of a square matrix, as a dict of numpy
+    arrays (vbase, width, cref, val, col, off); see amgps_sell_layout."""
+    keep = []
+    csr = _csr_struct(A, keep)
+    ns, st, no = C.c_int64(), C.c_int64(), C.c_int64()
+    z = None
+    stat = lib().amgps_sell_layout(C.byref(csr), C.byref(ns), C.byref(st), C.byref(no),
+                                   z, z, z, z, z, z)
+    if stat:
+        raise AmgpsError(stat, lib().amgps_last_error(None).decode())
+    out = {"vbase": np.zeros(ns.value, np.int64), "width": np.zeros(ns.value, np.int32),
+           "cref": np.zeros(ns.value, np.int32), "val": np.zeros(st.value, np.float64),
+           "col": np.zeros(st.value, np.int32), "off": np.zeros(max(no.value, 1), np.int32)}
+    ptr = lambda a: a.ctypes.data
+    stat = lib().amgps_sell_layout(C.byref(csr), C.byref(ns), C.byref(st), C.byref(no),
+                                   ptr(out["vbase"]), ptr(out["width"]), ptr(out["cref"]),
+                                   ptr(out["val"]), ptr(out["col"]), ptr(out["off"]))
+    if stat:
+        raise AmgpsError(stat, lib().amgps_last_error(None).decode())
+    out["off"] = out["off"][:no.value]
+    return out
 
 
 def _csr_struct(A, keep):

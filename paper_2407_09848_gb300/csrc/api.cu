@@ -1694,6 +1694,30 @@ amgps_status amgps_tma_plan_stats(const amgps_csr* A, amgps_prec prec, int64_t* 
   });
 }
 
+amgps_status amgps_sell_layout(const amgps_csr* A, int64_t* nslices, int64_t* stored,
+                               int64_t* noff, int64_t* vbase, int32_t* width, int32_t* cref,
+                               double* val, int32_t* col, int32_t* off) {
+  return guard(nullptr, [&] {
+    REQ(A && nslices && stored && noff, AMGPS_E_ARG, "null argument");
+    validate_csr(*A, "A", true);
+    const HostSell h = build_sell(*A);
+    *nslices = h.nslices;
+    *stored = h.stored;
+    *noff = (int64_t)h.off.size();
+    if (!vbase) return;  // size query
+    REQ(width && cref && val && col && (off || h.off.empty()), AMGPS_E_ARG, "null array");
+    for (int64_t s = 0; s < h.nslices; ++s) {
+      vbase[s] = h.sd[s].vbase;
+      width[s] = h.sd[s].w;
+      cref[s] = h.sd[s].cref;
+      for (int64_t e = h.sd[s].vbase; e < h.sd[s].vbase + (int64_t)h.sd[s].w * kSlice; ++e)
+        col[e] = h.sd[s].cref >= 0 ? -1 : h.col[e];
+    }
+    std::copy(h.val.begin(), h.val.end(), val);
+    std::copy(h.off.begin(), h.off.end(), off);
+  });
+}
+
 amgps_status amgps_opt4_weights(int degree, double* beta_out) {
   if (!beta_out || degree < 1 || degree > AMGPS_TABLE_KMAX) return AMGPS_E_ARG;
   for (int j = 0; j < degree; ++j) beta_out[j] = AMGPS_OPT4_BETA[degree - 1][j];

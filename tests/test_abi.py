@@ -234,3 +234,93 @@ def test_fp64_stage_count_is_even(lib):
     assert tiles > 0 and stage == 57600 and nst == 2
     tiles, gen, stage, nst = amgps.tma_plan_stats(pr.to_csr(pr.poisson(256, 8, 8)), "f64")
     assert nst == 4
+
+
+def _sell_spmv(L, n, x):
+    """y = A x evaluated from the SELL-32 arrays the way the device rows read
+    them: explicit columns, or row + offset clamped to [0, n-1] in uniform
+    slices; lanes past n are dropped."""
+    y = np.zeros(n)
+    lanes = np.arange(32)
+    for s in range(len(L["vbase"])):
+        rows = 32 * s + lanes
+        live = rows < n
+        for k in range(int(L["width"][s])):
+            e = int(L["vbase"][s]) + 32 * k + lanes
+            if L["cref"][s] >= 0:
+                c = np.clip(rows + int(L["off"][L["cref"][s] + k]), 0, n - 1)
+            else:
+                c = L["col"][e]
+            y[rows[live]] += L["val"][e][live] * x[c[live]]
+    return y
+
+
+def _sell_entries(L, n):
+    """(row, col, val) of every stored nonzero of the layout."""
+    out = []
+    lanes = np.arange(32)
+    for s in range(len(L["vbase"])):
+        rows = 32 * s + lanes
+        for k in range(int(L["width"][s])):
+            e = int(L["vbase"][s]) + 32 * k + lanes
+            v = L["val"][e]
+            if L["cref"][s] >= 0:
+                assert np.all(L["col"][e] == -1)
+                c = rows + int(L["off"][L["cref"][s] + k])
+            else:
+                c = L["col"][e]
+                assert np.all((c >= 0) & (c < n))     # padding keeps an in-range column
+            nz = v != 0
+            assert np.all(rows[nz] < n) and np.all((c[nz] >= 0) & (c[nz] < n))
+            out.append(np.stack([rows[nz], c[nz]], 1))
+            out.append(v[nz])
+    rc = np.concatenate(out[0::2]) if out else np.zeros((0, 2), int)
+    vals = np.concatenate(out[1::2]) if out else np.zeros(0)
+    return rc, vals
+
+
+def test_sell_layout_reproduces_the_matrix(lib):
+    # host-only: the layout hierarchy_load uploads holds every entry of A once,
+    # bit for bit, and the device's row semantics evaluated on it give A x
+    import scipy.sparse as sp
+    from oracle import sa
+    from paper_2407_09848_gb300 import problems as pr
+    mats = {"poisson16": pr.to_csr(pr.poisson(16)),
+            "poisson33x17x9": pr.to_csr(pr.poisson(33, 17, 9)),
+            "varcoef": pr.to_csr(pr.varcoef(20, 1.0, 3.0, seed=2, ny=13, nz=11)),
+            "aniso": pr.to_csr(pr.aniso(12, 1e-3)),
+            "lap1d_70": sp.diags([-np.ones(69), 2 * np.ones(70), -np.ones(69)], [-1, 0, 1]).tocsr()}
+    st = pr.poisson(16)
+    lev = pr.geometric_aggregates(st.shape, coarse_max=8)
+    As, _, _ = sa.sa_hierarchy(pr.to_csr(st), [a for a, _, _ in lev], [c for _, c, _ in lev])
+    for i, A in enumerate(As[1:]):
+        mats[f"sa_level{i + 1}"] = sp.csr_matrix(A)
+    rng = np.random.default_rng(4)
+    R = sp.random(300, 300, density=0.03, random_state=5, data_rvs=lambda m: rng.uniform(-1, 1, m))
+    R = (R + R.T + sp.diags(np.full(300, 20.0))).tolil()
+    R[7, :] = rng.uniform(-1, 1, 300)                 # one dense row: a wide explicit slice
+    R[7, 7] = 50.0
+    mats["random_explicit"] = sp.csr_matrix(R)
+    kinds = set()
+    for name, A in mats.items():
+        A = sp.csr_matrix(A)
+        A.sum_duplicates()
+        A.eliminate_zeros()
+        n = A.shape[0]
+        L = amgps.sell_layout(A)
+        assert len(L["vbase"]) == (n + 31) // 32
+        kinds |= {"uniform" if c >= 0 else "explicit" for c in L["cref"]}
+        rc, vals = _sell_entries(L, n)
+        B = sp.csr_matrix((vals, (rc[:, 0], rc[:, 1])), shape=A.shape)
+        assert B.nnz == A.nnz == len(vals), name            # no entry stored twice
+        B.sort_indices()
+        A.sort_indices()
+        assert np.array_equal(B.indptr, A.indptr) and np.array_equal(B.indices, A.indices), name
+        assert np.array_equal(B.data, A.data), name         # values copied bit for bit
+        x = rng.uniform(-1, 1, n)
+        y = _sell_spmv(L, n, x)
+        assert np.max(np.abs(y - A @ x)) <= 1e-13 * np.abs(A).sum(axis=1).max(), name
+    assert kinds == {"uniform", "explicit"}
+    # a wide smoothed-aggregation level stays uniform (no column stream)
+    Lw = amgps.sell_layout(mats["sa_level1"])
+    assert np.all(Lw["cref"] >= 0) and Lw["width"].max() > 32

@@ -317,6 +317,19 @@ amgps_status amgps_set_option(amgps_ctx* ctx, int option, int64_t value);
 amgps_status amgps_tma_plan_stats(const amgps_csr* A, amgps_prec prec, int64_t* tiles,
                                   int64_t* generic_slices, int* stage_bytes, int* nstages);
 
+/* Host-only inspection (no device needed): the TMA plan behind
+ * amgps_tma_plan_stats.  info[32] receives, in order: rows per tile, stencil
+ * width w, window groups G, d0 (stage-window index of the tile's own rows),
+ * value bytes, vector bytes, window bytes, stage bytes, stages, then
+ * g_start[4], g_elems[4], g_smem[4] (window g copies u[r0 + g_start .. +
+ * g_elems) to stage-window index g_smem) and d[8] (entry k of tile row i
+ * reads stage-window index d[k] + i); unused slots are 0.  Call once with null
+ * tiles/gen for *ntiles and *ngen, then with tiles[2 * ntiles] (first row,
+ * value index of each tile) and gen[ngen] (slices left to the direct kernel).
+ * AMGPS_E_ARG for a malformed A. */
+amgps_status amgps_tma_plan(const amgps_csr* A, amgps_prec prec, int32_t* info, int64_t* ntiles,
+                            int64_t* tiles, int64_t* ngen, int32_t* gen);
+
 /* Host-only inspection (no device needed): the SELL-32 layout that
  * amgps_hierarchy_load uploads for the square matrix A.  Slice s holds rows
  * 32s .. 32s+31; entry k of its lane l (row 32s+l) sits at index

@@ -83,6 +83,8 @@ _SIGS = {
                             C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "amgps_mlp_adam": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_float, C.c_float,
                         C.c_float, C.c_float, C.c_void_p], C.c_int),
+    "amgps_tma_plan": ([C.POINTER(CSR), C.c_int, C.c_void_p, C.POINTER(C.c_int64), C.c_void_p,
+                        C.POINTER(C.c_int64), C.c_void_p], C.c_int),
     "amgps_sell_layout": ([C.POINTER(CSR), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                            C.POINTER(C.c_int64), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                            C.c_void_p, C.c_void_p], C.c_int),
@@ -190,6 +192,32 @@ def tma_plan_stats(A, prec="f64"):
     if st:
         raise AmgpsError(st, lib().amgps_last_error(None).decode())
     return t.value, g.value, sb.value, ns.value
+
+
+def tma_plan(A, prec="f64"):
+    """Host-only: the TMA plan of a square matrix (see amgps_tma_plan) as a dict:
+    the scalar fields, g_start / g_elems / g_smem / d arrays, tiles (ntiles x 2:
+    first row, value index) and gen (slices left to the direct kernel)."""
+    keep = []
+    csr = _csr_struct(A, keep)
+    info = np.zeros(32, np.int32)
+    nt, ng = C.c_int64(), C.c_int64()
+    stat = lib().amgps_tma_plan(C.byref(csr), PREC[prec], info.ctypes.data, C.byref(nt), None,
+                                C.byref(ng), None)
+    if stat:
+        raise AmgpsError(stat, lib().amgps_last_error(None).decode())
+    tiles = np.zeros((max(nt.value, 1), 2), np.int64)
+    gen = np.zeros(max(ng.value, 1), np.int32)
+    stat = lib().amgps_tma_plan(C.byref(csr), PREC[prec], info.ctypes.data, C.byref(nt),
+                                tiles.ctypes.data, C.byref(ng), gen.ctypes.data)
+    if stat:
+        raise AmgpsError(stat, lib().amgps_last_error(None).decode())
+    keys = ("rows", "w", "ngroups", "d0", "vals_bytes", "vec_bytes", "win_bytes",
+            "stage_bytes", "nstages")
+    out = {k: int(v) for k, v in zip(keys, info[:9])}
+    out.update(g_start=info[9:13].copy(), g_elems=info[13:17].copy(), g_smem=info[17:21].copy(),
+               d=info[21:29].copy(), tiles=tiles[:nt.value], gen=gen[:ng.value])
+    return out
 
 
 def sell_layout(A):

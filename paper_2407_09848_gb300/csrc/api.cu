@@ -1694,6 +1694,41 @@ amgps_status amgps_tma_plan_stats(const amgps_csr* A, amgps_prec prec, int64_t* 
   });
 }
 
+amgps_status amgps_tma_plan(const amgps_csr* A, amgps_prec prec, int32_t* info, int64_t* ntiles,
+                            int64_t* tiles, int64_t* ngen, int32_t* gen) {
+  return guard(nullptr, [&] {
+    REQ(A && info && ntiles && ngen, AMGPS_E_ARG, "null argument");
+    REQ(prec == AMGPS_F64 || prec == AMGPS_F32 || prec == AMGPS_BF16, AMGPS_E_ARG,
+        "unknown precision");
+    validate_csr(*A, "A", true);
+    const HostSell h = build_sell(*A);
+    const size_t vsz = prec == AMGPS_F64 ? 8 : (prec == AMGPS_F32 ? 4 : 2);
+    const size_t xsz = prec == AMGPS_F64 ? 8 : 4;
+    const HostPlan hp = build_tma_plan(h, vsz, xsz, tma_smem_budget(xsz));
+    const TmaPlan& p = hp.p;
+    static_assert(kTmaMaxGroups == 4 && kTmaMaxW == 8, "info layout");
+    std::fill(info, info + 32, 0);
+    const int32_t head[9] = {p.rows, p.w, p.ngroups, p.d0, p.vals_bytes, p.vec_bytes,
+                             p.win_bytes, p.stage_bytes, p.nstages};
+    std::copy(head, head + 9, info);
+    for (int g = 0; g < kTmaMaxGroups; ++g) {
+      info[9 + g] = p.g_start[g];
+      info[13 + g] = p.g_elems[g];
+      info[17 + g] = p.g_smem[g];
+    }
+    for (int k = 0; k < kTmaMaxW; ++k) info[21 + k] = p.d[k];
+    *ntiles = (int64_t)hp.tiles.size();
+    *ngen = (int64_t)hp.gen.size();
+    if (!tiles) return;  // size query
+    REQ(gen || hp.gen.empty(), AMGPS_E_ARG, "null array");
+    for (size_t t = 0; t < hp.tiles.size(); ++t) {
+      tiles[2 * t] = hp.tiles[t].r0;
+      tiles[2 * t + 1] = hp.tiles[t].vbase;
+    }
+    std::copy(hp.gen.begin(), hp.gen.end(), gen);
+  });
+}
+
 amgps_status amgps_sell_layout(const amgps_csr* A, int64_t* nslices, int64_t* stored,
                                int64_t* noff, int64_t* vbase, int32_t* width, int32_t* cref,
                                double* val, int32_t* col, int32_t* off) {

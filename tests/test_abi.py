@@ -324,3 +324,48 @@ def test_sell_layout_reproduces_the_matrix(lib):
     # a wide smoothed-aggregation level stays uniform (no column stream)
     Lw = amgps.sell_layout(mats["sa_level1"])
     assert np.all(Lw["cref"] >= 0) and Lw["width"].max() > 32
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_tma_plan_stage_emulation(lib, prec):
+    # host-only: replay the producer's copies of every planned tile into a
+    # stage (values block, the tile's own rows, one window of u per group) and
+    # the consumers' shared-memory reads (entry k of tile row i at window index
+    # d[k] + i): each planned row must give (A u)_row, its own-row read (d0) must
+    # be u_row, and tiles plus left-over slices must cover every slice once
+    from paper_2407_09848_gb300 import problems as pr
+    rng = np.random.default_rng(11)
+    planned = 0
+    for st in (pr.poisson(64, 40, 12), pr.varcoef(48, 1.0, 3.0, seed=3, ny=40, nz=9),
+               pr.aniso(40, 1e-3), pr.poisson(480, 4, 4), pr.poisson(300, 3, 3)):
+        A = pr.to_csr(st)
+        n = A.shape[0]
+        L = amgps.sell_layout(A)
+        P = amgps.tma_plan(A, prec)
+        rows, w = P["rows"], P["w"]
+        spt = rows // 32
+        covered = np.zeros(len(L["vbase"]), int)
+        covered[P["gen"]] += 1
+        u = rng.uniform(-1, 1, n)
+        Au = A @ u
+        planned += len(P["tiles"])
+        for r0, vb in P["tiles"]:
+            assert r0 % rows == 0 and r0 + rows <= n
+            s0 = r0 // 32
+            covered[s0:s0 + spt] += 1
+            assert np.all(L["cref"][s0:s0 + spt] == L["cref"][s0])   # one uniform pattern
+            vals = L["val"][vb:vb + w * rows]                         # the values copy
+            win = np.zeros(int(P["win_bytes"]) // (8 if prec == "f64" else 4))
+            for g in range(P["ngroups"]):
+                a, m, o = int(P["g_start"][g]), int(P["g_elems"][g]), int(P["g_smem"][g])
+                assert 0 <= r0 + a and r0 + a + m <= n                # copies stay inside u
+                win[o:o + m] = u[r0 + a:r0 + a + m]
+            i = np.arange(rows)
+            cs, lane = i // 32, i % 32
+            acc = np.zeros(rows)
+            for k in range(w):
+                acc += vals[cs * w * 32 + k * 32 + lane] * win[P["d"][k] + i]
+            assert np.max(np.abs(acc - Au[r0:r0 + rows])) <= 1e-13 * np.abs(A).sum(axis=1).max()
+            assert np.array_equal(win[P["d0"] + i], u[r0:r0 + rows])
+        assert np.all(covered == 1)
+    assert planned > 90

@@ -162,6 +162,10 @@ def adjoint_pins(*kinds):
     return run
 
 
+def sa_hierarchy_pins():
+    TSA.test_sa_hierarchy_pcg_32()
+
+
 def vcycle_adjoint_pins():
     TD.test_vcycle_backward_symmetric_and_fd()
 
@@ -274,8 +278,43 @@ MUTANTS = [
     ("sa_tentative_transposed", SA + "tentative", "(np.arange(n), agg)", "(agg, np.arange(n))", sa_pins),
     ("loss_gradient_factor", AD + "error_reduction_loss", "gz = -2.0 * Ae1 / den / m",
      "gz = -Ae1 / den / m", loss_pins),
+    ("power_one_step_short", SM + "power_lambda", "for _ in range(iters):",
+     "for _ in range(iters - 1):", power_pins),
+    ("jacobi_polynomial_exponent", PA + "p_jacobi", "** k", "** (k + 1)", smoother_pins("l1jacobi")),
+    # (the 4th-kind and optimal 1st-kind sups equal the limit at x -> 0, which
+    # gamma_sup takes analytically, so the objective itself is pinned by the
+    # optimised 4th-kind series, whose maxima the Remez exchange locates with it)
+    ("objective_denominator", PA + "f_objective", "(1.0 - p * p)", "(1.0 + p * p)", opt4_pins),
+    ("gamma_limit_at_zero", PA + "gamma_sup", "best = 1.0 / (2.0 * abs(pprime0))",
+     "best = 1.0 / abs(pprime0)", poly_pins),
+    ("W4_derivative", PA + "W4_deriv_at_one", "j * (j + 1) * (2 * j + 1) / 3.0",
+     "j * (j + 1) * (2 * j + 1) / 6.0", poly_pins),
+    ("T1_outside_sign", PA + "T1", "(-1.0) ** k * np.cosh", "np.cosh", cheb1_param_pins),
+    ("value_at_one_q", PA + "value_at_one", "q = (1 + s) / (1 - s)", "q = (1 + a) / (1 - a)",
+     cheb1_param_pins),
+    ("opt4_basis_index", PA + "_phi_basis", "W4(j - 1, t) / (2 * j - 1)", "W4(j - 1, t) / (2 * j + 1)",
+     opt4_pins),
+    ("amg_coarse_diag_level", AM + "__init__", "self.Mc = l1_diag(self.A[-1])",
+     "self.Mc = l1_diag(self.A[0])[:self.A[-1].shape[0]]", coarse_pins),
+    ("sa_hierarchy_stale_level", SA + "sa_hierarchy", "P, om = sa_prolongator(As[-1], agg, nc)",
+     "P, om = sa_prolongator(As[0], agg, nc)", sa_hierarchy_pins),
+    ("sa_lambda_signed", SA + "lambda_bound", "abs(A).sum(axis=1)", "A.sum(axis=1)", sa_pins),
+    ("adjoint_cheb1_recurrence", AD + "_cheb1_backward", "c1, c2 = rhos[j] * rhos[j - 1], 2.0 * rhos[j] / delta",
+     "c1, c2 = rhos[j], 2.0 * rhos[j] / delta", adjoint_pins("cheb1_opt")),
+    ("adjoint_cheb1_rho", AD + "_cheb1_backward", "gb = (rbar / M) / rho", "gb = rbar / M",
+     adjoint_pins("cheb1")),
+    ("adjoint_vcycle_pre_input", AD + "vcycle_backward", "gx1 = gx1 - A @ gres", "gx1 = gx1 + A @ gres",
+     vcycle_adjoint_pins),
+    ("adjoint_vcycle_prolong_transposed", AD + "vcycle_backward", "gxc = P.T @ gx2", "gxc = P.T @ xbar",
+     vcycle_adjoint_pins),
+    ("adjoint_dispatch_beta", AD + "smooth_backward", 'beta = None if kd == "cheb4" else spec.beta',
+     "beta = None", adjoint_pins("weights")),
     # MLP of the learned weights
     ("mlp_output_scale", ML + "forward", "np.exp(0.5 * t)", "np.exp(t)", mlp_pins),
+    ("mlp_hidden_relu", ML + "forward", "h2 = np.maximum(a2, 0.0)", "h2 = a2", mlp_pins),
+    ("mlp_layer2_gradient", ML + "backward", "gW2 = ga2.T @ h1", "gW2 = ga2.T @ a1", mlp_pins),
+    ("adam_second_moment", ML + "adam", "v = b2 * v + (1 - b2) * grad * grad",
+     "v = b2 * v + (1 - b2) * grad", mlp_pins),
     ("mlp_tanh_derivative", ML + "backward", "(1.0 - t * t)", "(1.0 - t)", mlp_pins),
     ("mlp_relu_mask", ML + "backward", "ga1 = gh1 * (a1 > 0)", "ga1 = gh1", mlp_pins),
     ("adam_bias_correction", ML + "adam", "mh = m / (1 - b1 ** step)", "mh = m", mlp_pins),
@@ -288,6 +327,7 @@ def test_pin_groups_pass_on_the_oracle():
         run()
 
 
+@pytest.mark.filterwarnings("ignore::RuntimeWarning")   # a mutant may produce NaNs
 @pytest.mark.parametrize("mid,target,old,new,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
 def test_planted_mistake_is_caught(mid, target, old, new, pins):
     with mutant(target, old, new):

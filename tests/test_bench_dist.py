@@ -79,3 +79,20 @@ def test_reference_arm_json_line():
     assert r["impl"] == "reference" and r["value"] > 0 and r["higher_is_better"] is False
     assert r["config"]["iterations"] == 11 and r["cpu_baseline"]["kind"] == "oracle"
     assert r["e2e"]["h2d_bytes_per_step"] == 0 and r["e2e"]["value"] == r["value"]
+
+
+def test_clock_summary_parses_nvidia_smi_lines():
+    # the clocks key of the bench line: median SM clock under load, the
+    # maximum, and every throttle reason seen active in any sample
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(0)
+    c.lines = ["2070, 2070, 1100.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+               "1965, 2070, 1398.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+               "2070, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+               "[N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]",
+               "garbage"]
+    s = c.summary()
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    c.lines = []
+    assert c.summary()["samples"] == 0 and c.summary()["sm_mhz"] is None

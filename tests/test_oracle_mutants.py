@@ -1,6 +1,6 @@
-"""Planted mistakes in the oracle (no GPU).
+"""Planted mistakes in the oracle and in the input generators (no GPU).
 
-Each mutant changes one expression of one oracle function the way a
+Each mutant changes one expression of one oracle (or generator) function the way a
 transcription slip would -- a dropped term, a wrong sign, index or coefficient,
 a transposed operand, a stale variable -- and at least one of the oracle's own
 pins must then fail.  This is the evidence that the pins constrain every part
@@ -27,6 +27,7 @@ import test_oracle_mlp as TM
 import test_oracle_params as TP
 import test_oracle_sa as TSA
 import test_oracle_smoother as TS
+import test_problems as TPR
 from oracle import smoother as oracle_smoother
 from paper_2407_09848_gb300 import problems as pr
 
@@ -174,6 +175,13 @@ def loss_pins():
     TD.test_error_reduction_loss_gradient_fd()
 
 
+def generator_pins():
+    TPR.test_poisson_stencil_values()
+    TPR.test_aniso_weak_direction_is_z()
+    TPR.test_varcoef_faces_are_harmonic_means_and_boundary_faces_the_cell_value()
+    TPR.test_grf_correlation_length()
+
+
 def mlp_pins():
     TM.test_backward_central_differences()
     TM.test_adam_first_step_closed_form()
@@ -185,6 +193,7 @@ AM = "oracle.amg:OracleAMG."
 SA = "oracle.sa:"
 AD = "oracle.adjoint:"
 ML = "oracle.mlp:"
+GE = "paper_2407_09848_gb300.problems:"
 
 # (id, target, original text, planted mistake, pins that must catch it)
 MUTANTS = [
@@ -309,6 +318,16 @@ MUTANTS = [
      vcycle_adjoint_pins),
     ("adjoint_dispatch_beta", AD + "smooth_backward", 'beta = None if kd == "cheb4" else spec.beta',
      "beta = None", adjoint_pins("weights")),
+    # the seeded input generators both sides consume
+    ("gen_arithmetic_mean_faces", GE + "varcoef", "2.0 * a[..., :-1] * a[..., 1:] / (a[..., :-1] + a[..., 1:])",
+     "0.5 * (a[..., :-1] + a[..., 1:])", generator_pins),
+    ("gen_neumann_boundary", GE + "varcoef", "f = np.concatenate([a[..., :1], inner, a[..., -1:]], axis=-1)",
+     "f = np.concatenate([0 * a[..., :1], inner, 0 * a[..., -1:]], axis=-1)", generator_pins),
+    ("gen_aniso_axis", GE + "aniso", "np.full((nz + 1, ny, nx), float(eps))",
+     "np.ones((nz + 1, ny, nx))", generator_pins),
+    ("gen_grf_filter_width", GE + "grf", "s = ell / np.sqrt(2.0)", "s = ell", generator_pins),
+    ("gen_diag_drops_face", GE + "_from_faces", "+ fz[:-1, :, :] + fz[1:, :, :]", "+ fz[1:, :, :]",
+     generator_pins),
     # MLP of the learned weights
     ("mlp_output_scale", ML + "forward", "np.exp(0.5 * t)", "np.exp(t)", mlp_pins),
     ("mlp_hidden_relu", ML + "forward", "h2 = np.maximum(a2, 0.0)", "h2 = a2", mlp_pins),

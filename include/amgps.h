@@ -317,6 +317,17 @@ amgps_status amgps_set_option(amgps_ctx* ctx, int option, int64_t value);
 amgps_status amgps_tma_plan_stats(const amgps_csr* A, amgps_prec prec, int64_t* tiles,
                                   int64_t* generic_slices, int* stage_bytes, int* nstages);
 
+/* Host-only (no device needed): the step scalars the kernels use for one
+ * application of `kind` at `degree` (weights and rho as in
+ * amgps_set_smoother), arrays of degree+1 doubles indexed by step j.
+ * 4th kind (CHEB4, CHEB4_OPT, WEIGHTS): step j computes
+ * z_j = c1[j] z_{j-1} + c2[j] M^{-1} r_{j-1}, x += beta[j] z_j (Sec. 2.1).
+ * 1st kind (CHEB1, CHEB1_OPT; Algorithm 1): d_0 = c2[0] r_0 and, for j >= 1,
+ * d_j = c1[j] d_{j-1} + c2[j] r_j, with residuals scaled by *rhoinv.
+ * l1-Jacobi uses none of them.  AMGPS_E_ARG for a bad kind, degree or weight. */
+amgps_status amgps_step_coefs(amgps_kind kind, int degree, const double* weights, double rho,
+                              double* c1, double* c2, double* beta, double* rhoinv);
+
 /* Host-only inspection (no device needed): the TMA plan behind
  * amgps_tma_plan_stats.  info[32] receives, in order: rows per tile, stencil
  * width w, window groups G, d0 (stage-window index of the tile's own rows),

@@ -83,6 +83,8 @@ _SIGS = {
                             C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "amgps_mlp_adam": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_float, C.c_float,
                         C.c_float, C.c_float, C.c_void_p], C.c_int),
+    "amgps_step_coefs": ([C.c_int, C.c_int, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p,
+                          C.c_void_p, C.POINTER(C.c_double)], C.c_int),
     "amgps_tma_plan": ([C.POINTER(CSR), C.c_int, C.c_void_p, C.POINTER(C.c_int64), C.c_void_p,
                         C.POINTER(C.c_int64), C.c_void_p], C.c_int),
     "amgps_sell_layout": ([C.POINTER(CSR), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
@@ -192,6 +194,20 @@ def tma_plan_stats(A, prec="f64"):
     if st:
         raise AmgpsError(st, lib().amgps_last_error(None).decode())
     return t.value, g.value, sb.value, ns.value
+
+
+def step_coefs(kind, degree, weights=None, rho=0.0):
+    """Host-only: (c1, c2, beta, rhoinv) of one application, arrays indexed by
+    step j = 0..degree (see amgps_step_coefs)."""
+    c1, c2, beta = (np.zeros(degree + 1) for _ in range(3))
+    ri = C.c_double()
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    stat = lib().amgps_step_coefs(KIND[kind], int(degree), None if w is None else w.ctypes.data,
+                                  float(rho), c1.ctypes.data, c2.ctypes.data, beta.ctypes.data,
+                                  C.byref(ri))
+    if stat:
+        raise AmgpsError(stat, lib().amgps_last_error(None).decode())
+    return c1, c2, beta, ri.value
 
 
 def tma_plan(A, prec="f64"):

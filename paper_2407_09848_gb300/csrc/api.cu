@@ -1694,6 +1694,23 @@ amgps_status amgps_tma_plan_stats(const amgps_csr* A, amgps_prec prec, int64_t* 
   });
 }
 
+amgps_status amgps_step_coefs(amgps_kind kind, int degree, const double* weights, double rho,
+                              double* c1, double* c2, double* beta, double* rhoinv) {
+  return guard(nullptr, [&] {
+    check_kind_degree(kind, degree);
+    REQ(c1 && c2 && beta && rhoinv, AMGPS_E_ARG, "null argument");
+    REQ(kind != AMGPS_WEIGHTS || weights, AMGPS_E_ARG, "AMGPS_WEIGHTS needs weights");
+    REQ(std::isfinite(rho), AMGPS_E_ARG, "non-finite rho");
+    const Coefs cf = make_coefs(kind, degree, weights, rho);
+    for (int j = 0; j <= degree; ++j) {
+      c1[j] = cf.c1[j];
+      c2[j] = cf.c2[j];
+      beta[j] = cf.beta[j];
+    }
+    *rhoinv = cf.rhoinv;
+  });
+}
+
 amgps_status amgps_tma_plan(const amgps_csr* A, amgps_prec prec, int32_t* info, int64_t* ntiles,
                             int64_t* tiles, int64_t* ngen, int32_t* gen) {
   return guard(nullptr, [&] {

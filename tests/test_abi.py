@@ -369,3 +369,45 @@ def test_tma_plan_stage_emulation(lib, prec):
             assert np.array_equal(win[P["d0"] + i], u[r0:r0 + rows])
         assert np.all(covered == 1)
     assert planned > 90
+
+
+@pytest.mark.parametrize("kind", ["cheb4", "cheb4_opt", "weights", "cheb1_opt", "cheb1"])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 6, 9, 16])
+def test_step_coefs_realise_the_error_polynomials(lib, kind, k):
+    # host-only: run the library's step scalars through the kernels' recurrences
+    # on one eigen-component (M^{-1}A = lambda, b = 0, error e0 = 1): the error
+    # after one application must be the closed-form polynomial of Sec. 2.1 /
+    # Algorithm 1 (the oracle's parameter code)
+    from oracle import params as P
+    # the 4th-kind closed form (via arccos) holds on [0, 1]; tau_k also beyond
+    lam = np.linspace(0.0, 1.0 if kind.startswith("cheb4") or kind == "weights" else 1.3, 131)
+    weights = 1.0 + 0.2 * np.sin(np.arange(1, k + 1)) if kind == "weights" else None
+    rho = 1.07 if kind == "cheb1" else 0.0
+    c1, c2, beta, rhoinv = amgps.step_coefs(kind, k, weights, rho)
+    if kind in ("cheb4", "cheb4_opt", "weights"):
+        x, z, r = np.ones_like(lam), np.zeros_like(lam), -lam   # r = M^{-1}(b - A x)
+        for j in range(1, k + 1):
+            z = c1[j] * z + c2[j] * r
+            x = x + beta[j] * z
+            r = r - lam * z
+        if kind == "cheb4":
+            ref = P.p_cheb4(k, lam)
+            assert np.all(beta[1:] == 1.0)
+        else:
+            # the library's tabulated weights (pinned to the oracle's Remez
+            # solution by test_opt4_table_agrees_with_oracle)
+            b = amgps.opt4_weights(k) if kind == "cheb4_opt" else weights
+            ref = P.p_opt4(b, lam)
+    else:
+        a = P.a_star(k)
+        rr = 1.07 if kind == "cheb1" else 1.0
+        assert rhoinv == pytest.approx(1.0 / rr, rel=1e-15)
+        r = rhoinv * (-lam)
+        d = c2[0] * r
+        x = 1.0 + d
+        for j in range(1, k):
+            r = r - rhoinv * lam * d
+            d = c1[j] * d + c2[j] * r
+            x = x + d
+        ref = P.p_cheb1(k, a, lam, rr)
+    assert np.max(np.abs(x - ref)) <= 5e-12 * max(1.0, np.abs(ref).max())

@@ -317,6 +317,12 @@ amgps_status amgps_set_option(amgps_ctx* ctx, int option, int64_t value);
 amgps_status amgps_tma_plan_stats(const amgps_csr* A, amgps_prec prec, int64_t* tiles,
                                   int64_t* generic_slices, int* stage_bytes, int* nstages);
 
+/* Host-only (no device needed): the BF16 bit patterns that
+ * amgps_hierarchy_load stores for AMGPS_BF16 levels -- each finite FP64 value
+ * rounded directly to the nearest BF16 value, ties to even (no intermediate
+ * FP32 rounding).  AMGPS_E_ARG for a non-finite value. */
+amgps_status amgps_round_bf16(const double* x, int64_t n, uint16_t* out);
+
 /* Host-only (no device needed): the step scalars the kernels use for one
  * application of `kind` at `degree` (weights and rho as in
  * amgps_set_smoother), arrays of degree+1 doubles indexed by step j.

@@ -83,6 +83,7 @@ _SIGS = {
                             C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "amgps_mlp_adam": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_float, C.c_float,
                         C.c_float, C.c_float, C.c_void_p], C.c_int),
+    "amgps_round_bf16": ([C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
     "amgps_step_coefs": ([C.c_int, C.c_int, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p,
                           C.c_void_p, C.POINTER(C.c_double)], C.c_int),
     "amgps_tma_plan": ([C.POINTER(CSR), C.c_int, C.c_void_p, C.POINTER(C.c_int64), C.c_void_p,
@@ -194,6 +195,16 @@ def tma_plan_stats(A, prec="f64"):
     if st:
         raise AmgpsError(st, lib().amgps_last_error(None).decode())
     return t.value, g.value, sb.value, ns.value
+
+
+def round_bf16(x):
+    """Host-only: BF16 bit patterns (uint16) of FP64 values as the loader rounds them."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros(x.size, np.uint16)
+    stat = lib().amgps_round_bf16(x.ctypes.data, x.size, out.ctypes.data)
+    if stat:
+        raise AmgpsError(stat, lib().amgps_last_error(None).decode())
+    return out
 
 
 def step_coefs(kind, degree, weights=None, rho=0.0):

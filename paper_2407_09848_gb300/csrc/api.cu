@@ -1694,6 +1694,16 @@ amgps_status amgps_tma_plan_stats(const amgps_csr* A, amgps_prec prec, int64_t* 
   });
 }
 
+amgps_status amgps_round_bf16(const double* x, int64_t n, uint16_t* out) {
+  return guard(nullptr, [&] {
+    REQ(n >= 0 && (n == 0 || (x && out)), AMGPS_E_ARG, "null argument");
+    for (int64_t i = 0; i < n; ++i) {
+      REQ(std::isfinite(x[i]), AMGPS_E_ARG, "non-finite value");
+      out[i] = dbl_to_bf16(x[i]);
+    }
+  });
+}
+
 amgps_status amgps_step_coefs(amgps_kind kind, int degree, const double* weights, double rho,
                               double* c1, double* c2, double* beta, double* rhoinv) {
   return guard(nullptr, [&] {

@@ -411,3 +411,51 @@ def test_step_coefs_realise_the_error_polynomials(lib, kind, k):
             x = x + d
         ref = P.p_cheb1(k, a, lam, rr)
     assert np.max(np.abs(x - ref)) <= 5e-12 * max(1.0, np.abs(ref).max())
+
+
+def _bf16_value(bits):
+    import struct
+    from fractions import Fraction
+    return Fraction(struct.unpack("<f", struct.pack("<I", int(bits) << 16))[0])
+
+
+def _bf16_reference(x):
+    """Nearest BF16 to x, ties to the even pattern, by exact rational comparison
+    of the two BF16 neighbours that bracket x (BF16 = the high 16 bits of an
+    FP32 pattern)."""
+    import struct
+    from fractions import Fraction
+    X = Fraction(x)
+    f = struct.unpack("<I", struct.pack("<f", float(np.float32(x))))[0] >> 16
+    cands = [c & 0xFFFF for c in (f - 1, f, f + 1)]
+    cands = [c for c in cands if (c & 0x7F80) != 0x7F80]          # finite patterns only
+    best = min(cands, key=lambda c: (abs(_bf16_value(c) - X), c & 1))
+    return best
+
+
+def test_bf16_rounding_is_direct_and_ties_to_even(lib):
+    # reading 13: FP64 -> BF16 directly, round to nearest, ties to even; an
+    # intermediate FP32 rounding would turn a value just above a BF16 midpoint
+    # into the midpoint itself and round it the wrong way
+    import struct
+    rng = np.random.default_rng(13)
+    xs = list(rng.standard_normal(2000) * 10.0 ** rng.integers(-30, 30, 2000))
+    for b in rng.integers(0x0080, 0x7F00, 300):       # around BF16 values and midpoints
+        lo, hi = _bf16_value(b), _bf16_value(b + 1)
+        mid = float((lo + hi) / 2)
+        xs += [mid, np.nextafter(mid, np.inf), np.nextafter(mid, -np.inf), float(lo), -mid]
+        # just above the midpoint but within half an FP32 ulp of it: FP32
+        # rounding lands exactly on the midpoint (the double-rounding trap)
+        f32_ulp = float(np.spacing(np.float32(mid)))
+        xs.append(mid + 0.25 * f32_ulp)
+        xs.append(mid - 0.25 * f32_ulp)
+    xs += [0.0, -0.0, 6.0, -1.0, 1.0 / 3.0, 3.0e38, -3.0e38, 1e-38]
+    got = amgps.round_bf16(np.array(xs))
+    want = np.array([_bf16_reference(x) for x in xs], dtype=np.uint16)
+    bad = np.nonzero(got != want)[0]
+    assert bad.size == 0, [(xs[i], hex(got[i]), hex(want[i])) for i in bad[:5]]
+    # Poisson's values are exact in BF16
+    assert np.array_equal(amgps.round_bf16(np.array([6.0, -1.0, 24.0, -4.0])),
+                          np.array([0x40C0, 0xBF80, 0x41C0, 0xC080], dtype=np.uint16))
+    with pytest.raises(amgps.AmgpsError):
+        amgps.round_bf16(np.array([1.0, np.inf]))

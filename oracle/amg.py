@@ -68,7 +68,7 @@ class OracleAMG:
         x = smooth(A, b, x, spec, M=M)
         return x
 
-    def pcg(self, b, rtol=1e-8, maxit=1000, x0=None, flexible=False, precond=None):
+    def pcg(self, b, rtol=1e-8, maxit=1000, flexible=False, precond=None):
         """Preconditioned CG, preconditioner = one V-cycle.
 
         flexible=True takes the Polak-Ribiere form of the direction update,
@@ -77,13 +77,14 @@ class OracleAMG:
         stays robust when the preconditioner is not exactly a fixed symmetric
         operator.  precond (optional) replaces the V-cycle, e.g. one smoother
         application for the smoother-only experiment of the remark in
-        Sec. 2.3.  Returns (x, iterations, recurrence residual ratio,
-        history); the iteration count is the number of products A p performed."""
+        Sec. 2.3.  Starts from x0 = 0.  Returns (x, iterations, recurrence
+        residual ratio, history); the iteration count is the number of products
+        A p performed."""
         B = self.vcycle if precond is None else precond
         A = self.A[0]
         b = np.asarray(b, dtype=np.float64)
-        x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
-        r = b - A @ x if x0 is not None else b.copy()
+        x = np.zeros_like(b)
+        r = b.copy()
         bnorm = np.linalg.norm(b)
         hist = [np.linalg.norm(r) / bnorm]
         if hist[-1] <= rtol:

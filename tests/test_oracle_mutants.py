@@ -203,6 +203,8 @@ MUTANTS = [
     ("cheb4_c2_denominator", SM + "cheb4", "(8 * j - 4) / (2 * j + 1) / rho",
      "(8 * j - 4) / (2 * j - 1) / rho", smoother_pins("cheb4")),
     ("cheb4_no_Minv", SM + "cheb4", "/ rho * (r / M)", "/ rho * r", smoother_pins("cheb4")),
+    ("cheb4_rho_inverted", SM + "cheb4", "(8 * j - 4) / (2 * j + 1) / rho", "(8 * j - 4) / (2 * j + 1) * rho",
+     smoother_pins("cheb4")),
     ("cheb4opt_weighted_r", SM + "cheb4", "r = r - A @ z", "r = r - bj * (A @ z)",
      smoother_pins("cheb4_opt")),
     ("cheb4_drops_a_residual", SM + "cheb4", "if j < k:", "if j < k - 1:", smoother_pins("cheb4")),

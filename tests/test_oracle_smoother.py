@@ -12,15 +12,15 @@ from oracle import params as P
 from oracle.smoother import SmootherSpec, l1_diag, power_lambda, smooth, error_poly
 
 KIND_CASES = [("l1jacobi", None), ("cheb4", None), ("cheb4_opt", None),
-              ("weights", "rand"), ("cheb1_opt", None), ("cheb1", 1.1)]
+              ("weights", "rand"), ("cheb1_opt", None), ("cheb1", 1.1), ("cheb4", 1.2)]
 
 
 def make_spec(kind, extra, k, seed=0):
     if kind == "weights":
         beta = 1.0 + 0.3 * np.random.default_rng(seed).uniform(-1, 1, k)
         return SmootherSpec(kind, k, beta=beta)
-    if kind == "cheb1":
-        return SmootherSpec(kind, k, rho=extra)
+    if kind == "cheb1" or (kind == "cheb4" and extra is not None):
+        return SmootherSpec(kind, k, rho=extra)   # an explicit rho(M^{-1}A) estimate
     return SmootherSpec(kind, k)
 
 

@@ -371,7 +371,8 @@ def test_tma_plan_stage_emulation(lib, prec):
     assert planned > 90
 
 
-@pytest.mark.parametrize("kind", ["cheb4", "cheb4_opt", "weights", "cheb1_opt", "cheb1"])
+@pytest.mark.parametrize("kind", ["cheb4", "cheb4_opt", "weights", "cheb1_opt", "cheb1",
+                                  "cheb4_rho"])
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 6, 9, 16])
 def test_step_coefs_realise_the_error_polynomials(lib, kind, k):
     # host-only: run the library's step scalars through the kernels' recurrences
@@ -382,7 +383,9 @@ def test_step_coefs_realise_the_error_polynomials(lib, kind, k):
     # the 4th-kind closed form (via arccos) holds on [0, 1]; tau_k also beyond
     lam = np.linspace(0.0, 1.0 if kind.startswith("cheb4") or kind == "weights" else 1.3, 131)
     weights = 1.0 + 0.2 * np.sin(np.arange(1, k + 1)) if kind == "weights" else None
-    rho = 1.07 if kind == "cheb1" else 0.0
+    rho = {"cheb1": 1.07, "cheb4_rho": 1.2}.get(kind, 0.0)
+    explicit_rho = kind == "cheb4_rho"
+    kind = "cheb4" if explicit_rho else kind
     c1, c2, beta, rhoinv = amgps.step_coefs(kind, k, weights, rho)
     if kind in ("cheb4", "cheb4_opt", "weights"):
         x, z, r = np.ones_like(lam), np.zeros_like(lam), -lam   # r = M^{-1}(b - A x)
@@ -391,7 +394,7 @@ def test_step_coefs_realise_the_error_polynomials(lib, kind, k):
             x = x + beta[j] * z
             r = r - lam * z
         if kind == "cheb4":
-            ref = P.p_cheb4(k, lam)
+            ref = P.p_cheb4(k, lam / (1.2 if explicit_rho else 1.0))
             assert np.all(beta[1:] == 1.0)
         else:
             # the library's tabulated weights (pinned to the oracle's Remez

@@ -462,3 +462,17 @@ def test_bf16_rounding_is_direct_and_ties_to_even(lib):
                           np.array([0x40C0, 0xBF80, 0x41C0, 0xC080], dtype=np.uint16))
     with pytest.raises(amgps.AmgpsError):
         amgps.round_bf16(np.array([1.0, np.inf]))
+
+
+def test_binding_rejects_non_device_vectors():
+    # host-side: the binding passes only contiguous FP64 CUDA tensors of the
+    # right length to the library (a host pointer never reaches a kernel)
+    import torch
+    with pytest.raises(TypeError):
+        amgps._dptr(torch.zeros(8, dtype=torch.float64), 8, "b")           # host tensor
+    with pytest.raises(TypeError):
+        amgps._dptr(np.zeros(8), 8, "b")                                  # not a tensor
+    with pytest.raises(TypeError):
+        amgps._dptr(torch.zeros(8, dtype=torch.float32), 8, "b")
+    with pytest.raises(TypeError):
+        amgps._dptr(torch.zeros((4, 4), dtype=torch.float64).t(), 16, "b")  # non-contiguous

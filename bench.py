@@ -91,6 +91,18 @@ def step_source_hash():
     return h.hexdigest()
 
 
+def oracle_threads():
+    """Threads the CPU oracle's BLAS calls may use (1 unless the environment
+    set the pools before this module pinned them)."""
+    vals = []
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        try:
+            vals.append(int(os.environ.get(v, "1")))
+        except ValueError:
+            pass
+    return max(vals) if vals else 1
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -386,7 +398,7 @@ def run_reference(a):
            "data": "synthetic",
            "config": {"workload": workload_name(a), "grid": a.grid, "kind": a.kind,
                       "degree": a.degree, "rtol": a.rtol, "iterations": its},
-           "cpu_baseline": {"value": value_ms, "unit": "ms", "cores": 1, "kind": "oracle",
+           "cpu_baseline": {"value": value_ms, "unit": "ms", "cores": oracle_threads(), "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value_ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -540,7 +552,7 @@ def run_ours(a):
     cpu = None
     if not a.no_cpu and rank == 0:
         t_iter, _ = time_oracle_iteration(H, b, a.kind, a.degree)
-        cpu = {"value": t_iter * its * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
+        cpu = {"value": t_iter * its * 1e3, "unit": "ms", "cores": oracle_threads(), "kind": "oracle",
                "sample": f"one oracle PCG iteration (V-cycle + SpMV + updates) of the same "
                          f"{workload_name(a)} solve, {t_iter:.2f} s, x {its} iterations"}
 

@@ -77,6 +77,7 @@ def test_reference_arm_json_line():
                 "cpu_baseline", "e2e"):
         assert key in r, key
     assert r["impl"] == "reference" and r["value"] > 0 and r["higher_is_better"] is False
+    assert r["cpu_baseline"]["cores"] == 1      # BLAS pools pinned to one thread
     assert r["config"]["iterations"] == 11 and r["cpu_baseline"]["kind"] == "oracle"
     assert r["e2e"]["h2d_bytes_per_step"] == 0 and r["e2e"]["value"] == r["value"]
 
@@ -96,3 +97,21 @@ def test_clock_summary_parses_nvidia_smi_lines():
     assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
     c.lines = []
     assert c.summary()["samples"] == 0 and c.summary()["sm_mhz"] is None
+
+
+def test_oracle_threads_reports_the_pools():
+    sys.path.insert(0, ROOT)
+    import bench
+    old = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS",
+                                          "MKL_NUM_THREADS")}
+    try:
+        os.environ.update(OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        assert bench.oracle_threads() == 1
+        os.environ["OMP_NUM_THREADS"] = "4"
+        assert bench.oracle_threads() == 4
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v

@@ -10,6 +10,12 @@ for the GPU path (identical iteration counts) and the scale factor of the
 oracle's bounded timing sample in the benchmark.
 
 Run: python tests/golden/make_oracle_iterations.py [--grids 32,256] [--jobs 6]
+
+Runs are merged into the stored file by (grid, kind, degree).  The committed
+file was written by the default run plus
+  --kinds cheb4,cheb4_opt,cheb1_opt,l1jacobi --degrees 8,10,12,16 --grids 32
+  --kinds cheb4,cheb4_opt,cheb1_opt,l1jacobi --degrees 8,10,12 --grids 256
+  --kinds l1jacobi --degrees 1,2,3,4,5,6
 """
 import argparse
 import json

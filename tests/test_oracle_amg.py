@@ -275,3 +275,27 @@ def test_conjugacy_defect_under_a_variable_preconditioner(flexible):
         assert abs(lhs - rhs) <= 1e-10 * scale, (k, lhs, rhs)
         if k >= 1:
             assert abs(rhs) > 1e-6 * scale               # the preconditioner change matters
+
+
+@pytest.mark.parametrize("kind,k", [("cheb4_opt", 4), ("cheb4", 2), ("cheb1_opt", 6), ("cheb1", 4),
+                                    ("l1jacobi", 1), ("cheb4_opt", 16)])
+def test_stored_iteration_counts_match_the_oracle(kind, k):
+    # the GPU tests compare against tests/golden/oracle_pcg_iterations.json;
+    # a sample of its 32^3 entries must be what the oracle gives today
+    import json
+    import os
+    from oracle.smoother import power_lambda
+    path = os.path.join(os.path.dirname(__file__), "golden", "oracle_pcg_iterations.json")
+    runs = {(r["grid"], r["kind"], r["degree"]): r for r in json.load(open(path))["runs"]}
+    stored = runs[(32, kind, k)]["iterations"]
+    A, Pl = hier(pr.poisson(32), 512)
+    specs = []
+    for Al in A[:-1]:
+        if kind == "cheb1":
+            lam = power_lambda(Al, pr.vec_uniform(Al.shape[0], seed=0), iters=10)
+            specs.append(SmootherSpec(kind, k, rho=1.1 * lam))
+        else:
+            specs.append(SmootherSpec(kind, k))
+    b = pr.rhs_uniform(A[0].shape[0], seed=0)
+    _, it, rel, _ = OracleAMG(A, Pl, specs).pcg(b, rtol=1e-8, maxit=1000)
+    assert rel <= 1e-8 and it == stored

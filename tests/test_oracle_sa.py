@@ -113,3 +113,23 @@ def test_geometric_aggregates_match_unsmoothed_hierarchy():
     assert len(levels) == H.n_levels - 1
     for (agg, nc, shp), lv, nxt in zip(levels, H.levels[:-1], H.levels[1:]):
         assert np.array_equal(agg, lv.agg) and nc == nxt.A.shape[0] and shp == nxt.shape
+
+
+def test_stored_sa_iteration_counts_match_the_oracle():
+    # the GPU tests compare against tests/golden/oracle_sa_pcg_iterations.json;
+    # its 32^3 entries must be what the oracle gives today
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "oracle_sa_pcg_iterations.json")
+    runs = [r for r in json.load(open(path))["runs"] if r["grid"] == 32]
+    assert len(runs) == 3
+    st = pr.poisson(32)
+    levels = pr.geometric_aggregates(st.shape, coarse_max=512)
+    As, Ps, om = sa.sa_hierarchy(pr.to_csr(st), [a for a, _, _ in levels],
+                                 [nc for _, nc, _ in levels])
+    b = pr.rhs_uniform(32768, seed=0)
+    for r in runs:
+        assert [a.shape[0] for a in As] == r["levels"] and [a.nnz for a in As] == r["nnz"]
+        assert np.allclose(om, r["omega"], rtol=1e-15, atol=0)
+        _, it, rel, _ = OracleAMG(As, Ps, SmootherSpec(r["kind"], r["degree"])).pcg(b, rtol=1e-8)
+        assert rel <= 1e-8 and it == r["iterations"]

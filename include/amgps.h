@@ -242,14 +242,18 @@ amgps_status amgps_mlp_adam(float* params_dev, const float* grads_dev, float* m_
  * under an allocator that owns all device memory, or a phase of a real-time
  * loop where allocation is forbidden).  No counterpart in the paper: same
  * kernels and result as amgps_smooth, but the work vectors live in one static
- * device array (3 MiB on each GPU that loads the library, held until exit), so
- * levels with more than 65536 rows are rejected with AMGPS_E_ARG.  The first
- * call on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.
- * Every call shares the array: calls that overlap on the GPU (other streams,
- * other contexts, other host threads) race and corrupt each other's results.
- * Nothing needs clearing between calls: each call writes every scratch entry
- * it reads before reading it.  Arguments as for amgps_smooth. */
+ * device array of 3 MiB, so levels with more than 65536 rows are rejected with
+ * AMGPS_E_ARG.  amgps_create claims that array on its device (it looks up the
+ * array's device address with cudaGetSymbolAddress, which under lazy module
+ * loading also brings the array onto the device) and keeps the address in the
+ * context; the array stays on that device until the process exits.  Kernels
+ * are loaded by the CUDA runtime on their first launch: before the phase where
+ * allocation is forbidden, run the same smoother once through amgps_smooth (or
+ * load modules eagerly, CUDA_MODULE_LOADING=EAGER).  Every call shares the
+ * array: calls that overlap on the GPU (other streams, other contexts, other
+ * host threads) race and corrupt each other's results.  Nothing needs
+ * clearing between calls: each call writes every scratch entry it reads before
+ * reading it.  Arguments as for amgps_smooth. */
 amgps_status amgps_smooth_noalloc(amgps_ctx* ctx, int level, amgps_kind kind, int degree,
                                   const double* b_dev, double* x_dev, int x_is_zero);
 

@@ -175,6 +175,7 @@ struct amgps_ctx {
   std::vector<Pair> pending;
   std::vector<cudaEvent_t> pool;
   int64_t prof_launches[5] = {};  // class 3 (kernel count) is kept apart
+  void* noalloc = nullptr;        // device address of the allocation-free scratch array
   double prof_ms[5] = {};
   double prof_bytes[5] = {};
 };
@@ -949,32 +950,30 @@ void pcg_impl(amgps_ctx* c, const double* b, double* x, double rtol, int maxit, 
 // Its work vectors (the recurrence residual r, the two z buffers, the second
 // x buffer and, for FP32/BF16 hierarchies, the FP32 copies of b and x) live in
 // this file-scope device array instead of the context's per-level buffers, so
-// the call itself allocates nothing.  The array exists on every GPU that loads
-// the library, for the life of the process: kNoAllocRows rows x 6 vectors x
-// 8 bytes = 3 MiB.  Host code must not pass the symbol itself to a kernel (on
-// the host it is only a stand-in); noalloc_scratch() looks up its device
-// address once per device with that device current.
+// the call itself allocates nothing.  kNoAllocRows rows x 6 vectors x 8 bytes
+// = 3 MiB.  Host code must not pass the symbol itself to a kernel (on the host
+// it is only a stand-in): amgps_create looks up its device address with the
+// context's device current and keeps it in the context.  That lookup is also
+// what brings this file's device module (which holds only the array) onto the
+// device under the CUDA runtime's lazy module loading, so the array is claimed
+// when a context is created, not by the first allocation-free call.  The
+// address stays valid while that device's primary context lives, which the
+// library context's own buffers need as well.
 // ---------------------------------------------------------------------------
 constexpr int64_t kNoAllocRows = 65536;
 constexpr int kNoAllocVectors = 6;
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocVectors * kNoAllocRows];
 
-void* noalloc_scratch(int device) {
-  static std::mutex mu;
-  static void* addr[256] = {};
-  REQ(device >= 0 && device < 256, AMGPS_E_ARG, "device index out of range");
-  std::lock_guard<std::mutex> lock(mu);
-  if (!addr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      throw Fail{AMGPS_E_CUDA, std::string("cudaGetSymbolAddress(scratch): ") +
-                                   cudaGetErrorString(e)};
-    }
-    addr[device] = p;
+// Device address of the scratch array on the current device.
+void* noalloc_scratch_lookup() {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    throw Fail{AMGPS_E_CUDA, std::string("cudaGetSymbolAddress(scratch): ") +
+                                 cudaGetErrorString(e)};
   }
-  return addr[device];
+  return p;
 }
 
 // ===========================================================================
@@ -1049,6 +1048,7 @@ amgps_status amgps_create(amgps_ctx** out, int device, void* user_stream) {
     u->device = device;
     CK(cudaDeviceGetAttribute(&u->nsm, cudaDevAttrMultiProcessorCount, device));
     u->ustream = (cudaStream_t)user_stream;
+    u->noalloc = noalloc_scratch_lookup();  // with `device` current (see above)
     CK(cudaStreamCreateWithFlags(&u->stream, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&u->ev_in, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&u->ev_out, cudaEventDisableTiming));
@@ -1347,7 +1347,8 @@ amgps_status amgps_smooth_noalloc(amgps_ctx* c, int level, amgps_kind kind, int 
         "AMGPS_WEIGHTS: set the level's weights of this degree first");
     const Coefs cf = make_coefs(kind, degree, sp.w, sp.rho);
     enter(c);
-    char* base = (char*)noalloc_scratch(c->device);
+    REQ(c->noalloc != nullptr, AMGPS_E_STATE, "no scratch address in this context");
+    char* base = (char*)c->noalloc;
     const size_t stride = (size_t)kNoAllocRows * sizeof(double);
     // Point the level's work vectors at the static scratch for this call only.
     struct Restore {

@@ -6,8 +6,10 @@ outside allocator owns the device memory, or allocation is forbidden in that
 phase of their loop).  amgps_smooth_noalloc runs the same kernels with its work
 vectors in a static device array of 65536 rows; this test calls it through the
 C ABI twice in a row and checks each result against amgps_smooth's within the
-parity tolerance of the other GPU tests, and that a larger level is refused.
-The file name makes pytest collect it last.
+parity tolerance of the other GPU tests, that a larger level is refused, and
+that the calls leave the device's free memory and torch's allocator untouched
+(the scratch array is claimed when the context is created).  The file name
+makes pytest collect it last.
 """
 import numpy as np
 import pytest
@@ -75,3 +77,36 @@ def test_smooth_noalloc_rejects_large_level(torch_cuda):
     S.smooth_noalloc(1, "cheb4_opt", 4, b1, x1, x_is_zero=True)
     S.smooth(1, "cheb4_opt", 4, b1, x2, x_is_zero=True)
     assert rel(x1.cpu().numpy(), x2.cpu().numpy()) <= TOL
+
+
+def test_smooth_noalloc_allocates_nothing(torch_cuda):
+    """Free device memory (cudaMemGetInfo) and torch's allocated bytes are the
+    same before the first allocation-free call on a fresh context and after
+    several of them.  The kernels are loaded first through amgps_smooth (the
+    CUDA runtime loads a kernel's module on its first launch)."""
+    from paper_2407_09848_gb300.amgps import Solver
+    torch = torch_cuda
+    H = pr.build_hierarchy(pr.poisson(24, 22, 20), coarse_max=100)
+    S = Solver().load(H.A, H.P)
+    n = H.levels[0].A.shape[0]
+    rng = np.random.default_rng(3)
+    b = torch.from_numpy(rng.uniform(-1, 1, n)).cuda()
+    x0 = torch.from_numpy(rng.uniform(-1, 1, n)).cuda()
+    calls = [("cheb4_opt", 4, True), ("cheb4_opt", 4, False), ("cheb1_opt", 3, False),
+             ("l1jacobi", 2, True)]
+    outs = [x0.clone() for _ in calls]
+    refs = [x0.clone() for _ in calls]
+    for (kind, k, zero), r in zip(calls, refs):
+        S.smooth(0, kind, k, b, r, x_is_zero=zero)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    used0 = torch.cuda.memory_allocated()
+    for rep in range(3):
+        for (kind, k, zero), o in zip(calls, outs):
+            o.copy_(x0)
+            S.smooth_noalloc(0, kind, k, b, o, x_is_zero=zero)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0, rep
+        assert torch.cuda.memory_allocated() == used0, rep
+    for o, r in zip(outs, refs):
+        assert rel(o.cpu().numpy(), r.cpu().numpy()) <= TOL

@@ -6,6 +6,7 @@ from oracle.adjoint import smooth_backward, vcycle_backward
 from oracle.amg import OracleAMG
 from oracle.smoother import SmootherSpec
 from paper_2407_09848_gb300 import problems as pr
+from parity import assert_parity
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
@@ -51,8 +52,8 @@ def test_smooth_backward_matches_oracle(case, kind, k, level):
                                         None if start is None else dev(torch, start),
                                         dev(torch, gx))
         rb, rx0, rw = smooth_backward(A, b, start, spec, gx)
-        assert rel(gb.cpu().numpy(), rb) <= TOL
-        assert rel(gx0.cpu().numpy(), rx0) <= TOL
+        assert_parity(gb.cpu().numpy(), rb, TOL, "dL/db")
+        assert_parity(gx0.cpu().numpy(), rx0, TOL, "dL/dx0")
         if rw is not None:
             assert np.max(np.abs(gw - rw)) <= TOL * np.max(np.abs(rw))
         else:
@@ -75,7 +76,7 @@ def test_vcycle_backward_matches_oracle(case, k):
     r, gz = rng.uniform(-1, 1, (2, n))
     gr, gw = S.vcycle_backward(dev(torch, r), dev(torch, gz))
     rr, rw = vcycle_backward(ora, r, gz)
-    assert rel(gr.cpu().numpy(), rr) <= TOL
+    assert_parity(gr.cpu().numpy(), rr, TOL, "dL/dr")
     for l in range(nl - 1):
         assert np.max(np.abs(gw[l, :k] - rw[l])) <= TOL * np.max(np.abs(rw[l]))
         assert np.all(gw[l, k:] == 0)

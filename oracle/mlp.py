@@ -6,9 +6,12 @@ level to the k = 4 weights of Eq. polsmootheropt,
     h1 = relu(W1 f + b1)      (64)
     h2 = relu(W2 h1 + b2)     (64)
     o  = W3 h2 + b3           (4)
-    beta = beta_ref * exp(0.5 * tanh(o))
+    beta = beta_ref * exp(2 * tanh(o / 2))
 
-with beta_ref the optimal 4th-kind weights, so o = 0 reproduces them.  The
+with beta_ref the optimal 4th-kind weights, so o = 0 reproduces them; the
+factor exp(2 tanh(o/2)) has slope 1 at o = 0 and spans (e^-2, e^2), far wider
+than any weight of a safe polynomial needs, so training is not held at a
+bound of the parametrisation.  The
 parameter vector is [W1 (64x8 row-major), b1, W2 (64x64), b2, W3 (4x64), b3]:
 4996 numbers.  Adam is the textbook update with bias correction.
 """
@@ -40,8 +43,8 @@ def forward(theta, F, beta_ref):
     a2 = h1 @ P["W2"].T + P["b2"]
     h2 = np.maximum(a2, 0.0)
     o = h2 @ P["W3"].T + P["b3"]
-    t = np.tanh(o)
-    beta = np.asarray(beta_ref) * np.exp(0.5 * t)
+    t = np.tanh(0.5 * o)
+    beta = np.asarray(beta_ref) * np.exp(2.0 * t)
     return beta, (F, a1, h1, a2, h2, t, beta)
 
 
@@ -50,7 +53,7 @@ def backward(theta, cache, gbeta):
     counterpart in the paper)."""
     P = unpack(theta)
     F, a1, h1, a2, h2, t, beta = cache
-    go = gbeta * beta * 0.5 * (1.0 - t * t)          # d beta / d o
+    go = gbeta * beta * (1.0 - t * t)                # d beta / d o = beta (1 - t^2)
     gW3 = go.T @ h2
     gb3 = go.sum(axis=0)
     gh2 = go @ P["W3"]

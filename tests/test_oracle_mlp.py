@@ -1,5 +1,6 @@
-"""Pins for the oracle MLP (no GPU): backward by central differences, the
-identity at o = 0, and Adam's first step in closed form."""
+"""Pins for the oracle MLP (no GPU): a forward pass worked out by hand on small
+integer weights, backward by central differences, the identity at o = 0, and
+Adam's first step in closed form."""
 import numpy as np
 
 from oracle import mlp
@@ -23,6 +24,41 @@ def test_zero_output_layer_gives_reference_weights():
     beta, _ = mlp.forward(th, F, ref)
     assert np.allclose(beta, ref[None, :], atol=0, rtol=1e-15)
     del P
+
+
+def test_forward_by_hand():
+    """Two feature rows through weights that are zero except for a few small
+    integers; the hidden activations and the outputs o below were worked out by
+    hand (ReLU zeroes a1[1] of row 0 and a2[0] of row 1), and beta follows from
+    tanh(m/2) = (e^m - 1)/(e^m + 1) for integer m."""
+    W1, b1, W2, b2 = np.zeros((64, 8)), np.zeros(64), np.zeros((64, 64)), np.zeros(64)
+    W3, b3 = np.zeros((4, 64)), np.zeros(4)
+    W1[0, 0], W1[0, 1], b1[0] = 1, 1, -1       # row 0: 1 + 2 - 1 = 2
+    W1[1, 2], b1[1] = -1, 1                    # row 0: -3 + 1 = -2 -> 0
+    W1[2, 7], b1[2] = 2, 5                     # row 0: -2 + 5 = 3
+    W2[0, 0], W2[0, 2], b2[0] = 1, -1, 2       # row 0: 2 - 3 + 2 = 1
+    W2[1, 1], W2[1, 2], b2[1] = 7, 1, -1       # row 0: 0 + 3 - 1 = 2
+    W2[3, 0] = -1                              # row 0: -2 -> 0
+    W3[0, 0] = 1                               # o0 = h2[0]
+    W3[1, 1], W3[1, 0] = 1, -2                 # o1 = h2[1] - 2 h2[0]
+    W3[2, 1], b3[2] = -1, 1                    # o2 = 1 - h2[1]
+    W3[3, 3], b3[3] = 5, 3                     # o3 = 5 h2[3] + 3
+    th = np.concatenate([W1.ravel(), b1, W2.ravel(), b2, W3.ravel(), b3])
+    assert th.size == mlp.NPARAM
+    F = np.zeros((2, 8))
+    F[0, :] = [1, 2, 3, 0, 0, 0, 0, -1]
+    ref = np.array([1.0, 1.25, 1.5, 2.0])
+    beta, (Fc, a1, h1, a2, h2, t, _) = mlp.forward(th, F, ref)
+    # row 1 (all features 0): h1 = relu(b1) = (0, 1, 5); a2 = (-5 + 2, 7 + 5 - 1, 0, 0)
+    assert np.array_equal(h1[:, :4], [[2, 0, 3, 0], [0, 1, 5, 0]])
+    assert np.array_equal(h2[:, :4], [[1, 2, 0, 0], [0, 11, 0, 0]])
+    assert not h1[:, 4:].any() and not h2[:, 4:].any()
+    o = np.array([[1, 0, -1, 3], [0, 11, -10, 3]], dtype=np.float64)
+    fac = np.exp(2.0 * (np.exp(o) - 1.0) / (np.exp(o) + 1.0))
+    assert np.allclose(beta, ref * fac, rtol=1e-14, atol=0)
+    # o = 0 leaves the weight unchanged; o = 1 multiplies it by exp(2 (e-1)/(e+1))
+    assert beta[0, 1] == 1.25 and beta[1, 0] == 1.0
+    assert abs(beta[0, 0] - np.exp(2 * (np.e - 1) / (np.e + 1))) <= 1e-15
 
 
 def test_backward_central_differences():

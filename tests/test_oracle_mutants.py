@@ -183,6 +183,7 @@ def generator_pins():
 
 
 def mlp_pins():
+    TM.test_forward_by_hand()
     TM.test_backward_central_differences()
     TM.test_adam_first_step_closed_form()
 
@@ -331,7 +332,11 @@ MUTANTS = [
     ("gen_diag_drops_face", GE + "_from_faces", "+ fz[:-1, :, :] + fz[1:, :, :]", "+ fz[1:, :, :]",
      generator_pins),
     # MLP of the learned weights
-    ("mlp_output_scale", ML + "forward", "np.exp(0.5 * t)", "np.exp(t)", mlp_pins),
+    ("mlp_output_scale", ML + "forward", "np.exp(2.0 * t)", "np.exp(t)", mlp_pins),
+    ("mlp_tanh_argument", ML + "forward", "t = np.tanh(0.5 * o)", "t = np.tanh(o)", mlp_pins),
+    ("mlp_layer1_bias", ML + "forward", 'a1 = F @ P["W1"].T + P["b1"]', 'a1 = F @ P["W1"].T', mlp_pins),
+    ("mlp_layer2_transposed", ML + "forward", 'a2 = h1 @ P["W2"].T + P["b2"]',
+     'a2 = h1 @ P["W2"] + P["b2"]', mlp_pins),
     ("mlp_hidden_relu", ML + "forward", "h2 = np.maximum(a2, 0.0)", "h2 = a2", mlp_pins),
     ("mlp_layer2_gradient", ML + "backward", "gW2 = ga2.T @ h1", "gW2 = ga2.T @ a1", mlp_pins),
     ("adam_second_moment", ML + "adam", "v = b2 * v + (1 - b2) * grad * grad",

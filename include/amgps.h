@@ -219,7 +219,7 @@ amgps_status amgps_vcycle_loss_grad(amgps_ctx* ctx, const double* E0_dev, int m,
 amgps_status amgps_error_cycles(amgps_ctx* ctx, double* E_dev, int m, int cycles);
 
 /* The weight-predicting MLP of the learned smoother (not in the paper):
- * 8 level features -> 64 -> 64 -> 4, ReLU, beta = beta_ref exp(0.5 tanh(o)).
+ * 8 level features -> 64 -> 64 -> 4, ReLU, beta = beta_ref exp(2 tanh(o / 2)).
  * Stateless FP32 kernels on caller-owned device buffers, enqueued on `stream`
  * (cudaStream_t, may be NULL); errors through amgps_last_error(NULL).
  * params: 4996 floats [W1 (64x8 row-major), b1 (64), W2 (64x64), b2, W3 (4x64),

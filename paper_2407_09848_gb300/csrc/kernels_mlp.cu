@@ -1,7 +1,7 @@
 // The weight-predicting MLP of the learned smoother (no counterpart in the
 // paper): 8 level features -> 64 -> 64 -> 4 weights of Eq. polsmootheropt,
 //   h1 = relu(W1 f + b1), h2 = relu(W2 h1 + b2), o = W3 h2 + b3,
-//   beta = beta_ref * exp(0.5 tanh(o)),
+//   beta = beta_ref * exp(2 tanh(o / 2)),
 // with forward, backward and Adam kernels in FP32.  Parameters are one vector
 // [W1 (64x8), b1, W2 (64x64), b2, W3 (4x64), b3] (4996 floats).  Each sum over
 // the batch is taken in sample order by one thread, so results repeat exactly.
@@ -13,7 +13,7 @@ namespace {
 constexpr int NF = 8, NH = 64, NO = 4;
 constexpr int OW1 = 0, OB1 = OW1 + NH * NF, OW2 = OB1 + NH, OB2 = OW2 + NH * NH,
               OW3 = OB2 + NH, OB3 = OW3 + NO * NH, NPARAM = OB3 + NO;
-constexpr int NACT = NH + NH + NO;  // per sample: a1, a2, tanh(o)
+constexpr int NACT = NH + NH + NO;  // per sample: a1, a2, tanh(o / 2)
 static_assert(NPARAM == 4996, "parameter layout");
 
 // one block (64 threads) per sample
@@ -40,9 +40,9 @@ __global__ void __launch_bounds__(NH) k_mlp_forward(const float* __restrict__ th
   if (j < NO) {
     float o = th[OB3 + j];
     for (int i = 0; i < NH; ++i) o = fmaf(th[OW3 + j * NH + i], h2[i], o);
-    const float t = tanhf(o);
+    const float t = tanhf(0.5f * o);
     acts[b * NACT + 2 * NH + j] = t;
-    beta[b * NO + j] = ref[j] * expf(0.5f * t);
+    beta[b * NO + j] = ref[j] * expf(2.f * t);
   }
 }
 
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(NH) k_mlp_deltas(const float* __restrict__ th,
   __shared__ float go[NO], ga2[NH];
   if (j < NO) {
     const float t = acts[b * NACT + 2 * NH + j];
-    go[j] = gbeta[b * NO + j] * beta[b * NO + j] * 0.5f * (1.f - t * t);
+    go[j] = gbeta[b * NO + j] * beta[b * NO + j] * (1.f - t * t);  // d beta / d o
     work[b * NACT + 2 * NH + j] = go[j];
   }
   __syncthreads();

@@ -22,6 +22,9 @@ Contents (each function cites the paper passage it restates):
 * :mod:`oracle.adjoint`  - reverse-mode derivatives of the smoother and of the
   V-cycle error-reduction loss.
 * :mod:`oracle.mlp`      - FP64 reference of the weight-predicting MLP.
+* :mod:`oracle.omp`      - the smoother, V-cycle and PCG loops restated in
+  plain C with OpenMP row loops (``oracle/c/amg_omp.c``), for timing the
+  oracle on every host core; checked against the numpy oracle.
 
 Parity status: every function is pinned by tests against printed constants,
 closed forms or brute force, except where its docstring says "parity unpinned".

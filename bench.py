@@ -7,20 +7,23 @@ optimised 4th-kind Chebyshev smoother of degree 4 (Eq. polsmootheropt) before
 and after the coarse correction, dense Cholesky on the coarsest level, FP64.
 One step = one full PCG solve from x0 = 0 with the inputs resident on the GPU.
 
-Printed (one JSON line on rank 0): time to solution (ms, lower is better), the
-roofline of the dominant kernel (the fused smoother step on the finest level:
-algorithmic bytes / CUDA-event time against the measured HBM copy peak), the
-end-to-end time through the host-buffer C-ABI call, the oracle CPU baseline on
-a bounded sample, clocks during the timed region and the kernel launch count.
+Printed (one JSON line on rank 0): time to solution (ms, lower is better,
+timed with no per-kernel events), the roofline of the dominant kernel (the
+fused smoother step on the finest level, from a separate pass of the same
+solves with CUDA events around each of its launches), the end-to-end time
+through the host-buffer C-ABI call, the CPU oracle baseline, clocks during the
+timed region and the kernel launch count.
 
---impl reference times the FP64 CPU oracle instead (the reference of this
-build), each step one PCG iteration of the same solve, scaled by the oracle's
-iteration count to the same metric.
+CPU baseline and reference arm: the all-core C build of the oracle loops
+(oracle/c/amg_omp.c, OpenMP on every host core) solving the same system.
+--impl reference times it as the reference of this build, each step one whole
+PCG solve of the same workload.
 """
 import os
 
-# the CPU oracle is timed single-threaded: pin BLAS pools before numpy loads
-for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+# numpy's BLAS pools stay single-threaded (the C oracle build sets its own
+# OpenMP thread count through its library call, not through this variable)
+for _v in ("OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
 import argparse
@@ -45,7 +48,7 @@ STEP_SOURCES = [os.path.join(ROOT, "paper_2407_09848_gb300", "csrc", f)
 LEARNED = os.path.join(ROOT, "paper_2407_09848_gb300", "data", "learned_weights_lognormal64.npz")
 
 
-def parse():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -60,7 +63,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the mixed-precision (192^3) and learned+mixed (256^3) comparisons")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def workload_name(a):
@@ -91,16 +94,18 @@ def step_source_hash():
     return h.hexdigest()
 
 
-def oracle_threads():
-    """Threads the CPU oracle's BLAS calls may use (1 unless the environment
-    set the pools before this module pinned them)."""
-    vals = []
-    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
-        try:
-            vals.append(int(os.environ.get(v, "1")))
-        except ValueError:
-            pass
-    return max(vals) if vals else 1
+def host_info():
+    """Logical CPUs and CPU model of the host the CPU oracle runs on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
 
 
 def measured_peak():
@@ -217,9 +222,7 @@ def configure(S, H, kind, degree, torch):
         S.set_smoother(-1, kind, degree)
 
 
-def time_oracle_iteration(H, b, kind, degree):
-    """Seconds of one oracle PCG iteration (V-cycle + SpMV + CG updates)."""
-    from oracle.amg import OracleAMG
+def oracle_specs(H, kind, degree):
     from oracle.smoother import SmootherSpec, power_lambda
     from paper_2407_09848_gb300 import problems as pr
     specs = []
@@ -229,10 +232,55 @@ def time_oracle_iteration(H, b, kind, degree):
             specs.append(SmootherSpec(kind, degree, rho=1.1 * lam))
         else:
             specs.append(SmootherSpec(kind, degree))
-    ora = OracleAMG(H.A, H.P, specs)
-    t = time.perf_counter()
-    ora.pcg(b, rtol=1e-300, maxit=1)
-    return time.perf_counter() - t, ora
+    return specs
+
+
+def omp_oracle(A, P, specs):
+    """The all-core C build of the oracle loops on this hierarchy."""
+    from oracle import omp
+    return omp.OmpAMG(A, P, specs)
+
+
+def time_omp_solves(ora, b, rtol, count, warmup=1, budget_s=30.0):
+    """Wall seconds of whole PCG solves by the C oracle: `warmup` untimed, then
+    up to `count` timed ones (fewer once `budget_s` of timed work is spent,
+    at least one).  Returns (times, iterations, relres)."""
+    for _ in range(warmup):
+        ora.pcg(b, rtol=rtol, maxit=1000)
+    times, it, rel = [], 0, 0.0
+    while len(times) < count:
+        t = time.perf_counter()
+        _, it, rel, _ = ora.pcg(b, rtol=rtol, maxit=1000)
+        times.append(time.perf_counter() - t)
+        if sum(times) >= budget_s:
+            break
+    return times, it, rel
+
+
+def cpu_oracle_baseline(A, P, specs, b, rtol, label, count=3, warmup=1):
+    """CPU baseline: median of whole solves by the all-core C oracle build,
+    plus its single-thread time for one PCG iteration scaled by the iteration
+    count (stated as extrapolated)."""
+    from oracle import omp
+    ora = omp_oracle(A, P, specs)
+    threads = omp.threads()
+    times, it, rel = time_omp_solves(ora, b, rtol, count=count, warmup=warmup)
+    omp.set_threads(1)
+    try:
+        t = time.perf_counter()
+        ora.pcg(b, rtol=1e-300, maxit=1)  # one V-cycle, one product with A_0, the CG updates
+        t1 = time.perf_counter() - t
+    finally:
+        omp.set_threads(threads)
+    ora.close()
+    return {"value": 1e3 * statistics.median(times), "unit": "ms", "cores": threads,
+            "kind": "oracle",
+            "sample": f"{len(times)} whole PCG solves of {label} by the all-core C build of the "
+                      f"oracle loops (OpenMP, {threads} threads), median",
+            "iterations": it, "relres": rel, "host": host_info(),
+            "single_thread": {"value": 1e3 * t1 * it, "unit": "ms", "cores": 1,
+                              "extrapolated_from": f"one PCG iteration ({1e3 * t1:.1f} ms) x {it} "
+                                                   f"iterations"}}
 
 
 def timed_solve(S, bd, x, rtol, torch, reps=2):
@@ -251,10 +299,47 @@ def timed_solve(S, bd, x, rtol, torch, reps=2):
     return it, best, rel
 
 
-def run_mixed_c2(a, torch):
-    """192^3 variable coefficient (k = exp(g), GRF sigma 1, ell 8): FP64 vs
-    FP32 / BF16 values on the smoother and transfer path (CHEB4_OPT k = 4)."""
+def step_roofline_of_solve(S, bd, x, rtol, torch, workload, prec):
+    """HBM roofline of the level-0 step over one profiled solve (CUDA events
+    around each level-0 step launch)."""
+    from paper_2407_09848_gb300.amgps import PROF_STEP
+    S.profile(True)
+    S.profile_read(PROF_STEP, reset=True)
+    S.pcg(bd, x, rtol=rtol, maxit=2000)
+    torch.cuda.synchronize()
+    S.profile(False)
+    n_step, ms_step, by_step = S.profile_read(PROF_STEP, reset=True)
+    return step_hbm_roofline(n_step, ms_step, by_step, committed_traffic(workload, prec))
+
+
+def run_mixed_c1(a, torch, H, b):
+    """256^3 Poisson, CHEB4_OPT k = 4: FP32 and BF16 matrix values on the
+    smoother and transfer path (FP32 vectors and accumulation, FP64 PCG and
+    coarse solve), with the level-0 step's HBM roofline."""
     import numpy as np
+    from paper_2407_09848_gb300.amgps import Solver
+    bd = torch.from_numpy(b).cuda()
+    out = {"workload": f"poisson{a.grid}^3, CHEB4_OPT k4, rtol {a.rtol}"}
+    for prec in ("f32", "bf16"):
+        S = Solver().load(H.A, H.P, prec=prec)
+        S.set_smoother(-1, "cheb4_opt", 4)
+        x = torch.empty_like(bd)
+        it, ms, rel = timed_solve(S, bd, x, a.rtol, torch)
+        true = float(np.linalg.norm(b - H.levels[0].A @ x.cpu().numpy()) / np.linalg.norm(b))
+        wl = f"poisson{a.grid}^3_cheb4_opt_k4_{prec}"
+        out[prec] = {"iterations": it, "ms": round(ms, 3), "relres": rel, "true_relres": true,
+                     "roofline": step_roofline_of_solve(S, bd, x, a.rtol, torch, wl, prec)}
+        S.close()
+    return out
+
+
+def run_mixed_c2(a, torch, cpu=True):
+    """192^3 variable coefficient (k = exp(g), GRF sigma 1, ell 8): FP64 vs
+    FP32 / BF16 values on the smoother and transfer path (CHEB4_OPT k = 4),
+    each with the level-0 step's HBM roofline, and the all-core C oracle's
+    FP64 solve of the same system."""
+    import numpy as np
+    from oracle.smoother import SmootherSpec
     from paper_2407_09848_gb300 import problems as pr
     from paper_2407_09848_gb300.amgps import Solver
     H = pr.build_hierarchy(pr.varcoef(192, 1.0, 8.0, seed=0), coarse_max=512)
@@ -270,8 +355,15 @@ def run_mixed_c2(a, torch):
         if ref is None:
             ref = xs
         out[prec] = {"iterations": it, "ms": round(ms, 3), "relres": rel, "true_relres": true,
-                     "solution_rel_diff_vs_f64": float(np.linalg.norm(xs - ref) / np.linalg.norm(ref))}
+                     "solution_rel_diff_vs_f64": float(np.linalg.norm(xs - ref) / np.linalg.norm(ref)),
+                     "roofline": step_roofline_of_solve(S, bd, x, a.rtol, torch,
+                                                        "varcoef192^3_cheb4_opt_k4", prec)}
         S.close()
+    if cpu:
+        out["cpu_oracle_f64"] = cpu_oracle_baseline(H.A, H.P, [SmootherSpec("cheb4_opt", 4)] *
+                                                    (H.n_levels - 1), b, a.rtol,
+                                                    "the 192^3 variable-coefficient system",
+                                                    count=1, warmup=0)
     return {"workload": "varcoef192^3 sigma1 ell8, CHEB4_OPT k4, rtol 1e-8", **out}
 
 
@@ -328,11 +420,13 @@ def run_sa_c1(a, torch):
     return out
 
 
-def run_learned_c4(a, torch):
+def run_learned_c4(a, torch, cpu=True):
     """256^3 log-normal (sigma 2, ell 16) and anisotropic (eps 1e-3 in z):
     plain FP64 with the optimal 4th-kind weights vs learned weights with
-    BF16 / FP32 values (FP64 PCG and coarse solve)."""
+    BF16 / FP32 values (FP64 PCG and coarse solve), and the all-core C
+    oracle's FP64 solve with the optimal weights."""
     import numpy as np
+    from oracle.smoother import SmootherSpec
     from paper_2407_09848_gb300 import learn
     from paper_2407_09848_gb300 import problems as pr
     from paper_2407_09848_gb300.amgps import Solver
@@ -365,44 +459,98 @@ def run_learned_c4(a, torch):
             row[f"{prec}_learned"] = {"iterations": it, "ms": round(ms, 3), "relres": rel}
             S.close()
         row["speedup_bf16_learned_vs_f64_opt"] = round(row["f64_opt"]["ms"] / row["bf16_learned"]["ms"], 3)
+        if cpu:
+            row["cpu_oracle_f64_opt"] = cpu_oracle_baseline(
+                H.A, H.P, [SmootherSpec("cheb4_opt", 4)] * (H.n_levels - 1), b, a.rtol,
+                f"the 256^3 {name} system", count=1, warmup=0)
         res[name] = row
     return res
+
+
+def workload_config(a, H):
+    """The workload both arms run (identical keys and values in both lines)."""
+    return {"workload": workload_name(a), "grid": a.grid, "n": int(H.levels[0].A.shape[0]),
+            "levels": H.n_levels, "nnz": int(H.levels[0].A.nnz), "kind": a.kind,
+            "degree": a.degree, "prec": a.prec, "rtol": a.rtol,
+            "l2": "inputs larger than L2 (finest matrix 0.94 GB, 129 MB L2)",
+            "parallelism": "replicas" if dist_env()[1] > 1 else "none"}
 
 
 def run_reference(a):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    from oracle import omp
     H, b = build_problem(a)
-    its = golden_iterations(a.grid, a.kind, a.degree)
-    from oracle.amg import OracleAMG  # noqa: F401  (import cost outside the timing)
-    if its is None:
-        print(json.dumps({"impl": "reference", "unavailable":
-                          f"no stored oracle iteration count for {workload_name(a)}"}))
-        return 0
-    _, ora = time_oracle_iteration(H, b, a.kind, a.degree)
+    ora = omp_oracle(H.A, H.P, oracle_specs(H, a.kind, a.degree))
+    threads = omp.threads()
+    for _ in range(a.warmup):
+        ora.pcg(b, rtol=a.rtol, maxit=1000)
     times = []
-    for i in range(a.warmup + a.steps):
+    for _ in range(a.steps):
         t = time.perf_counter()
-        ora.pcg(b, rtol=1e-300, maxit=1)
-        dt = time.perf_counter() - t
-        if i >= a.warmup:
-            times.append(dt)
-    per_iter = statistics.mean(times)
-    value_ms = per_iter * its * 1e3
-    sample = (f"one PCG iteration (V-cycle + SpMV + updates) of the {workload_name(a)} solve per step, "
-              f"mean of {a.steps}, x {its} oracle iterations")
+        _, its, rel, st = ora.pcg(b, rtol=a.rtol, maxit=1000)
+        times.append(time.perf_counter() - t)
+    ora.close()
+    value_ms = 1e3 * statistics.mean(times)
+    sample = (f"each step one whole PCG solve of {workload_name(a)} by the all-core C build of the "
+              f"oracle loops (OpenMP, {threads} threads); value = mean over {a.steps} steps")
     out = {"impl": "reference", "metric": METRIC, "value": value_ms, "unit": "ms",
            "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": value_ms,
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic",
-           "config": {"workload": workload_name(a), "grid": a.grid, "kind": a.kind,
-                      "degree": a.degree, "rtol": a.rtol, "iterations": its},
-           "cpu_baseline": {"value": value_ms, "unit": "ms", "cores": oracle_threads(), "kind": "oracle",
-                            "sample": sample},
+           "data": "synthetic", "config": workload_config(a, H),
+           "result": {"iterations": its, "relres": rel, "converged": st == 0,
+                      "step_ms_min": 1e3 * min(times), "step_ms_max": 1e3 * max(times)},
+           "cpu_baseline": {"value": value_ms, "unit": "ms", "cores": threads, "kind": "oracle",
+                            "sample": sample, "host": host_info()},
            "e2e": {"value": value_ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
+
+
+def profiled_pass(S, bd, x, a, torch, smi):
+    """The same solves again with CUDA events around each level-0 step launch
+    (class 0), each level-0 residual + restriction (1), each PCG SpMV (2) and
+    the levels below 0 (4).  Returns per-class (launches, ms, bytes) summed over
+    the pass, its solve count and the clock summary sampled during it."""
+    from paper_2407_09848_gb300.amgps import PROF_COARSE, PROF_RESTRICT, PROF_SPMV, PROF_STEP
+    classes = (PROF_STEP, PROF_RESTRICT, PROF_SPMV, PROF_COARSE)
+    S.profile(True)
+    for c in classes:
+        S.profile_read(c, reset=True)
+    torch.cuda.synchronize()
+    with ClockSampler(smi) as clk:
+        for _ in range(a.steps):
+            S.pcg(bd, x, rtol=a.rtol)
+        torch.cuda.synchronize()
+    S.profile(False)
+    out = {c: S.profile_read(c, reset=True) for c in classes}
+    return out, a.steps, clk.summary()
+
+
+def step_hbm_roofline(n_step, ms_step, by_step, traffic=None, kernel=None):
+    peak, peak_src = measured_peak()
+    achieved = (by_step / 1e9) / (ms_step / 1e3) if ms_step > 0 else None
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved else None, "traffic": traffic,
+            "kernel": kernel or "fused smoother step on level 0 (k_step_tma + leftover k_step)",
+            "launches": n_step, "avg_launch_us": 1e3 * ms_step / max(n_step, 1),
+            "bytes_per_launch": by_step / max(n_step, 1), "peak_source": peak_src}
+
+
+def committed_traffic(workload, prec):
+    """ncu DRAM bytes per launch of the level-0 step from the committed capture,
+    when it was taken on the current sources of the step kernels."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    with open(TRAFFIC_FILE) as f:
+        tr = json.load(f)
+    entries = tr if isinstance(tr, list) else [tr]
+    for e in entries:
+        if (e.get("source_sha256") == step_source_hash() and e.get("workload") == workload
+                and e.get("prec", "f64") == prec):
+            return e.get("dram_bytes_per_launch")
+    return None
 
 
 def run_ours(a):
@@ -417,7 +565,7 @@ def run_ours(a):
         pg = dist
     from paper_2407_09848_gb300 import build as bld
     bld.build()
-    from paper_2407_09848_gb300.amgps import (PROF_RESTRICT, PROF_SPMV, PROF_STEP, Solver)
+    from paper_2407_09848_gb300.amgps import PROF_COARSE, PROF_RESTRICT, PROF_SPMV, PROF_STEP, Solver
 
     H, b = build_problem(a)
     n = H.levels[0].A.shape[0]
@@ -429,10 +577,10 @@ def run_ours(a):
         its, rel = S.pcg(bd, x, rtol=a.rtol)
     torch.cuda.synchronize()
 
-    # ---- timed region: K solves, CUDA events on the caller's stream ----
-    S.profile(True)
-    for c in (PROF_STEP, PROF_RESTRICT, PROF_SPMV, 3, 4):
-        S.profile_read(c, reset=True)
+    # ---- timed region: K solves, CUDA events on the caller's stream, no
+    # per-kernel events inside ----
+    S.profile(False)
+    S.profile_read(3, reset=True)
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     smi = gpu_smi_id(torch, local)
@@ -448,32 +596,19 @@ def run_ours(a):
     if pg:
         pg.barrier()
     total_ms = ev0.elapsed_time(ev1)
-    S.profile(False)
-    n_step, ms_step, by_step = S.profile_read(PROF_STEP, reset=True)
-    n_rr, ms_rr, _ = S.profile_read(PROF_RESTRICT, reset=True)
-    n_sp, ms_sp, _ = S.profile_read(PROF_SPMV, reset=True)
-    _, ms_coarse, _ = S.profile_read(4, reset=True)
     launches, _, _ = S.profile_read(3, reset=True)
     ms_per = max_over_ranks(total_ms / a.steps, pg)
     true_res = float(np.linalg.norm(b - H.levels[0].A @ x.cpu().numpy()) / np.linalg.norm(b))
+    clk = clk.summary()
 
-    # ---- roofline of the fused smoother step on the finest level ----
-    peak, peak_src = measured_peak()
-    achieved = (by_step / 1e9) / (ms_step / 1e3) if ms_step > 0 else None
-    traffic = None
-    if os.path.exists(TRAFFIC_FILE):
-        with open(TRAFFIC_FILE) as f:
-            tr = json.load(f)
-        if tr.get("source_sha256") == step_source_hash() and tr.get("workload") == workload_name(a):
-            traffic = tr.get("dram_bytes_per_launch")
-    hbm = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-           "frac": achieved / peak if achieved else None, "traffic": traffic,
-           "kernel": "fused smoother step on level 0 (k_step_tma + leftover k_step)",
-           "launches": n_step, "avg_launch_us": 1e3 * ms_step / max(n_step, 1),
-           "bytes_per_launch": by_step / max(n_step, 1), "peak_source": peak_src,
-           "share_of_step_time": ms_step / total_ms if total_ms else None}
+    # ---- per-kernel split and roofline: a separate pass of the same solves ----
+    prof, nprof, clk_prof = profiled_pass(S, bd, x, a, torch, smi)
+    n_step, ms_step, by_step = prof[PROF_STEP]
+    ms_rr, ms_sp, ms_coarse = prof[PROF_RESTRICT][1], prof[PROF_SPMV][1], prof[PROF_COARSE][1]
+    traffic = committed_traffic(workload_name(a), a.prec)
+    hbm = step_hbm_roofline(n_step, ms_step, by_step, traffic)
+    hbm["share_of_solve_time"] = (ms_step / nprof) / ms_per if ms_per else None
     roof = hbm
-    clk = clk.summary() if hasattr(clk, "summary") else clk
     if a.prec == "f64" and a.kind in ("cheb4", "cheb4_opt", "weights") and n_step:
         # FP64 path: the step is bound by the FP64 pipe (ncu: ~85% busy vs
         # DRAM ~60%).  The 4th-kind steps run on the row-scaled matrix M^{-1}A
@@ -484,18 +619,23 @@ def run_ours(a):
         # first step after the initial one, and the post-smoothing initial
         # step, which has no c1 term): 2 nnz + 5 n per launch for k >= 2,
         # 2 nnz + 4 n for k = 1.  Peak: 304 FP64 FMA thread-instructions per
-        # clock (152 SMs x 2, ncu peak_sustained) x 2 flops x the SM clock.
+        # clock (152 SMs x 2, ncu peak_sustained) x 2 flops x the SM clock
+        # sampled during the profiled pass.
         k = a.degree
         nnz0 = float(H.levels[0].A.nnz)
         fl = 2 * nnz0 + (5 * n if k >= 2 else 4 * n)
-        mhz = clk.get("sm_mhz") or 2070.0
+        mhz = clk_prof.get("sm_mhz") or 2070.0
         fpeak = 304 * 2 * mhz * 1e6 / 1e12
         fach = fl / (1e-3 * ms_step / n_step) / 1e12
         roof = {"bound": "alu", "achieved": fach, "peak": fpeak, "unit": "TFLOP/s",
                 "frac": fach / fpeak, "traffic": traffic, "kernel": hbm["kernel"],
-                "flops_per_launch": fl, "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2 flops x sampled SM clock",
+                "flops_per_launch": fl,
+                "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2 flops x sampled SM clock",
                 "launches": n_step, "avg_launch_us": hbm["avg_launch_us"],
-                "share_of_step_time": hbm["share_of_step_time"], "hbm": hbm}
+                "share_of_solve_time": hbm["share_of_solve_time"], "hbm": hbm}
+    roof["measured_in"] = (f"a pass of {nprof} solves after the timed region, CUDA events around "
+                           f"each level-0 step launch on the library stream")
+    roof["clocks"] = clk_prof
 
     # ---- end to end through the host-buffer C-ABI call ----
     bh = torch.from_numpy(b.copy()).pin_memory()
@@ -541,39 +681,37 @@ def run_ours(a):
         S.set_flexible("cg")
         sweep = {"smoothers": sweep, "outer_cg_forms": outer}
 
-    # ---- comparisons: mixed precision (192^3) and learned + mixed (256^3) ----
+    # ---- comparisons: mixed precision (256^3 Poisson, 192^3 variable
+    # coefficient), learned + mixed (256^3), smoothed aggregation ----
     extras = None
     if not a.no_extras and rank == 0:
         S.close()
-        extras = {"mixed_c2": run_mixed_c2(a, torch), "learned_c4": run_learned_c4(a, torch),
+        extras = {"mixed_c1": run_mixed_c1(a, torch, H, b),
+                  "mixed_c2": run_mixed_c2(a, torch, cpu=not a.no_cpu),
+                  "learned_c4": run_learned_c4(a, torch, cpu=not a.no_cpu),
                   "smoothed_aggregation": run_sa_c1(a, torch)}
 
-    # ---- CPU baseline: the oracle on a bounded sample ----
+    # ---- CPU baseline: the all-core C oracle build on the same solve ----
     cpu = None
     if not a.no_cpu and rank == 0:
-        t_iter, _ = time_oracle_iteration(H, b, a.kind, a.degree)
-        cpu = {"value": t_iter * its * 1e3, "unit": "ms", "cores": oracle_threads(), "kind": "oracle",
-               "sample": f"one oracle PCG iteration (V-cycle + SpMV + updates) of the same "
-                         f"{workload_name(a)} solve, {t_iter:.2f} s, x {its} iterations"}
+        cpu = cpu_oracle_baseline(H.A, H.P, oracle_specs(H, a.kind, a.degree), b, a.rtol,
+                                  workload_name(a))
 
     out = {"metric": METRIC, "value": ms_per, "unit": "ms", "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms_per, "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": a.prec, "data": "synthetic",
-           "config": {"workload": workload_name(a), "grid": a.grid, "n": n,
-                      "levels": H.n_levels, "nnz": int(H.levels[0].A.nnz), "kind": a.kind,
-                      "degree": a.degree, "rtol": a.rtol, "iterations": its, "relres": rel,
-                      "true_relres": true_res,
-                      "oracle_iterations": golden_iterations(a.grid, a.kind, a.degree),
-                      "l2": "inputs larger than L2 (finest matrix 0.94 GB, 129 MB L2)",
-                      "parallelism": "replicas" if world > 1 else "single GPU"},
+           "config": workload_config(a, H),
+           "result": {"iterations": its, "relres": rel, "true_relres": true_res,
+                      "oracle_iterations": golden_iterations(a.grid, a.kind, a.degree)},
            "roofline": roof,
            "cpu_baseline": cpu,
            "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 8 * n,
                    "d2h_bytes_per_step": 8 * n},
            "gpu_launches": launches,
            "clocks": clk,
-           "kernel_ms": {"k_step_level0": ms_step / a.steps, "k_resid_restrict_level0": ms_rr / a.steps,
-                         "k_spmv_dot": ms_sp / a.steps, "coarse_levels": ms_coarse / a.steps},
+           "kernel_ms": {"k_step_level0": ms_step / nprof, "k_resid_restrict_level0": ms_rr / nprof,
+                         "k_spmv_dot": ms_sp / nprof, "coarse_levels": ms_coarse / nprof,
+                         "measured_in": "the profiled pass (per solve)"},
            "sweep": sweep,
            "comparisons": extras}
     if rank == 0:
@@ -584,7 +722,7 @@ def run_ours(a):
 
 
 def main():
-    a = parse()
+    a = parse_args()
     if a.impl == "reference":
         return run_reference(a)
     return run_ours(a)

@@ -77,8 +77,9 @@ def test_reference_arm_json_line():
                 "cpu_baseline", "e2e"):
         assert key in r, key
     assert r["impl"] == "reference" and r["value"] > 0 and r["higher_is_better"] is False
-    assert r["cpu_baseline"]["cores"] == 1      # BLAS pools pinned to one thread
-    assert r["config"]["iterations"] == 11 and r["cpu_baseline"]["kind"] == "oracle"
+    # the all-core C oracle build: every host core, whole solves per step
+    assert r["cpu_baseline"]["cores"] >= 1 and r["cpu_baseline"]["kind"] == "oracle"
+    assert r["result"]["iterations"] == 11 and r["result"]["converged"]
     assert r["e2e"]["h2d_bytes_per_step"] == 0 and r["e2e"]["value"] == r["value"]
 
 
@@ -99,19 +100,31 @@ def test_clock_summary_parses_nvidia_smi_lines():
     assert c.summary()["samples"] == 0 and c.summary()["sm_mhz"] is None
 
 
-def test_oracle_threads_reports_the_pools():
+def test_cpu_baseline_times_whole_solves_of_the_c_oracle():
     sys.path.insert(0, ROOT)
     import bench
-    old = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS",
-                                          "MKL_NUM_THREADS")}
-    try:
-        os.environ.update(OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
-        assert bench.oracle_threads() == 1
-        os.environ["OMP_NUM_THREADS"] = "4"
-        assert bench.oracle_threads() == 4
-    finally:
-        for k, v in old.items():
-            if v is None:
-                os.environ.pop(k, None)
-            else:
-                os.environ[k] = v
+    from oracle import omp
+    from oracle.amg import OracleAMG
+    from paper_2407_09848_gb300 import problems as pr
+    H = pr.build_hierarchy(pr.poisson(16), coarse_max=64)
+    b = pr.rhs_uniform(H.A[0].shape[0], seed=0)
+    specs = bench.oracle_specs(H, "cheb4_opt", 4)
+    cb = bench.cpu_oracle_baseline(H.A, H.P, specs, b, 1e-8, "16^3", count=2, warmup=0)
+    _, it, _, _ = OracleAMG(H.A, H.P, specs).pcg(b, rtol=1e-8)
+    assert cb["kind"] == "oracle" and cb["cores"] == omp.threads() and cb["unit"] == "ms"
+    assert cb["iterations"] == it and cb["value"] > 0 and cb["host"]["nproc"] == os.cpu_count()
+    assert cb["single_thread"]["cores"] == 1 and "extrapolated_from" in cb["single_thread"]
+    assert omp.threads() == cb["cores"]  # the single-thread sample restores the pool
+
+
+def test_reference_arm_line_has_the_workload_config(capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+    import json
+    args = bench.parse_args(["--impl", "reference", "--grid", "16", "--steps", "2", "--warmup", "1"])
+    assert bench.run_reference(args) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    H, _ = bench.build_problem(args)
+    assert line["impl"] == "reference" and line["config"] == bench.workload_config(args, H)
+    assert line["steps"] == 2 and line["value"] == line["ms_per_step"] > 0
+    assert line["result"]["converged"] and line["e2e"]["h2d_bytes_per_step"] == 0

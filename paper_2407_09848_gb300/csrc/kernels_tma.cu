@@ -19,9 +19,17 @@
 // four 480-row stages in flight (the FP64-bound consumers then never wait for
 // a copy), for FP32 vectors two CTAs per SM of 16 consumers on 1024-row tiles.
 //
+// Rows of the 7-point pattern (seven sorted offsets, the row itself in the
+// middle) take a variant with the width fixed at compile time: exactly seven
+// multiply-adds per row with no guarded eighth one (on GB300's narrow FP64
+// pipe a predicated-off DFMA still costs an issue slot), and the centre entry
+// multiplies the z_j value the row already loaded for its c1 term.
+//
 // Every wait is bounded (kWaitSpins polls).  A wait that gives up sets the
 // solver's error slot and makes all warps leave their loops; the producer
 // still waits (bounded) for the copies it issued before it exits.
+#include <type_traits>
+
 #include "kernels_common.cuh"
 
 namespace amgps {
@@ -89,7 +97,9 @@ __host__ __device__ constexpr int tma_warps() {
   return TmaShape<XT>::kGroups * TmaShape<XT>::kConsumers;
 }
 
-template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN>
+// W = 0: up to kTmaMaxW entries per row (p.w at run time); W > 0: exactly W,
+// with entry W / 2 the row itself (checked by the launcher)
+template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN, int W>
 __global__ void __launch_bounds__((tma_warps<XT>() + 1) * 32, TmaShape<XT>::kCtasPerSm)
     k_step_tma(const StepArgs<VT, XT> a, const TmaPlan p, const TmaTile* __restrict__ tiles,
                int ntiles, const int32_t* __restrict__ gen, int64_t ngen, double* err) {
@@ -196,11 +206,20 @@ __global__ void __launch_bounds__((tma_warps<XT>() + 1) * 32, TmaShape<XT>::kCta
       const XT di = step_needs_dinv<FAM>() ? sv[2 * p.rows + it_row] : XT(0);
       const XT zo = ZOWN ? sw[p.d0 + it_row] : XT(0);
       XT acc = step_init<FAM, F::kResidual>(rin, di);
+      if constexpr (W > 0) {
 #pragma unroll
-      for (int k = 0; k < kTmaMaxW; ++k) {
-        if (k < p.w) {
+        for (int k = 0; k < W; ++k) {
           const XT av = widen<XT>(svals[k * kSlice]);
-          acc = fma(F::kSign > 0 ? av : -av, sw[p.d[k] + it_row], acc);
+          const XT uk = (ZOWN && k == W / 2) ? zo : sw[p.d[k] + it_row];
+          acc = fma(F::kSign > 0 ? av : -av, uk, acc);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < kTmaMaxW; ++k) {
+          if (k < p.w) {
+            const XT av = widen<XT>(svals[k * kSlice]);
+            acc = fma(F::kSign > 0 ? av : -av, sw[p.d[k] + it_row], acc);
+          }
         }
       }
       step_finish<VT, XT, FAM, INIT, WR, ZOWN>(a, r0 + it_row, acc, rin, xin, di, zo);
@@ -220,74 +239,89 @@ __global__ void __launch_bounds__((tma_warps<XT>() + 1) * 32, TmaShape<XT>::kCta
     step_slice<VT, XT, FAM, INIT, WR, ZOWN>(a, gen[q], lane);
 }
 
-template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN>
+template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN, int W>
 void launch_inst(const StepArgs<VT, XT>& a, const TmaPlan& p, const TmaTile* tiles, int ntiles,
                  int grid, double* err, cudaStream_t s) {
   const int smem = kBarrierBytes + p.nstages * p.stage_bytes;
-  k_step_tma<VT, XT, FAM, INIT, WR, ZOWN><<<grid, (tma_warps<XT>() + 1) * 32, smem, s>>>(
+  k_step_tma<VT, XT, FAM, INIT, WR, ZOWN, W><<<grid, (tma_warps<XT>() + 1) * 32, smem, s>>>(
       a, p, tiles, ntiles, a.slices, a.slices ? a.nlist : 0, err);
   count_launch();
 }
 
-template <class VT, class XT, int FAM, bool INIT>
+template <class VT, class XT, int FAM, bool INIT, int W>
 void launch_wr(const StepArgs<VT, XT>& a, const TmaPlan& p, const TmaTile* tiles, int ntiles,
                int grid, double* err, cudaStream_t s) {
   const bool z = a.zown != nullptr;
   if (a.write_r) {
-    if (z) launch_inst<VT, XT, FAM, INIT, true, true>(a, p, tiles, ntiles, grid, err, s);
-    else launch_inst<VT, XT, FAM, INIT, true, false>(a, p, tiles, ntiles, grid, err, s);
+    if (z) launch_inst<VT, XT, FAM, INIT, true, true, W>(a, p, tiles, ntiles, grid, err, s);
+    else launch_inst<VT, XT, FAM, INIT, true, false, W>(a, p, tiles, ntiles, grid, err, s);
   } else {
-    if (z) launch_inst<VT, XT, FAM, INIT, false, true>(a, p, tiles, ntiles, grid, err, s);
-    else launch_inst<VT, XT, FAM, INIT, false, false>(a, p, tiles, ntiles, grid, err, s);
+    if (z) launch_inst<VT, XT, FAM, INIT, false, true, W>(a, p, tiles, ntiles, grid, err, s);
+    else launch_inst<VT, XT, FAM, INIT, false, false, W>(a, p, tiles, ntiles, grid, err, s);
   }
 }
 
-template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN>
+template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN, int W>
 void set_smem_attr(int bytes) {
-  cudaFuncSetAttribute(k_step_tma<VT, XT, FAM, INIT, WR, ZOWN>,
+  cudaFuncSetAttribute(k_step_tma<VT, XT, FAM, INIT, WR, ZOWN, W>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-template <class VT, class XT>
+template <class VT, class XT, int FAM, bool INIT, int W>
+void configure_wr(int bytes) {
+  set_smem_attr<VT, XT, FAM, INIT, true, true, W>(bytes);
+  set_smem_attr<VT, XT, FAM, INIT, true, false, W>(bytes);
+  set_smem_attr<VT, XT, FAM, INIT, false, true, W>(bytes);
+  set_smem_attr<VT, XT, FAM, INIT, false, false, W>(bytes);
+}
+
+template <class VT, class XT, int W>
 void configure_all(int bytes) {
-  set_smem_attr<VT, XT, FAM_CHEB4, true, true, true>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB4, true, true, false>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB4, true, false, true>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB4, true, false, false>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB4, false, true, true>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB4, false, true, false>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB4, false, false, true>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB4, false, false, false>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB1, true, true, true>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB1, true, true, false>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB1, true, false, true>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB1, true, false, false>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB1, false, true, true>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB1, false, true, false>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB1, false, false, true>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB1, false, false, false>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB4S, false, true, true>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB4S, false, true, false>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB4S, false, false, true>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB4S, false, false, false>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB4SR, true, true, true>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB4SR, true, true, false>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB4SR, true, false, true>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB4SR, true, false, false>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB4SR, false, true, true>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB4SR, false, true, false>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB4SR, false, false, true>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB4SR, false, false, false>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB1S, false, true, true>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB1S, false, true, false>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB1S, false, false, true>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB1S, false, false, false>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB1SR, true, true, true>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB1SR, true, true, false>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB1SR, true, false, true>(bytes);
-  set_smem_attr<VT, XT, FAM_CHEB1SR, true, false, false>(bytes);
-  set_smem_attr<VT, XT, FAM_JAC, true, false, false>(bytes);
-  set_smem_attr<VT, XT, FAM_RES, true, false, false>(bytes);
+  configure_wr<VT, XT, FAM_CHEB4, true, W>(bytes);
+  configure_wr<VT, XT, FAM_CHEB4, false, W>(bytes);
+  configure_wr<VT, XT, FAM_CHEB1, true, W>(bytes);
+  configure_wr<VT, XT, FAM_CHEB1, false, W>(bytes);
+  configure_wr<VT, XT, FAM_CHEB4S, false, W>(bytes);
+  configure_wr<VT, XT, FAM_CHEB4SR, true, W>(bytes);
+  configure_wr<VT, XT, FAM_CHEB4SR, false, W>(bytes);
+  configure_wr<VT, XT, FAM_CHEB1S, false, W>(bytes);
+  configure_wr<VT, XT, FAM_CHEB1SR, true, W>(bytes);
+  set_smem_attr<VT, XT, FAM_JAC, true, false, false, W>(bytes);
+  set_smem_attr<VT, XT, FAM_RES, true, false, false, W>(bytes);
+}
+
+// the family / INIT dispatch for one width variant
+template <class VT, class XT, int W>
+void launch_fam(const StepArgs<VT, XT>& a, const TmaPlan& p, const TmaTile* tiles, int ntiles,
+                int grid, double* err, cudaStream_t s) {
+  switch (a.fam) {
+    case FAM_CHEB4:
+      if (a.init) launch_wr<VT, XT, FAM_CHEB4, true, W>(a, p, tiles, ntiles, grid, err, s);
+      else launch_wr<VT, XT, FAM_CHEB4, false, W>(a, p, tiles, ntiles, grid, err, s);
+      break;
+    case FAM_CHEB4S:
+      launch_wr<VT, XT, FAM_CHEB4S, false, W>(a, p, tiles, ntiles, grid, err, s);
+      break;
+    case FAM_CHEB4SR:
+      if (a.init) launch_wr<VT, XT, FAM_CHEB4SR, true, W>(a, p, tiles, ntiles, grid, err, s);
+      else launch_wr<VT, XT, FAM_CHEB4SR, false, W>(a, p, tiles, ntiles, grid, err, s);
+      break;
+    case FAM_CHEB1S:
+      launch_wr<VT, XT, FAM_CHEB1S, false, W>(a, p, tiles, ntiles, grid, err, s);
+      break;
+    case FAM_CHEB1SR:
+      launch_wr<VT, XT, FAM_CHEB1SR, true, W>(a, p, tiles, ntiles, grid, err, s);
+      break;
+    case FAM_CHEB1:
+      if (a.init) launch_wr<VT, XT, FAM_CHEB1, true, W>(a, p, tiles, ntiles, grid, err, s);
+      else launch_wr<VT, XT, FAM_CHEB1, false, W>(a, p, tiles, ntiles, grid, err, s);
+      break;
+    case FAM_RES:
+      launch_inst<VT, XT, FAM_RES, true, false, false, W>(a, p, tiles, ntiles, grid, err, s);
+      break;
+    default:
+      launch_inst<VT, XT, FAM_JAC, true, false, false, W>(a, p, tiles, ntiles, grid, err, s);
+  }
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -295,9 +329,10 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 }  // namespace
 
 void tma_configure() {
-  configure_all<double, double>(TmaShape<double>::kSmemBudget + kBarrierBytes);
-  configure_all<float, float>(TmaShape<float>::kSmemBudget + kBarrierBytes);
-  configure_all<__nv_bfloat16, float>(TmaShape<float>::kSmemBudget + kBarrierBytes);
+  configure_all<double, double, 0>(TmaShape<double>::kSmemBudget + kBarrierBytes);
+  configure_all<double, double, 7>(TmaShape<double>::kSmemBudget + kBarrierBytes);
+  configure_all<float, float, 0>(TmaShape<float>::kSmemBudget + kBarrierBytes);
+  configure_all<__nv_bfloat16, float, 0>(TmaShape<float>::kSmemBudget + kBarrierBytes);
 }
 
 template <class VT, class XT>
@@ -307,34 +342,15 @@ bool launch_step_tma(const StepArgs<VT, XT>& a, const TmaPlan& p, const TmaTile*
   if (!aligned16(a.A.val) || !aligned16(a.u) || !aligned16(a.rin)) return false;
   if (a.fam != FAM_RES && (!aligned16(a.xin) || !aligned16(a.dinv))) return false;
   if (a.zown && a.zown != a.u) return false;  // z_j at the row is read from u's window
-  switch (a.fam) {
-    case FAM_CHEB4:
-      if (a.init) launch_wr<VT, XT, FAM_CHEB4, true>(a, p, tiles, ntiles, grid, err, s);
-      else launch_wr<VT, XT, FAM_CHEB4, false>(a, p, tiles, ntiles, grid, err, s);
-      break;
-    case FAM_CHEB4S:
-      launch_wr<VT, XT, FAM_CHEB4S, false>(a, p, tiles, ntiles, grid, err, s);
-      break;
-    case FAM_CHEB4SR:
-      if (a.init) launch_wr<VT, XT, FAM_CHEB4SR, true>(a, p, tiles, ntiles, grid, err, s);
-      else launch_wr<VT, XT, FAM_CHEB4SR, false>(a, p, tiles, ntiles, grid, err, s);
-      break;
-    case FAM_CHEB1S:
-      launch_wr<VT, XT, FAM_CHEB1S, false>(a, p, tiles, ntiles, grid, err, s);
-      break;
-    case FAM_CHEB1SR:
-      launch_wr<VT, XT, FAM_CHEB1SR, true>(a, p, tiles, ntiles, grid, err, s);
-      break;
-    case FAM_CHEB1:
-      if (a.init) launch_wr<VT, XT, FAM_CHEB1, true>(a, p, tiles, ntiles, grid, err, s);
-      else launch_wr<VT, XT, FAM_CHEB1, false>(a, p, tiles, ntiles, grid, err, s);
-      break;
-    case FAM_RES:
-      launch_inst<VT, XT, FAM_RES, true, false, false>(a, p, tiles, ntiles, grid, err, s);
-      break;
-    default:
-      launch_inst<VT, XT, FAM_JAC, true, false, false>(a, p, tiles, ntiles, grid, err, s);
+  // FP64 rows of the 7-point pattern: the fixed-width variant (its centre
+  // entry, index 3, is the row itself)
+  if constexpr (std::is_same<XT, double>::value) {
+    if (p.w == 7 && p.d[3] == p.d0) {
+      launch_fam<VT, XT, 7>(a, p, tiles, ntiles, grid, err, s);
+      return true;
+    }
   }
+  launch_fam<VT, XT, 0>(a, p, tiles, ntiles, grid, err, s);
   return true;
 }
 

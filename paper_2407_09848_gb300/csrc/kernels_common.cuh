@@ -18,6 +18,22 @@ __device__ __forceinline__ float ldval(const __nv_bfloat16* p) {
 template <class T>
 __device__ __forceinline__ T absv(T v) { return v < T(0) ? -v : v; }
 
+// Load of a vector entry.  CG = false: a plain load, or for the gathered
+// operand of a product the read-only path (__ldg), which is valid in kernels
+// whose launch does not write that vector.  CG = true: an L2 (coherent) load,
+// for the persistent kernel that reads in one phase what other blocks wrote in
+// an earlier phase of the same launch.
+template <bool CG, class T>
+__device__ __forceinline__ T ldv(const T* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+template <bool CG, class T>
+__device__ __forceinline__ T ldu(const T* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return __ldg(p);
+}
+
 // init + SIGN * (A u)_row from one pass over the row (SIGN = +1 or -1, so a
 // residual b - A u comes out of the same multiply-adds).  `lane` is the row's
 // position in slice `s`.  Rows past n (tail of the last slice) see only zero
@@ -25,12 +41,34 @@ __device__ __forceinline__ T absv(T v) { return v < T(0) ? -v : v; }
 // resource on this GPU (its FP64 pipe issues about 2 FMAs per clock per SM),
 // so the row costs exactly one multiply-add per stored entry and nothing else.
 // Entries k in [k0, k1) of row `row` of slice s: init + SIGN * sum a_k u_{c_k}.
-template <int SIGN, class VT, class XT>
+template <int SIGN, class VT, class XT, bool CG = false>
 __device__ __forceinline__ XT row_spmv_range(const DevMat<VT>& A, int64_t s, int lane, int64_t row,
                                              const XT* __restrict__ u, XT init, int k0, int k1) {
   const SliceDesc d = A.sd[s];
   const int64_t nm1 = A.n - 1;
   XT t = init;
+  if (k1 - k0 == 7) {
+    // the seven entries of a 7-point row without guards: on GB300's narrow
+    // FP64 pipe a predicated-off multiply-add still takes an issue slot
+    // (same operations in the same order as the general loop below)
+    XT a[7];
+    int64_t c[7];
+#pragma unroll
+    for (int kk = 0; kk < 7; ++kk) {
+      const int k = k0 + kk;
+      const int64_t e = d.vbase + (int64_t)k * kSlice + lane;
+      a[kk] = XT(ldval(A.val + e));
+      if (d.cref >= 0) {
+        const int64_t cc = row + (int64_t)A.off[d.cref + k];
+        c[kk] = cc < 0 ? 0 : (cc > nm1 ? nm1 : cc);
+      } else {
+        c[kk] = A.col[e];
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < 7; ++kk) t = fma(SIGN > 0 ? a[kk] : -a[kk], ldu<CG>(u + c[kk]), t);
+    return t;
+  }
   for (int kb = k0; kb < k1; kb += 8) {
     XT a[8];
     int64_t c[8];
@@ -52,16 +90,16 @@ __device__ __forceinline__ XT row_spmv_range(const DevMat<VT>& A, int64_t s, int
     }
 #pragma unroll
     for (int kk = 0; kk < 8; ++kk)
-      if (kb + kk < k1) t = fma(SIGN > 0 ? a[kk] : -a[kk], __ldg(u + c[kk]), t);
+      if (kb + kk < k1) t = fma(SIGN > 0 ? a[kk] : -a[kk], ldu<CG>(u + c[kk]), t);
   }
   return t;
 }
 
 // The whole row: entries 0 .. w-1 of the slice.
-template <int SIGN, class VT, class XT>
+template <int SIGN, class VT, class XT, bool CG = false>
 __device__ __forceinline__ XT row_spmv(const DevMat<VT>& A, int64_t s, int lane, int64_t row,
                                        const XT* __restrict__ u, XT init) {
-  return row_spmv_range<SIGN, VT, XT>(A, s, lane, row, u, init, 0, A.sd[s].w);
+  return row_spmv_range<SIGN, VT, XT, CG>(A, s, lane, row, u, init, 0, A.sd[s].w);
 }
 
 // The SpMV of one smoother step is accumulated as init + SIGN * (A u):
@@ -129,22 +167,78 @@ __device__ __forceinline__ void step_finish(const StepArgs<VT, XT>& a, int64_t r
 
 // One smoother step on the 32 rows of slice s, one row per lane, operands
 // read from global memory (the direct form of the step).
-template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN>
+template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN, bool CG = false>
 __device__ __forceinline__ void step_slice(const StepArgs<VT, XT>& a, int64_t s, int lane) {
   const int64_t row = s * kSlice + lane;
   const bool live = row < a.A.n;
   XT rin = XT(0), xin = XT(0), zo = XT(0), di = XT(0);
   if (live) {
-    rin = a.rin[row];
-    if (FAM != FAM_RES) xin = a.xin[row];
-    if (step_needs_dinv<FAM>()) di = a.dinv[row];
-    if (ZOWN) zo = a.zown[row];
+    rin = ldv<CG>(a.rin + row);
+    if (FAM != FAM_RES) xin = ldv<CG>(a.xin + row);
+    if (step_needs_dinv<FAM>()) di = a.dinv[row];  // formed at set-up, never written here
+    if (ZOWN) zo = ldv<CG>(a.zown + row);
   }
   using F = StepForm<FAM, INIT>;
-  const XT acc = row_spmv<F::kSign, VT, XT>(a.A, s, lane, row, a.u,
-                                             step_init<FAM, F::kResidual>(rin, di));
+  const XT acc = row_spmv<F::kSign, VT, XT, CG>(a.A, s, lane, row, a.u,
+                                                 step_init<FAM, F::kResidual>(rin, di));
   if (!live) return;
   step_finish<VT, XT, FAM, INIT, WR, ZOWN>(a, row, acc, rin, xin, di, zo);
+}
+
+// Per-element bodies of the elementwise V-cycle kernels, shared by their own
+// launches (kernels_smooth.cu, kernels_krylov.cu) and by the persistent
+// coarse-level kernel (kernels_cycle.cu), so both give the same bits.
+
+// First step from x = 0 (no product with A), row i:
+//   4th kind: z_1 = c2 M^{-1} b, x = beta_1 z_1 (r_0 = b is not copied)
+//   1st kind: r^(0) = (1/rho) M^{-1} b, d^(0) = r^(0)/theta, x = d^(0)
+//   Jacobi:   x = M^{-1} b
+template <class XT, int FAM, bool CG = false>
+__device__ __forceinline__ void first_row(int64_t i, const XT* b, const XT* dinv, XT* rout,
+                                          XT* zout, XT* xout, XT c2, XT beta, XT rhoinv) {
+  const XT bm = ldv<CG>(b + i) * dinv[i];
+  if constexpr (FAM == FAM_CHEB4) {
+    const XT z = c2 * bm;
+    zout[i] = z;
+    xout[i] = beta * z;
+  } else if constexpr (FAM == FAM_CHEB1) {
+    const XT r = rhoinv * bm;
+    rout[i] = r;
+    const XT z = c2 * r;
+    zout[i] = z;
+    xout[i] = z;
+  } else {
+    xout[i] = bm;
+  }
+}
+
+// b_c[I] = sum of res over the children of coarse row I, in list order
+template <class XT, bool CG = false>
+__device__ __forceinline__ void aggregate_row(int64_t I, const int32_t* cptr, const int32_t* cidx,
+                                              const XT* res, XT* bc) {
+  XT acc = XT(0);
+  const int q1 = cptr[I + 1];
+  for (int q = cptr[I]; q < q1; ++q) acc += ldv<CG>(res + cidx[q]);
+  bc[I] = acc;
+}
+
+// x_i += e_c[agg_i]
+template <class XT, bool CG = false>
+__device__ __forceinline__ void prolong_row(int64_t i, const int32_t* agg, const XT* ec, XT* x) {
+  x[i] = ldv<CG>(x + i) + ldv<CG>(ec + agg[i]);
+}
+
+// x_i = (A_c^{-1} b)_i for the coarsest level, one warp per row: lane l sums
+// columns l, l + 32, ... in order, then a fixed butterfly adds the lanes
+template <class XT, bool CG = false>
+__device__ __forceinline__ void coarse_gemv_row(int i, int nc, const double* ainv, const XT* b,
+                                                XT* x, int lane) {
+  const double* row = ainv + (size_t)i * nc;
+  double acc = 0.0;
+  for (int j = lane; j < nc; j += 32) acc = fma(row[j], (double)ldv<CG>(b + j), acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) x[i] = XT(acc);
 }
 
 // Sum over a block (any blockDim multiple of 32, <= 1024); result valid in thread 0.

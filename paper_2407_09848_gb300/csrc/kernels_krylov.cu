@@ -270,12 +270,7 @@ __global__ void __launch_bounds__(kBlock) k_coarse_gemv(int nc, const double* __
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   if (i >= nc) return;
-  const double* row = ainv + (size_t)i * nc;
-  double acc = 0.0;
-  for (int j = lane; j < nc; j += 32) acc = fma(row[j], (double)b[j], acc);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) x[i] = XT(acc);
+  coarse_gemv_row<XT>(i, nc, ainv, b, x, lane);
 }
 
 template <class XT>

@@ -130,10 +130,7 @@ void launch_step(const StepArgs<VT, XT>& a, cudaStream_t s) {
   }
 }
 
-// First step from x = 0 (no product with A):
-//   4th kind: z_1 = c2 M^{-1} b, x = beta_1 z_1 (r_0 = b is not copied)
-//   1st kind: r^(0) = (1/rho) M^{-1} b, d^(0) = r^(0)/theta, x = d^(0)
-//   Jacobi:   x = M^{-1} b
+// First step from x = 0 (no product with A): first_row (kernels_common.cuh).
 template <class XT, int FAM>
 __global__ void __launch_bounds__(kBlock) k_first(int64_t n, const XT* __restrict__ b,
                                                   const XT* __restrict__ dinv,
@@ -142,20 +139,7 @@ __global__ void __launch_bounds__(kBlock) k_first(int64_t n, const XT* __restric
                                                   XT rhoinv) {
   const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
   if (i >= n) return;
-  const XT bm = b[i] * dinv[i];
-  if constexpr (FAM == FAM_CHEB4) {
-    const XT z = c2 * bm;
-    zout[i] = z;
-    xout[i] = beta * z;
-  } else if constexpr (FAM == FAM_CHEB1) {
-    const XT r = rhoinv * bm;
-    rout[i] = r;
-    const XT z = c2 * r;
-    zout[i] = z;
-    xout[i] = z;
-  } else {
-    xout[i] = bm;
-  }
+  first_row<XT, FAM>(i, b, dinv, rout, zout, xout, c2, beta, rhoinv);
 }
 
 template <class XT>
@@ -183,10 +167,7 @@ __global__ void __launch_bounds__(kBlock) k_aggregate(const int32_t* __restrict_
                                                       XT* __restrict__ bc) {
   const int64_t I = (int64_t)blockIdx.x * kBlock + threadIdx.x;
   if (I >= nc) return;
-  XT acc = XT(0);
-  const int q1 = cptr[I + 1];
-  for (int q = cptr[I]; q < q1; ++q) acc += res[cidx[q]];
-  bc[I] = acc;
+  aggregate_row<XT>(I, cptr, cidx, res, bc);
 }
 
 template <class XT>
@@ -202,7 +183,7 @@ template <class XT>
 __global__ void __launch_bounds__(kBlock) k_prolong(int64_t n, const int32_t* __restrict__ agg,
                                                     const XT* __restrict__ ec, XT* x) {
   const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
-  if (i < n) x[i] += ec[agg[i]];
+  if (i < n) prolong_row<XT>(i, agg, ec, x);
 }
 
 template <class XT>

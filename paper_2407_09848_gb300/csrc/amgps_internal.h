@@ -101,15 +101,20 @@ constexpr int kMaxSplit = 32;
 //     three tiles ahead of the FP64-bound consumers;
 //   FP32/BF16: 1024-row tiles (32 slices), two CTAs per SM, each 1 producer
 //     warp and one group of 16 consumer warps, up to 112.5 KB of stages.
+// kVecSlots: the tile's own rows copied into a stage -- r_in, x_in and, for
+// FP32 vectors, 1/M (FP64 consumers read 1/M from global memory in the few
+// steps that need it, which keeps a 512-wide grid's stage four deep).
 template <class XT>
 struct TmaShape {  // FP32 vectors (FP32 and BF16 levels)
   static constexpr int kRows = 1024, kGroups = 1, kConsumers = 16, kCtasPerSm = 2;
   static constexpr int kSmemBudget = 115200;
+  static constexpr int kVecSlots = 3;
 };
 template <>
 struct TmaShape<double> {
   static constexpr int kRows = 480, kGroups = 2, kConsumers = 15, kCtasPerSm = 1;
   static constexpr int kSmemBudget = 230400;
+  static constexpr int kVecSlots = 2;
 };
 // the same figures by vector size, for the host-side planner
 inline int tma_rows(size_t xsize) {
@@ -121,6 +126,13 @@ inline int tma_ctas_per_sm(size_t xsize) {
 inline int tma_smem_budget(size_t xsize) {
   return xsize == 8 ? TmaShape<double>::kSmemBudget : TmaShape<float>::kSmemBudget;
 }
+inline int tma_vec_slots(size_t xsize) {
+  return xsize == 8 ? TmaShape<double>::kVecSlots : TmaShape<float>::kVecSlots;
+}
+// Two offset groups share one window when the merged window holds at most
+// this many elements more than the two separate ones (the +-nx offsets of a
+// 481..544-wide grid against 480-row tiles).
+constexpr int kTmaMergeSlack = 64;
 // The stage count of a plan is a multiple of the group count: then the
 // previous fill of the stage a group waits on is a tile of the same group,
 // already consumed, so the parity wait cannot pass on a stale phase.  (With
@@ -176,6 +188,47 @@ void launch_add(int64_t n, const XT* x, const XT* y, XT* out, cudaStream_t s);
 void launch_sub(int64_t n, const double* x, const double* y, double* out, cudaStream_t s);
 void launch_scale_dev(int64_t n, const double* x, double* out, const double* s_dev, double factor,
                       cudaStream_t s);
+
+// ---- persistent kernel for the coarse levels of a V-cycle (kernels_cycle.cu) ----
+// The levels below the TMA-fed ones are launch-latency-bound: their kernels
+// last a few microseconds each.  The host records the kernel sequence of
+// those levels once (the same calls, same arguments, same order) as a list of
+// phases, and one co-resident grid runs the phases with a grid-wide barrier
+// between consecutive ones.
+enum CycleOp { CY_STEP = 0, CY_FIRST = 1, CY_AGG = 2, CY_PROLONG = 3, CY_GEMV = 4, CY_COPY = 5 };
+
+template <class VT, class XT>
+struct CyclePhase {
+  int op = CY_STEP;
+  int fam = FAM_CHEB4;   // CY_FIRST: FAM_CHEB4, FAM_CHEB1 or FAM_JAC
+  int64_t n = 0;         // rows (CY_AGG: coarse rows)
+  StepArgs<VT, XT> a;    // CY_STEP (direct form, every slice of the level)
+  const int32_t* i0 = nullptr;  // CY_AGG: cptr; CY_PROLONG: agg
+  const int32_t* i1 = nullptr;  // CY_AGG: cidx
+  const XT* in0 = nullptr;      // CY_FIRST: b; CY_AGG: res; CY_PROLONG: e_c; CY_GEMV: b; CY_COPY: src
+  const XT* in1 = nullptr;      // CY_FIRST: 1/M
+  XT* out0 = nullptr;           // CY_FIRST: r; CY_AGG: b_c; CY_PROLONG, CY_GEMV: x; CY_COPY: dst
+  XT* out1 = nullptr;           // CY_FIRST: z
+  XT* out2 = nullptr;           // CY_FIRST: x
+  const double* ainv = nullptr;  // CY_GEMV
+  XT c2 = 0, beta = 0, rhoinv = 1;
+};
+
+// grid-barrier words: arrivals (zeroed before each launch) and generation
+struct CycleSync {
+  unsigned* count = nullptr;
+  unsigned* gen = nullptr;
+};
+
+// Blocks of the persistent launch: all co-resident (occupancy x SMs, at most
+// kCycleMaxBlocksPerSm per SM); 0 when the kernel cannot run.
+template <class VT, class XT>
+int cycle_grid(int nsm);
+// Launches the phases (a cooperative launch: the driver refuses it if the grid
+// cannot be co-resident).  Returns the launch's error code.
+template <class VT, class XT>
+cudaError_t launch_cycle(const CyclePhase<VT, XT>* phases, int nph, const CycleSync& sync, int grid,
+                         double* err, cudaStream_t s);
 
 // ---- weight-predicting MLP (kernels_mlp.cu) ----
 constexpr int kMlpParams = 4996;

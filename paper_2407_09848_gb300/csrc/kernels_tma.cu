@@ -5,15 +5,16 @@
 // at any moment form one contiguous band and the vector windows that
 // neighbouring tiles share are read from HBM once and then from L2.  Warp 0 of
 // each CTA is the producer: one lane issues cp.async.bulk copies of a tile's
-// values, of its rows of r_in, x_in and (when the step needs it) 1/M, and of
+// values, of its rows of r_in, x_in and (when the step needs it, FP32 vectors)
+// 1/M, and of
 // the contiguous windows of the multiplied vector u (one per group of nearby
 // column offsets) into a shared-memory stage, completing on that stage's
 // "full" mbarrier.  The other warps are consumers, in groups that take
 // alternate tiles; a group's warps split the tile's 32-row slices: they wait
 // on "full", evaluate the rows from shared memory, store r/z/x to global
 // memory, and arrive on the stage's "empty" mbarrier so the producer may
-// refill it.  After the tiles, all consumers also run the slices outside the
-// plan with direct loads.  The arithmetic and its order are those of k_step,
+// refill it.  Before the tiles, while the first copies land, all consumers
+// run the slices outside the plan with direct loads.  The arithmetic and its order are those of k_step,
 // so both paths give the same bits.  Tile height, groups and CTAs per SM come
 // from TmaShape<XT>: for FP64 one CTA per SM with two groups of 15 warps and
 // four 480-row stages in flight (the FP64-bound consumers then never wait for
@@ -144,8 +145,9 @@ __global__ void __launch_bounds__((tma_warps<XT>() + 1) * 32, TmaShape<XT>::kCta
             unsigned char* base = stages + (size_t)st * p.stage_bytes;
             const int64_t r0 = rq;
             stage_r0[st] = rq;
-            // the residual needs no x_in or 1/M; a scaled step with scaled rin no 1/M
-            constexpr bool wdi = step_needs_dinv<FAM>();
+            // the residual needs no x_in or 1/M; a scaled step with scaled rin no
+            // 1/M; FP64 stages hold no 1/M slot (read from global memory)
+            constexpr bool wdi = step_needs_dinv<FAM>() && TmaShape<XT>::kVecSlots == 3;
             constexpr int nvec = FAM == FAM_RES ? 1 : (wdi ? 3 : 2);
             mbar_expect_tx(&full[st], (uint32_t)(p.vals_bytes + nvec * p.vec_bytes + p.win_bytes));
             bulk_g2s(base, a.A.val + vq, (uint32_t)p.vals_bytes, &full[st]);
@@ -153,7 +155,7 @@ __global__ void __launch_bounds__((tma_warps<XT>() + 1) * 32, TmaShape<XT>::kCta
             bulk_g2s(sv, a.rin + r0, (uint32_t)p.vec_bytes, &full[st]);
             if (FAM != FAM_RES) bulk_g2s(sv + p.rows, a.xin + r0, (uint32_t)p.vec_bytes, &full[st]);
             if (wdi) bulk_g2s(sv + 2 * p.rows, a.dinv + r0, (uint32_t)p.vec_bytes, &full[st]);
-            XT* sw = sv + 3 * p.rows;
+            XT* sw = sv + TmaShape<XT>::kVecSlots * p.rows;
             for (int g = 0; g < p.ngroups; ++g)
               bulk_g2s(sw + p.g_smem[g], a.u + r0 + p.g_start[g],
                        (uint32_t)(p.g_elems[g] * (int)sizeof(XT)), &full[st]);
@@ -181,6 +183,13 @@ __global__ void __launch_bounds__((tma_warps<XT>() + 1) * 32, TmaShape<XT>::kCta
   const int grp = c / kCons, cw = c % kCons;
   const int spt = p.rows / kSlice;  // slices per tile
   using F = StepForm<FAM, INIT>;
+  // First the slices outside the plan (pattern changes, windows leaving
+  // [0, n)): direct loads, round-robin over all consumer warps, while the
+  // producer's first copies are in flight.  Their rows are disjoint from the
+  // tiles' rows, so the order changes no result.
+  for (int64_t q = (int64_t)blockIdx.x * tma_warps<XT>() + c; q < ngen;
+       q += (int64_t)gridDim.x * tma_warps<XT>())
+    step_slice<VT, XT, FAM, INIT, WR, ZOWN>(a, gen[q], lane);
   // group g takes this CTA's tiles g, g + kGroups, ...  The stage of tile it
   // last held tile it - nstages; nstages is a multiple of kGroups, so that
   // tile belongs to this group and was consumed before this wait, and the
@@ -196,14 +205,18 @@ __global__ void __launch_bounds__((tma_warps<XT>() + 1) * 32, TmaShape<XT>::kCta
     }
     const unsigned char* base = stages + (size_t)st * p.stage_bytes;
     const XT* sv = reinterpret_cast<const XT*>(base + p.vals_bytes);
-    const XT* sw = sv + 3 * p.rows;
+    const XT* sw = sv + TmaShape<XT>::kVecSlots * p.rows;
     const int64_t r0 = stage_r0[st];
     for (int cs = cw; cs < spt; cs += kCons) {
       const int it_row = cs * kSlice + lane;  // row inside the tile
       const VT* svals = reinterpret_cast<const VT*>(base) + (size_t)cs * p.w * kSlice + lane;
       const XT rin = sv[it_row];
       const XT xin = FAM == FAM_RES ? XT(0) : sv[p.rows + it_row];
-      const XT di = step_needs_dinv<FAM>() ? sv[2 * p.rows + it_row] : XT(0);
+      XT di = XT(0);
+      if constexpr (step_needs_dinv<FAM>()) {
+        if constexpr (TmaShape<XT>::kVecSlots == 3) di = sv[2 * p.rows + it_row];
+        else di = __ldg(a.dinv + r0 + it_row);  // formed at set-up, never written here
+      }
       const XT zo = ZOWN ? sw[p.d0 + it_row] : XT(0);
       XT acc = step_init<FAM, F::kResidual>(rin, di);
       if constexpr (W > 0) {
@@ -227,16 +240,7 @@ __global__ void __launch_bounds__((tma_warps<XT>() + 1) * 32, TmaShape<XT>::kCta
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[st]);
   }
-  if (abort_flag) {
-    if (lane == 0) *err = 1.0;
-    return;
-  }
-  // the slices outside the plan (pattern changes, windows leaving [0, n)):
-  // direct loads, round-robin over all consumer warps; their rows are
-  // disjoint from the tiles' rows
-  for (int64_t q = (int64_t)blockIdx.x * tma_warps<XT>() + c; q < ngen;
-       q += (int64_t)gridDim.x * tma_warps<XT>())
-    step_slice<VT, XT, FAM, INIT, WR, ZOWN>(a, gen[q], lane);
+  if (abort_flag && lane == 0) *err = 1.0;
 }
 
 template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN, int W>

@@ -291,12 +291,13 @@ HostPlan build_tma_plan(const HostSell& h, size_t vsize, size_t xsize, int smem_
   P.w = width[dom];
   const int32_t* off = h.off.data() + dom;
   const int64_t A = 16 / (int64_t)xsize;
-  // groups of offsets whose tile-height windows overlap or touch
+  // groups of offsets whose tile-height windows overlap, touch, or leave a
+  // gap of at most kTmaMergeSlack elements (copied along)
   int gk[kTmaMaxW];
   int64_t glo[kTmaMaxW], ghi[kTmaMaxW];
   int ng = 0;
   for (int k = 0; k < P.w; ++k) {
-    if (ng > 0 && off[k] - ghi[ng - 1] <= rows) {
+    if (ng > 0 && off[k] - ghi[ng - 1] <= rows + kTmaMergeSlack) {
       ghi[ng - 1] = off[k];
     } else {
       glo[ng] = ghi[ng] = off[k];
@@ -326,7 +327,8 @@ HostPlan build_tma_plan(const HostSell& h, size_t vsize, size_t xsize, int smem_
   P.vals_bytes = (int)(P.w * rows * vsize);
   P.vec_bytes = (int)(rows * xsize);
   P.win_bytes = (int)(acc * (int64_t)xsize);
-  P.stage_bytes = (int)ceil_to(P.vals_bytes + 3 * P.vec_bytes + P.win_bytes, 128);
+  P.stage_bytes =
+      (int)ceil_to(P.vals_bytes + tma_vec_slots(xsize) * P.vec_bytes + P.win_bytes, 128);
   P.nstages = std::min<int>(kTmaMaxStages, (smem_budget - 2 * kTmaMaxStages * 8) / P.stage_bytes);
   P.nstages -= P.nstages % tma_groups(xsize);  // see tma_groups()
   if (P.nstages < 2) {

@@ -222,15 +222,22 @@ def test_binding_constants_match_header():
         assert enum["AMGPS_" + kind.upper()] == v, kind
     for prec, v in amgps.PREC.items():
         assert enum["AMGPS_" + prec.upper()] == v, prec
-    assert (enum["AMGPS_OPT_TMA"], enum["AMGPS_OPT_FLEXIBLE"], enum["AMGPS_OPT_COARSE_SWEEPS"]) == (
-        amgps.OPT_TMA, amgps.OPT_FLEXIBLE, amgps.OPT_COARSE_SWEEPS)
+    assert (enum["AMGPS_OPT_TMA"], enum["AMGPS_OPT_FLEXIBLE"], enum["AMGPS_OPT_COARSE_SWEEPS"],
+            enum["AMGPS_OPT_COARSE_KERNEL"]) == (amgps.OPT_TMA, amgps.OPT_FLEXIBLE,
+                                                 amgps.OPT_COARSE_SWEEPS, amgps.OPT_COARSE_KERNEL)
 
 
 def test_fp64_stage_count_is_even(lib):
-    # a 480-wide grid leaves room for three 57.6 KB FP64 stages; the planner
-    # keeps two, a multiple of the FP64 shape's two consumer groups
+    # a banded matrix whose seven offsets chain into one 2880-element window
+    # (gaps of at most 544) leaves room for three 57.6 KB FP64 stages (values
+    # 26,880 B, r_in and x_in 7,680 B, window 23,040 B); the planner keeps two,
+    # a multiple of the FP64 shape's two consumer groups
+    import scipy.sparse as sp
     from paper_2407_09848_gb300 import problems as pr
-    tiles, gen, stage, nst = amgps.tma_plan_stats(pr.to_csr(pr.poisson(480, 8, 8)), "f64")
+    offs = [-1200, -656, -112, 0, 112, 656, 1200]
+    n = 9600
+    A = sp.diags([np.full(n - abs(o), 8.0 if o == 0 else -1.0) for o in offs], offs).tocsr()
+    tiles, gen, stage, nst = amgps.tma_plan_stats(A, "f64")
     assert tiles > 0 and stage == 57600 and nst == 2
     tiles, gen, stage, nst = amgps.tma_plan_stats(pr.to_csr(pr.poisson(256, 8, 8)), "f64")
     assert nst == 4
@@ -337,7 +344,8 @@ def test_tma_plan_stage_emulation(lib, prec):
     rng = np.random.default_rng(11)
     planned = 0
     for st in (pr.poisson(64, 40, 12), pr.varcoef(48, 1.0, 3.0, seed=3, ny=40, nz=9),
-               pr.aniso(40, 1e-3), pr.poisson(480, 4, 4), pr.poisson(300, 3, 3)):
+               pr.aniso(40, 1e-3), pr.poisson(480, 4, 4), pr.poisson(300, 3, 3),
+               pr.poisson(512, 4, 4), pr.varcoef(520, 1.0, 3.0, seed=4, ny=4, nz=3)):
         A = pr.to_csr(st)
         n = A.shape[0]
         L = amgps.sell_layout(A)
@@ -369,6 +377,24 @@ def test_tma_plan_stage_emulation(lib, prec):
             assert np.array_equal(win[P["d0"] + i], u[r0:r0 + rows])
         assert np.all(covered == 1)
     assert planned > 90
+
+
+def test_tma_plan_merges_the_windows_of_512_wide_grids(lib):
+    # host-only: with 480-row tiles the -nx..+nx offsets of a 481..545-wide grid
+    # share one window (the gap it copies along is at most 64 elements), so a
+    # 7-point level has three window groups and, with no 1/M slot in FP64
+    # stages, four stages; one column wider the gap exceeds the slack, five
+    # groups exceed the plan's four and no tile is planned
+    from paper_2407_09848_gb300 import problems as pr
+    for nx in (481, 512, 545):
+        P = amgps.tma_plan(pr.to_csr(pr.poisson(nx, 16, 16)), "f64")
+        assert P["ngroups"] == 3 and P["nstages"] == 4 and len(P["tiles"]) > 0, nx
+        assert P["g_elems"][1] >= 2 * nx + 480  # rows -nx .. nx + 479 of the tile
+    P = amgps.tma_plan(pr.to_csr(pr.poisson(546, 16, 16)), "f64")
+    assert len(P["tiles"]) == 0
+    # 256-wide grids keep their windows and four stages
+    P = amgps.tma_plan(pr.to_csr(pr.poisson(256, 16, 16)), "f64")
+    assert P["ngroups"] == 3 and P["nstages"] == 4
 
 
 @pytest.mark.parametrize("kind", ["cheb4", "cheb4_opt", "weights", "cheb1_opt", "cheb1",

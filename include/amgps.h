@@ -308,8 +308,16 @@ amgps_status amgps_synchronize(amgps_ctx* ctx);
  * AMGPS_OPT_COARSE_SWEEPS (default 0): the coarsest level of the V-cycle is
  * solved with the dense FP64 inverse (0), or by m = 1..1000 l1-Jacobi sweeps
  * from zero, x <- x + M^{-1}(b - A_c x), the coarse solver of the paper's
- * experiments (Sec. 4 uses 30); the V-cycle stays symmetric either way. */
-enum { AMGPS_OPT_TMA = 1, AMGPS_OPT_FLEXIBLE = 2, AMGPS_OPT_COARSE_SWEEPS = 3 };
+ * experiments (Sec. 4 uses 30); the V-cycle stays symmetric either way.
+ * AMGPS_OPT_COARSE_KERNEL (default 0): 1 runs the levels below the last one
+ * that runs the TMA-fed step, down to the coarsest, as one persistent kernel
+ * (one co-resident grid with a bounded grid-wide barrier between dependent
+ * kernels' work) when they use aggregation transfers and one warp per slice;
+ * 0 launches their kernels one by one (inside the CUDA graph of the coarse
+ * levels).  Results are identical either way.  A barrier wait that gives up
+ * is reported by the next amgps_pcg as AMGPS_E_TIMEOUT. */
+enum { AMGPS_OPT_TMA = 1, AMGPS_OPT_FLEXIBLE = 2, AMGPS_OPT_COARSE_SWEEPS = 3,
+       AMGPS_OPT_COARSE_KERNEL = 4 };
 amgps_status amgps_set_option(amgps_ctx* ctx, int option, int64_t value);
 
 /* Host-only planning query (no device needed): how the TMA-fed step would

@@ -1,6 +1,6 @@
 """Build libamgps.so in-tree for sm_103a with nvcc (no CMake, no torch extension).
 
-The three CUDA translation units compile in parallel, then link into
+The CUDA translation units compile in parallel, then link into
 ``paper_2407_09848_gb300/libamgps.so``.  Objects go to ``_build/`` (ignored).
 """
 from __future__ import annotations
@@ -18,6 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libamgps.so")
 SOURCES = ["api.cu", "kernels_smooth.cu", "kernels_krylov.cu", "kernels_tma.cu", "kernels_mlp.cu",
+           "kernels_cycle.cu",
            "kernels_setup.cu", "layout.cu",
            "setup_host.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -176,6 +176,15 @@ struct amgps_ctx {
   std::vector<cudaEvent_t> pool;
   int64_t prof_launches[5] = {};  // class 3 (kernel count) is kept apart
   void* noalloc = nullptr;        // device address of the allocation-free scratch array
+  // persistent kernel for the coarse levels (option AMGPS_OPT_COARSE_KERNEL)
+  int use_cycle = 0;
+  bool tail_ok = false;
+  int tail_level = -1;             // first level it runs
+  int tail_nph = 0;                // recorded phases
+  int tail_grid = 0;               // co-resident blocks
+  void* tail_dev = nullptr;        // CyclePhase<VT, XT>[tail_cap] on the device
+  size_t tail_cap = 0;             // bytes
+  unsigned* tail_sync = nullptr;   // barrier words: count, generation
   double prof_ms[5] = {};
   double prof_bytes[5] = {};
 };
@@ -229,6 +238,7 @@ void free_hierarchy(amgps_ctx* c) {
     c->gexec = nullptr;
   }
   c->graph_ok = false;
+  c->tail_ok = false;
   if (!c->allocs.empty()) cudaStreamSynchronize(c->stream);
   for (void* p : c->allocs) cudaFree(p);
   c->allocs.clear();
@@ -344,6 +354,90 @@ double step_bytes(const Level& L, int nvec) {
 // ---------------------------------------------------------------------------
 template <class VT, class XT>
 struct Engine {
+  // While a phase list is being recorded (build_tail), the kernel calls below
+  // append their arguments to it instead of launching.
+  static std::vector<CyclePhase<VT, XT>>*& rec() {
+    thread_local std::vector<CyclePhase<VT, XT>>* r = nullptr;
+    return r;
+  }
+
+  static void do_first(int fam, int64_t n, const XT* b, const XT* dinv, XT* r, XT* z, XT* x,
+                       XT c2, XT beta, XT rhoinv, cudaStream_t s) {
+    if (auto* R = rec()) {
+      CyclePhase<VT, XT> p;
+      p.op = CY_FIRST;
+      p.fam = fam;
+      p.n = n;
+      p.in0 = b;
+      p.in1 = dinv;
+      p.out0 = r;
+      p.out1 = z;
+      p.out2 = x;
+      p.c2 = c2;
+      p.beta = beta;
+      p.rhoinv = rhoinv;
+      R->push_back(p);
+      return;
+    }
+    launch_first<XT>(fam, n, b, dinv, r, z, x, c2, beta, rhoinv, s);
+  }
+
+  static void do_copy(XT* dst, const XT* src, int64_t n, cudaStream_t s) {
+    if (auto* R = rec()) {
+      CyclePhase<VT, XT> p;
+      p.op = CY_COPY;
+      p.n = n;
+      p.in0 = src;
+      p.out0 = dst;
+      R->push_back(p);
+      return;
+    }
+    CK(cudaMemcpyAsync(dst, src, n * sizeof(XT), cudaMemcpyDeviceToDevice, s));
+  }
+
+  static void do_aggregate(const Level& L, const XT* res, XT* bc, cudaStream_t s) {
+    if (auto* R = rec()) {
+      CyclePhase<VT, XT> p;
+      p.op = CY_AGG;
+      p.n = L.nc;
+      p.i0 = L.cptr;
+      p.i1 = L.cidx;
+      p.in0 = res;
+      p.out0 = bc;
+      R->push_back(p);
+      return;
+    }
+    launch_aggregate<XT>(L.cptr, L.cidx, L.nc, res, bc, s);
+  }
+
+  static void do_prolong(const Level& L, const XT* ec, XT* x, cudaStream_t s) {
+    if (auto* R = rec()) {
+      CyclePhase<VT, XT> p;
+      p.op = CY_PROLONG;
+      p.n = L.n;
+      p.i0 = L.agg;
+      p.in0 = ec;
+      p.out0 = x;
+      R->push_back(p);
+      return;
+    }
+    launch_prolong<XT>(L.n, L.agg, ec, x, s);
+  }
+
+  static void do_gemv(const Level& L, const XT* b, XT* x, cudaStream_t s) {
+    if (auto* R = rec()) {
+      CyclePhase<VT, XT> p;
+      p.op = CY_GEMV;
+      p.n = L.n;
+      p.ainv = L.ainv;
+      p.in0 = b;
+      p.out0 = x;
+      R->push_back(p);
+      return;
+    }
+    launch_coarse_gemv<XT>((int)L.n, L.ainv, b, x, s);
+  }
+
   // One fused step on level L: the TMA-fed kernel over its tiles plus the
   // direct kernel over the remaining slices, or the direct kernel alone.
   static void run_step(amgps_ctx* c, const Level& L, StepArgs<VT, XT> a, cudaStream_t s) {
@@ -361,8 +455,16 @@ struct Engine {
     // (two per CTA for FP32 vectors, four per CTA for FP64); below that the
     // persistent pipeline cannot fill and the direct kernel (more, smaller
     // blocks) is faster.  Option 2 takes it wherever planned.
-    const bool tma = L.ntma > 0 && (c->use_tma == 2 || (c->use_tma == 1 && L.ntma >= 4 * c->nsm));
-    if (tma) {
+    if (auto* R = rec()) {  // the persistent kernel runs the direct form
+      CyclePhase<VT, XT> p;
+      p.op = CY_STEP;
+      p.a = a;
+      p.a.slices = nullptr;
+      p.a.nlist = 0;
+      R->push_back(p);
+      return;
+    }
+    if (level_uses_tma(c, L)) {
       // the TMA kernel also runs the slices outside its plan (slice list)
       StepArgs<VT, XT> t = a;
       t.slices = L.ngen > 0 ? L.gen_slices : nullptr;
@@ -371,6 +473,10 @@ struct Engine {
         return;
     }
     launch_step<VT, XT>(a, s);
+  }
+
+  static bool level_uses_tma(const amgps_ctx* c, const Level& L) {
+    return L.ntma > 0 && (c->use_tma == 2 || (c->use_tma == 1 && L.ntma >= 4 * c->nsm));
   }
 
   // One smoother application on level l: x <- S(b, x) (x = 0 when xzero).
@@ -390,7 +496,7 @@ struct Engine {
       XT* oth = xb;
       int j0 = 0;
       if (xzero) {
-        launch_first<XT>(FAM_JAC, L.n, b, md, nullptr, nullptr, cur, XT(0), XT(0), XT(1), s);
+        do_first(FAM_JAC, L.n, b, md, nullptr, nullptr, cur, XT(0), XT(0), XT(1), s);
         j0 = 1;
       }
       for (int j = j0; j < k; ++j) {
@@ -408,7 +514,7 @@ struct Engine {
         ps.done();
         std::swap(cur, oth);
       }
-      if (cur != x) CK(cudaMemcpyAsync(x, cur, L.n * sizeof(XT), cudaMemcpyDeviceToDevice, s));
+      if (cur != x) do_copy(x, cur, L.n, s);
       check_launch();
       return;
     }
@@ -421,7 +527,7 @@ struct Engine {
         c2 *= rhoinv;
         rhoinv = 1.0;
       }
-      launch_first<XT>(cf.fam, L.n, b, md, r, zc, x, XT(c2), XT(cf.beta[1]), XT(rhoinv), s);
+      do_first(cf.fam, L.n, b, md, r, zc, x, XT(c2), XT(cf.beta[1]), XT(rhoinv), s);
       rin_next = (cf.fam == FAM_CHEB4) ? b : r;
     } else {
       StepArgs<VT, XT> a;
@@ -478,7 +584,7 @@ struct Engine {
       rin_next = r;
       std::swap(zc, zn);
     }
-    if (xcur != x) CK(cudaMemcpyAsync(x, xcur, L.n * sizeof(XT), cudaMemcpyDeviceToDevice, s));
+    if (xcur != x) do_copy(x, xcur, L.n, s);
     check_launch();
   }
 
@@ -493,7 +599,7 @@ struct Engine {
       cf.k = c->coarse_sweeps;
       smooth(c, l, cf, b, x, true);
     } else {
-      launch_coarse_gemv<XT>((int)L.n, L.ainv, b, x, c->stream);
+      do_gemv(L, b, x, c->stream);
       check_launch();
     }
   }
@@ -502,6 +608,11 @@ struct Engine {
   static void vcycle_level(amgps_ctx* c, int l, const XT* b, XT* x, bool record = false) {
     Level& L = c->lv[l];
     cudaStream_t s = c->stream;
+    if (!record && !rec() && c->tail_ok && l == c->tail_level && b == (const XT*)L.b &&
+        x == (XT*)L.x) {
+      launch_tail(c);
+      return;
+    }
     if (L.coarsest) {
       coarse_solve(c, l, b, x);
       return;
@@ -525,7 +636,7 @@ struct Engine {
       a.init = true;
       run_step(c, L, a, s);
       if (L.xfer_general) launch_xfer<XT>(L.Rm, (const XT*)L.r, (XT*)C.b, 0, L.rsplit, s);
-      else launch_aggregate<XT>(L.cptr, L.cidx, L.nc, (const XT*)L.r, (XT*)C.b, s);
+      else do_aggregate(L, (const XT*)L.r, (XT*)C.b, s);
       ps.done();
     }
     {
@@ -540,7 +651,7 @@ struct Engine {
       ps.done();
     }
     if (L.xfer_general) launch_xfer<XT>(L.Pm, (const XT*)C.x, x, 1, L.psplit, s);
-    else launch_prolong<XT>(L.n, L.agg, (const XT*)C.x, x, s);
+    else do_prolong(L, (const XT*)C.x, x, s);
     if (record) CK(cudaMemcpyAsync(L.bx2, x, L.n * sizeof(XT), cudaMemcpyDeviceToDevice, s));
     smooth(c, l, cf, b, x, false);
     check_launch();
@@ -697,30 +808,123 @@ struct Engine {
     return st != cudaStreamCaptureStatusNone;
   }
 
-  // Capture levels >= 1 of the V-cycle into a graph (fixed internal buffers).
-  static void build_graph(amgps_ctx* c) {
-    if (c->graph_ok || c->lv.size() < 2) return;
+  static void launch_tail(amgps_ctx* c) {
+    CycleSync sy;
+    sy.count = c->tail_sync;
+    sy.gen = c->tail_sync + 1;
+    CK(cudaMemsetAsync(sy.count, 0, sizeof(unsigned), c->stream));
+    const cudaError_t e = launch_cycle<VT, XT>((const CyclePhase<VT, XT>*)c->tail_dev, c->tail_nph,
+                                               sy, c->tail_grid, c->dscal + S_ERR, c->stream);
+    CK(e);
+  }
+
+  // The persistent kernel takes the levels from the first one (>= 1) that
+  // runs no TMA-fed step down to the coarsest, when all of them use the
+  // direct step, one warp per slice, and aggregation transfers.  Its phase
+  // list is the kernel sequence vcycle_level would launch there, recorded.
+  static void build_tail(amgps_ctx* c) {
+    c->tail_ok = false;
+    const int nl = (int)c->lv.size();
+    if (!c->use_cycle || nl < 3) return;
+    int lt = 1;
+    while (lt < nl - 1 && level_uses_tma(c, c->lv[lt])) ++lt;
+    if (lt >= nl - 1) return;  // only the coarsest level left
+    for (int l = lt; l < nl - 1; ++l) {
+      const Level& L = c->lv[l];
+      if (L.split > 1 || L.xfer_general || level_uses_tma(c, L)) return;
+    }
+    const int grid = cycle_grid<VT, XT>(c->nsm);
+    if (grid <= 0) return;
+    std::vector<CyclePhase<VT, XT>> ph;
+    rec() = &ph;
+    try {
+      vcycle_level(c, lt, (const XT*)c->lv[lt].b, (XT*)c->lv[lt].x);
+    } catch (...) {
+      rec() = nullptr;
+      throw;
+    }
+    rec() = nullptr;
+    const size_t bytes = ph.size() * sizeof(CyclePhase<VT, XT>);
+    if (bytes > c->tail_cap) {
+      if (c->tail_dev) CK(cudaFree(c->tail_dev));
+      c->tail_dev = nullptr;
+      c->tail_cap = 0;
+      CK(cudaMalloc(&c->tail_dev, bytes));
+      c->tail_cap = bytes;
+    }
+    if (!c->tail_sync) {
+      CK(cudaMalloc(&c->tail_sync, 2 * sizeof(unsigned)));
+      CK(cudaMemset(c->tail_sync, 0, 2 * sizeof(unsigned)));
+    }
+    CK(cudaMemcpyAsync(c->tail_dev, ph.data(), bytes, cudaMemcpyHostToDevice, c->stream));
+    c->tail_level = lt;
+    c->tail_nph = (int)ph.size();
+    c->tail_grid = grid;
+    // one trial launch outside any capture: a grid the driver cannot make
+    // co-resident is refused here, and the coarse levels keep their launches
+    // (the trial works on the coarse levels' own buffers, which every
+    // V-cycle overwrites before reading)
+    CycleSync sy;
+    sy.count = c->tail_sync;
+    sy.gen = c->tail_sync + 1;
+    CK(cudaMemsetAsync(sy.count, 0, sizeof(unsigned), c->stream));
+    const cudaError_t e = launch_cycle<VT, XT>((const CyclePhase<VT, XT>*)c->tail_dev, c->tail_nph,
+                                               sy, grid, c->dscal + S_ERR, c->stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    c->tail_ok = true;
+  }
+
+  // Capture levels >= 1 of the V-cycle into c->gexec; the capture's error code.
+  static cudaError_t capture_graph(amgps_ctx* c) {
     if (c->gexec) {
       CK(cudaGraphExecDestroy(c->gexec));
       c->gexec = nullptr;
     }
-    cudaGraph_t g;
+    cudaGraph_t g = nullptr;
     const int64_t before = launches_enqueued();
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = cudaSuccess;
     try {
       vcycle_level(c, 1, (const XT*)c->lv[1].b, (XT*)c->lv[1].x);
-    } catch (...) {
-      cudaGraph_t junk;
-      cudaStreamEndCapture(c->stream, &junk);
-      if (junk) cudaGraphDestroy(junk);
-      cudaGetLastError();
-      throw;
+    } catch (const Fail&) {
+      err = cudaErrorStreamCaptureInvalidated;
     }
-    CK(cudaStreamEndCapture(c->stream, &g));
-    c->graph_kernels = launches_enqueued() - before;
-    c->launch_adjust -= c->graph_kernels;
-    cudaError_t e = cudaGraphInstantiate(&c->gexec, g, 0);
+    const cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+    if (err == cudaSuccess) err = ee;
+    if (err != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return err;
+    }
+    const int64_t captured = launches_enqueued() - before;
+    err = cudaGraphInstantiate(&c->gexec, g, 0);
     cudaGraphDestroy(g);
+    if (err != cudaSuccess) {
+      c->gexec = nullptr;
+      cudaGetLastError();
+      return err;
+    }
+    c->graph_kernels = captured;
+    c->launch_adjust -= captured;
+    return cudaSuccess;
+  }
+
+  // Levels >= 1 of the V-cycle as a CUDA graph (fixed internal buffers),
+  // holding the persistent coarse-level kernel when it is available; if that
+  // kernel cannot be captured, the graph holds the coarse levels' launches.
+  static void build_graph(amgps_ctx* c) {
+    if (c->graph_ok || c->lv.size() < 2) return;
+    if (!capturing(c)) build_tail(c);
+    else c->tail_ok = false;
+    cudaError_t e = capture_graph(c);
+    if (e != cudaSuccess && c->tail_ok) {
+      c->tail_ok = false;
+      e = capture_graph(c);
+    }
     CK(e);
     c->graph_ok = true;
   }
@@ -1086,6 +1290,8 @@ amgps_status amgps_destroy(amgps_ctx* c) {
   if (c->dscal) cudaFree(c->dscal);
   if (c->part) cudaFree(c->part);
   if (c->counters) cudaFree(c->counters);
+  if (c->tail_dev) cudaFree(c->tail_dev);
+  if (c->tail_sync) cudaFree(c->tail_sync);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   if (c->ev_sync) cudaEventDestroy(c->ev_sync);
@@ -1660,7 +1866,8 @@ amgps_status amgps_synchronize(amgps_ctx* c) {
 amgps_status amgps_set_option(amgps_ctx* c, int option, int64_t value) {
   return guard(c, [&] {
     REQ(c, AMGPS_E_ARG, "null context");
-    REQ(option == AMGPS_OPT_TMA || option == AMGPS_OPT_FLEXIBLE || option == AMGPS_OPT_COARSE_SWEEPS,
+    REQ(option == AMGPS_OPT_TMA || option == AMGPS_OPT_FLEXIBLE ||
+            option == AMGPS_OPT_COARSE_SWEEPS || option == AMGPS_OPT_COARSE_KERNEL,
         AMGPS_E_ARG, "unknown option");
     if (option == AMGPS_OPT_TMA) {
       REQ(value >= 0 && value <= 2, AMGPS_E_ARG, "AMGPS_OPT_TMA takes 0, 1 or 2");
@@ -1669,6 +1876,10 @@ amgps_status amgps_set_option(amgps_ctx* c, int option, int64_t value) {
     } else if (option == AMGPS_OPT_FLEXIBLE) {
       REQ(value >= 0 && value <= 2, AMGPS_E_ARG, "AMGPS_OPT_FLEXIBLE takes 0, 1 or 2");
       c->flexible = (int)value;
+    } else if (option == AMGPS_OPT_COARSE_KERNEL) {
+      REQ(value == 0 || value == 1, AMGPS_E_ARG, "AMGPS_OPT_COARSE_KERNEL takes 0 or 1");
+      c->use_cycle = (int)value;
+      c->graph_ok = false;
     } else {
       REQ(value >= 0 && value <= 1000, AMGPS_E_ARG, "AMGPS_OPT_COARSE_SWEEPS takes 0..1000");
       c->coarse_sweeps = (int)value;

@@ -320,12 +320,17 @@ def test_profile_counts(poisson32):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
-def test_tma_step_equals_direct_step(torch_cuda, prec):
+@pytest.mark.parametrize("grid", ["varcoef48", "poisson512"])
+def test_tma_step_equals_direct_step(torch_cuda, prec, grid):
     # the TMA-fed kernel evaluates the same arithmetic in the same order as the
-    # direct-load kernel: results must agree bit for bit
-    from paper_2407_09848_gb300.amgps import Solver
+    # direct-load kernel: results must agree bit for bit (a 512-wide grid plans
+    # its -nx..+nx offsets as one window)
+    from paper_2407_09848_gb300.amgps import Solver, tma_plan_stats
     torch = torch_cuda
-    H = pr.build_hierarchy(pr.varcoef(48, 1.0, 4.0, seed=3, ny=40, nz=36), coarse_max=512)
+    st = (pr.varcoef(48, 1.0, 4.0, seed=3, ny=40, nz=36) if grid == "varcoef48"
+          else pr.poisson(512, 24, 20))
+    H = pr.build_hierarchy(st, coarse_max=512)
+    assert tma_plan_stats(H.levels[0].A, prec)[0] > 0
     S = Solver().load(H.A, H.P, prec=prec)
     rng = np.random.default_rng(12)
     for level in (0, 1):
@@ -485,3 +490,45 @@ def test_more_input_and_option_errors(torch_cuda):
     assert e.value.name == "AMGPS_E_ARG"
     S1.close()
     S.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+def test_coarse_kernel_equals_launches(torch_cuda, prec):
+    """The persistent kernel of the coarse levels gives the bits of their
+    launched kernels: V-cycles of several kinds (and with the coarse-sweeps
+    solver), and a PCG solve's iteration count and iterate.  It really runs:
+    a V-cycle then launches one kernel for all levels below the first."""
+    from paper_2407_09848_gb300.amgps import Solver
+    torch = torch_cuda
+    # 43,200 rows: no level is large enough for the TMA-fed step, so every
+    # level below the first runs in the persistent kernel
+    H = pr.build_hierarchy(pr.varcoef(40, 1.0, 4.0, seed=5, ny=36, nz=30), coarse_max=64)
+    assert H.n_levels >= 4
+    on, off = Solver().load(H.A, H.P, prec=prec), Solver().load(H.A, H.P, prec=prec)
+    on.set_coarse_kernel(True)
+    off.set_coarse_kernel(False)
+    n = H.A[0].shape[0]
+    r = to_dev(torch, pr.rhs_uniform(n, seed=8))
+    for kind, k, sweeps in [("cheb4_opt", 4, 0), ("cheb1_opt", 3, 0), ("l1jacobi", 2, 0),
+                            ("cheb4", 2, 30)]:
+        zs = []
+        for S in (on, off):
+            S.set_smoother(-1, kind, k)
+            S.set_coarse_sweeps(sweeps)
+            z = torch.empty(n, dtype=torch.float64, device="cuda")
+            S.vcycle(r, z)       # builds the graph (and the persistent kernel)
+            S.profile_read(3, reset=True)
+            S.vcycle(r, z)
+            torch.cuda.synchronize()
+            zs.append((z, S.profile_read(3, reset=True)[0]))
+        assert torch.equal(zs[0][0], zs[1][0]), (prec, kind, k, sweeps)
+        assert zs[0][1] < zs[1][1], (zs[0][1], zs[1][1])
+    for S in (on, off):
+        S.set_smoother(-1, "cheb4_opt", 4)
+        S.set_coarse_sweeps(0)
+    xs = []
+    for S in (on, off):
+        x = torch.empty(n, dtype=torch.float64, device="cuda")
+        it, rel = S.pcg(r, x, rtol=1e-8)
+        xs.append((it, rel, x))
+    assert xs[0][0] == xs[1][0] and xs[0][1] == xs[1][1] and torch.equal(xs[0][2], xs[1][2])

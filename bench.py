@@ -442,19 +442,34 @@ def run_learned_c4(a, torch, cpu=True):
         S64 = Solver().load(H.A, H.P, prec="f64")
         feats = learn.level_features(S64, H)
         betas = net.predict(feats)
-        safe = [learn.is_safe(bb) for bb in betas]
+        ref = learn.amgps.opt4_weights(4)
+        safe = [learn.make_safe(bb, ref) for bb in betas]
+        # the optimal weights judge the network on this hierarchy (set-up)
+        t0 = time.perf_counter()
+        used, rho_l, rho_o, keep = learn.judge(S64, betas)
+        t_judge = time.perf_counter() - t0
         x = torch.empty_like(bd)
-        row = {"learned_weights": [list(map(float, bb)) for bb in betas], "safe": safe}
+        row = {"predicted_weights": [list(map(float, bb)) for bb in betas],
+               "safe_weights": [list(map(float, w)) for w, _ in safe],
+               "t_towards_prediction": [float(t) for _, t in safe],
+               "judge": {"pcg_factor_learned": rho_l, "pcg_factor_optimal": rho_o,
+                         "learned_kept": bool(keep), "setup_s": round(t_judge, 3)},
+               "used_weights": [list(map(float, w)) for w in used]}
+        S64.set_smoother(-1, "cheb4_opt", 4)
         it, ms, rel = timed_solve(S64, bd, x, a.rtol, torch)
         row["f64_opt"] = {"iterations": it, "ms": round(ms, 3), "relres": rel}
+        # the network's safe weights without the judge, for the record
+        for l, (w, _) in enumerate(safe):
+            S64.set_smoother(l, "weights", 4, weights=w)
+        it, ms, rel = timed_solve(S64, bd, x, a.rtol, torch)
+        row["f64_learned_unjudged"] = {"iterations": it, "ms": round(ms, 3), "relres": rel}
         S64.close()
         for prec in ("bf16", "f32"):
             S = Solver().load(H.A, H.P, prec=prec)
             it, ms, rel = timed_solve(S, bd, x, a.rtol, torch)
             row[f"{prec}_opt"] = {"iterations": it, "ms": round(ms, 3), "relres": rel}
-            ref = learn.amgps.opt4_weights(4)
-            for l, bb in enumerate(betas):
-                S.set_smoother(l, "weights", 4, weights=bb if safe[l] else ref)
+            for l, w in enumerate(used):
+                S.set_smoother(l, "weights", 4, weights=w)
             it, ms, rel = timed_solve(S, bd, x, a.rtol, torch)
             row[f"{prec}_learned"] = {"iterations": it, "ms": round(ms, 3), "relres": rel}
             S.close()

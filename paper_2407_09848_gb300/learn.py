@@ -46,12 +46,38 @@ def is_safe(beta):
     return bool(np.all(np.abs(p_weights(beta, _GRID)) < 1.0))
 
 
+SAFE_BACKOFF = 0.95
+
+
+def make_safe(beta, ref):
+    """(weights, t): the prediction itself (t = 1) when its polynomial stays in
+    Pi_k, else the point beta_ref + t (beta - beta_ref) of the segment towards
+    the optimal weights, t = 0.95 t_max with t_max the largest t (bisection)
+    whose polynomial stays in Pi_k on the check grid (t = 0, the optimal
+    weights, is inside by Proposition 1's bound)."""
+    beta = np.asarray(beta, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    if is_safe(beta):
+        return beta, 1.0
+    lo, hi = 0.0, 1.0
+    for _ in range(40):
+        mid = 0.5 * (lo + hi)
+        if is_safe(ref + mid * (beta - ref)):
+            lo = mid
+        else:
+            hi = mid
+    t = SAFE_BACKOFF * lo
+    return ref + t * (beta - ref), t
+
+
 def level_features(solver, H, degree=DEGREE):
-    """8 features per non-coarsest level: degree, level size, depth, the
-    l1-Jacobi spectral estimate (10 power steps on the GPU), and coefficient
-    statistics of the level matrix (contrast of the diagonal, diagonal share
-    of the l1 row sum, spread of the log-diagonal, strongest-coupling share of
-    the off-diagonal row sum)."""
+    """8 features per non-coarsest level: degree, level size, mean stored
+    entries per row, the l1-Jacobi spectral estimate (10 power steps on the
+    GPU), and coefficient statistics of the level matrix (contrast of the
+    diagonal, diagonal share of the l1 row sum, spread of the log-diagonal,
+    strongest-coupling share of the off-diagonal row sum).  No feature counts
+    levels: a level of a large grid then looks like the level of a smaller
+    training grid that has its size and coefficients."""
     import scipy.sparse as sp
     import torch
     rows = []
@@ -65,7 +91,7 @@ def level_features(solver, H, degree=DEGREE):
         offmax = np.asarray((absA - sp.diags(np.abs(d))).max(axis=1).todense()).ravel()
         v0 = torch.from_numpy(pr.vec_uniform(n, seed=0)).cuda()
         lam = solver.estimate_lambda(l, v0, iters=10)
-        rows.append([degree / 8.0, np.log2(n) / 24.0, l / 8.0, lam,
+        rows.append([degree / 8.0, np.log2(n) / 24.0, A.nnz / n / 8.0, lam,
                      np.log10(d.max() / d.min()) / 4.0, float(np.mean(d / M)),
                      float(np.std(np.log(d))) / 2.0,
                      float(np.mean(offmax / np.maximum(offsum, 1e-300)))])
@@ -154,24 +180,73 @@ class Problem:
         self.pre_cycles = pre_cycles
 
     def set_weights(self, betas):
-        used = []
+        """Installs make_safe of each level's prediction; returns the t's."""
+        ts = []
         ref = amgps.opt4_weights(DEGREE)
         for l, b in enumerate(betas):
-            ok = is_safe(b)
-            w = b if ok else ref
+            w, t = make_safe(b, ref)
             self.S.set_smoother(l, "weights", DEGREE, weights=w)
-            used.append(ok)
-        return used
+            ts.append(t)
+        return ts
 
     def loss_grad(self, betas):
-        used = self.set_weights(betas)
+        ts = self.set_weights(betas)
         E = self.E0.clone()
         if self.pre_cycles:
             self.S.error_cycles(E, self.pre_cycles)
         loss, gw = self.S.loss_grad(E)
-        g = gw[:, :DEGREE].copy()
-        g[~np.asarray(used)] = 0.0  # a level that fell back does not depend on the network
+        # the installed weights are ref + t (beta - ref): d/dbeta = t, with t
+        # held at its value (t = 0: the level does not depend on the network)
+        g = gw[:, :DEGREE] * np.asarray(ts)[:, None]
         return loss, g
+
+
+def convergence_estimate(solver, weights, E0, cycles=PRE_CYCLES):
+    """Squared-convergence-factor estimate of the V-cycle with `weights` per
+    level (degree 4): the one-cycle A-norm error reduction of the vectors E0
+    (m x n_0, on the GPU, left unchanged) after `cycles` V-cycles."""
+    for l, w in enumerate(weights):
+        solver.set_smoother(l, "weights", DEGREE, weights=w)
+    E = E0.clone()
+    if cycles:
+        solver.error_cycles(E, cycles)
+    return solver.loss_grad(E)[0]
+
+
+JUDGE_ITERS = 12
+
+
+def pcg_factor(solver, weights, b, iters=JUDGE_ITERS):
+    """Mean residual reduction per iteration of `iters` PCG iterations
+    (||r_m|| / ||b||)^(1/m) on the FP64 hierarchy with `weights` per level."""
+    import torch
+    for l, w in enumerate(weights):
+        solver.set_smoother(l, "weights", DEGREE, weights=w)
+    x = torch.empty_like(b)
+    it, rel = solver.pcg(b, x, rtol=1e-300, maxit=iters, raise_on_noconv=False)
+    return rel ** (1.0 / max(it, 1))
+
+
+def judge(solver, betas, seed=7, iters=JUDGE_ITERS):
+    """The optimal 4th-kind weights as judge of the network (set-up, FP64
+    hierarchy): the predicted weights (made safe level by level) are kept only
+    when PCG preconditioned by their V-cycle reduces the residual of a seeded
+    U[-1,1] right-hand side faster, over the same `iters` iterations, than
+    with the optimal weights.  PCG convergence follows the spread of the
+    preconditioned spectrum, which the one-cycle error reduction (the
+    training loss) does not measure: a smoother that over-corrects some modes
+    can have the larger error-propagation norm and still give PCG the smaller
+    condition number.  Returns (weights per level, learned factor, optimal
+    factor, learned kept)."""
+    import torch
+    ref = amgps.opt4_weights(DEGREE)
+    learned = [make_safe(b, ref)[0] for b in betas]
+    n = solver.level_info(0)[0]
+    b = torch.from_numpy(pr.vec_uniform(n, seed=seed)).cuda()
+    f_l = pcg_factor(solver, learned, b, iters)
+    f_o = pcg_factor(solver, [ref] * len(betas), b, iters)
+    keep = f_l < f_o
+    return (learned if keep else [ref] * len(betas)), f_l, f_o, keep
 
 
 def make_training_set(count, grid, seed0=0, nvec=32):

@@ -77,14 +77,21 @@ def test_loss_grad_matches_oracle(torch_cuda):
 def test_safety_fallback_and_checkpoint(torch_cuda, tmp_path):
     from paper_2407_09848_gb300 import amgps, learn
     assert learn.is_safe(amgps.opt4_weights(4))
-    assert not learn.is_safe(np.array([3.0, 3.0, 3.0, 3.0]))
+    bad = np.array([3.0, 3.0, 3.0, 3.0])
+    assert not learn.is_safe(bad)
+    w, t = learn.make_safe(bad, amgps.opt4_weights(4))
+    assert 0.0 < t < 1.0 and learn.is_safe(w)
+    assert np.allclose(w, amgps.opt4_weights(4) + t * (bad - amgps.opt4_weights(4)))
     H = pr.build_hierarchy(pr.varcoef(12, 1.0, 3.0, seed=5), coarse_max=30)
     p = learn.Problem(H, nvec=4, seed=1, pre_cycles=0)
     ref = amgps.opt4_weights(4)
     nl = H.n_levels - 1
     l_ref, _ = p.loss_grad([ref] * nl)
-    l_bad, g_bad = p.loss_grad([np.array([3.0, 3.0, 3.0, 3.0])] * nl)
-    assert l_bad == l_ref and np.all(g_bad == 0)   # unsafe weights fall back
+    # unsafe weights are pulled back towards the optimal ones; the gradient
+    # in the prediction is the installed weights' gradient times t
+    l_bad, g_bad = p.loss_grad([bad] * nl)
+    l_w, g_w = p.loss_grad([w] * nl)
+    assert l_bad == l_w and np.allclose(g_bad, t * g_w, rtol=1e-12, atol=0)
     net = learn.WeightMLP(seed=1)
     probs = [p, learn.Problem(pr.build_hierarchy(pr.varcoef(12, 1.5, 4.0, seed=6), coarse_max=30),
                               nvec=4, seed=2)]
@@ -133,3 +140,28 @@ def test_trained_network_gain_over_optimal_weights(torch_cuda):
           f"(gain {100 * gain:.2f}%); training loss {hist[0]:.5f} -> {hist[-1]:.5f}")
     assert hist[-1] < hist[0]
     assert after < ref
+
+
+def test_optimal_weights_judge_the_network(torch_cuda):
+    # set-up judge: the network's (safe) weights are kept exactly when PCG
+    # with their V-cycle reduces the residual faster over the judge's
+    # iterations than with the optimal weights; a smoother that barely
+    # smooths (beta = 0.1) must lose
+    from paper_2407_09848_gb300 import amgps, learn
+    from paper_2407_09848_gb300.amgps import Solver
+    H = pr.build_hierarchy(pr.varcoef(24, 1.5, 4.0, seed=9), coarse_max=100)
+    S = Solver().load(H.A, H.P)
+    nl = H.n_levels - 1
+    ref = amgps.opt4_weights(4)
+    b = torch_cuda.from_numpy(pr.vec_uniform(H.A[0].shape[0], seed=7)).cuda()
+    fo = learn.pcg_factor(S, [ref] * nl, b)
+    assert 0.0 < fo < 1.0
+    for cand in (np.full(4, 0.1), np.full(4, 0.5), np.array([1.0, 1.1, 1.2, 1.6])):
+        assert learn.is_safe(cand)
+        used, fl, fo2, keep = learn.judge(S, [cand] * nl)
+        assert fo2 == fo and keep == (fl < fo)
+        assert all(np.array_equal(u, cand if keep else ref) for u in used)
+        if cand[0] == 0.1:
+            assert not keep and fl > fo
+    used, fl, fo2, keep = learn.judge(S, [ref] * nl)  # equal factors: not kept
+    assert fl == fo2 == fo and not keep

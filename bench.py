@@ -63,6 +63,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the mixed-precision (192^3) and learned+mixed (256^3) comparisons")
+    ap.add_argument("--cpu-oracle", default=None, help=argparse.SUPPRESS)
     return ap.parse_args(argv)
 
 
@@ -257,6 +258,42 @@ def time_omp_solves(ora, b, rtol, count, warmup=1, budget_s=30.0):
     return times, it, rel
 
 
+def problem_stencil(spec):
+    """The seeded stencil of a problem spec (dict): poisson / varcoef / aniso."""
+    from paper_2407_09848_gb300 import problems as pr
+    if spec["problem"] == "poisson":
+        return pr.poisson(spec["grid"])
+    if spec["problem"] == "varcoef":
+        return pr.varcoef(spec["grid"], spec["sigma"], spec["ell"], seed=spec.get("seed", 0))
+    return pr.aniso(spec["grid"], spec["eps"])
+
+
+def cpu_oracle_main(spec):
+    """Entry of the CPU-oracle subprocess (--cpu-oracle): builds the problem
+    of `spec` and prints cpu_oracle_baseline's dict as one JSON line.  A fresh
+    interpreter that never imports torch or initialises CUDA, so the OpenMP
+    pool spans every host core, as in the reference arm."""
+    from paper_2407_09848_gb300 import problems as pr
+    H = pr.build_hierarchy(problem_stencil(spec), coarse_max=512)
+    b = pr.rhs_uniform(H.levels[0].A.shape[0], seed=0)
+    specs = oracle_specs(H, spec["kind"], spec["degree"])
+    out = cpu_oracle_baseline(H.A, H.P, specs, b, spec["rtol"], spec["label"],
+                              count=spec.get("count", 3), warmup=spec.get("warmup", 1))
+    print(json.dumps(out))
+    return 0
+
+
+def cpu_oracle_subprocess(spec, timeout=900):
+    """cpu_oracle_baseline of `spec` run in a spawned interpreter (see
+    cpu_oracle_main); None with the reason when it fails."""
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-oracle", json.dumps(spec)],
+                       capture_output=True, text=True, timeout=timeout, cwd=ROOT)
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    if r.returncode != 0 or not lines:
+        return {"unavailable": f"CPU oracle subprocess rc={r.returncode}: {r.stderr[-300:]}"}
+    return json.loads(lines[-1])
+
+
 def cpu_oracle_baseline(A, P, specs, b, rtol, label, count=3, warmup=1):
     """CPU baseline: median of whole solves by the all-core C oracle build,
     plus its single-thread time for one PCG iteration scaled by the iteration
@@ -339,7 +376,6 @@ def run_mixed_c2(a, torch, cpu=True):
     each with the level-0 step's HBM roofline, and the all-core C oracle's
     FP64 solve of the same system."""
     import numpy as np
-    from oracle.smoother import SmootherSpec
     from paper_2407_09848_gb300 import problems as pr
     from paper_2407_09848_gb300.amgps import Solver
     H = pr.build_hierarchy(pr.varcoef(192, 1.0, 8.0, seed=0), coarse_max=512)
@@ -360,10 +396,10 @@ def run_mixed_c2(a, torch, cpu=True):
                                                         "varcoef192^3_cheb4_opt_k4", prec)}
         S.close()
     if cpu:
-        out["cpu_oracle_f64"] = cpu_oracle_baseline(H.A, H.P, [SmootherSpec("cheb4_opt", 4)] *
-                                                    (H.n_levels - 1), b, a.rtol,
-                                                    "the 192^3 variable-coefficient system",
-                                                    count=1, warmup=0)
+        out["cpu_oracle_f64"] = cpu_oracle_subprocess(
+            {"problem": "varcoef", "grid": 192, "sigma": 1.0, "ell": 8.0, "kind": "cheb4_opt",
+             "degree": 4, "rtol": a.rtol, "label": "the 192^3 variable-coefficient system",
+             "count": 1, "warmup": 0})
     return {"workload": "varcoef192^3 sigma1 ell8, CHEB4_OPT k4, rtol 1e-8", **out}
 
 
@@ -426,7 +462,6 @@ def run_learned_c4(a, torch, cpu=True):
     BF16 / FP32 values (FP64 PCG and coarse solve), and the all-core C
     oracle's FP64 solve with the optimal weights."""
     import numpy as np
-    from oracle.smoother import SmootherSpec
     from paper_2407_09848_gb300 import learn
     from paper_2407_09848_gb300 import problems as pr
     from paper_2407_09848_gb300.amgps import Solver
@@ -475,9 +510,12 @@ def run_learned_c4(a, torch, cpu=True):
             S.close()
         row["speedup_bf16_learned_vs_f64_opt"] = round(row["f64_opt"]["ms"] / row["bf16_learned"]["ms"], 3)
         if cpu:
-            row["cpu_oracle_f64_opt"] = cpu_oracle_baseline(
-                H.A, H.P, [SmootherSpec("cheb4_opt", 4)] * (H.n_levels - 1), b, a.rtol,
-                f"the 256^3 {name} system", count=1, warmup=0)
+            pspec = ({"problem": "varcoef", "grid": 256, "sigma": 2.0, "ell": 16.0}
+                     if name.startswith("lognormal") else {"problem": "aniso", "grid": 256,
+                                                           "eps": 1e-3})
+            row["cpu_oracle_f64_opt"] = cpu_oracle_subprocess(
+                {**pspec, "kind": "cheb4_opt", "degree": 4, "rtol": a.rtol,
+                 "label": f"the 256^3 {name} system", "count": 1, "warmup": 0})
         res[name] = row
     return res
 
@@ -709,8 +747,9 @@ def run_ours(a):
     # ---- CPU baseline: the all-core C oracle build on the same solve ----
     cpu = None
     if not a.no_cpu and rank == 0:
-        cpu = cpu_oracle_baseline(H.A, H.P, oracle_specs(H, a.kind, a.degree), b, a.rtol,
-                                  workload_name(a))
+        cpu = cpu_oracle_subprocess({"problem": "poisson", "grid": a.grid, "kind": a.kind,
+                                     "degree": a.degree, "rtol": a.rtol,
+                                     "label": workload_name(a), "count": 3, "warmup": 1})
 
     out = {"metric": METRIC, "value": ms_per, "unit": "ms", "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms_per, "higher_is_better": False,
@@ -738,6 +777,8 @@ def run_ours(a):
 
 def main():
     a = parse_args()
+    if a.cpu_oracle:
+        return cpu_oracle_main(json.loads(a.cpu_oracle))
     if a.impl == "reference":
         return run_reference(a)
     return run_ours(a)

@@ -128,3 +128,15 @@ def test_reference_arm_line_has_the_workload_config(capsys):
     assert line["impl"] == "reference" and line["config"] == bench.workload_config(args, H)
     assert line["steps"] == 2 and line["value"] == line["ms_per_step"] > 0
     assert line["result"]["converged"] and line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_cpu_oracle_runs_in_a_fresh_interpreter():
+    # the bench's CPU baselines run in a spawned interpreter that imports no
+    # torch, so the OpenMP pool is the host's whole core set
+    sys.path.insert(0, ROOT)
+    import bench
+    out = bench.cpu_oracle_subprocess({"problem": "poisson", "grid": 16, "kind": "cheb4_opt",
+                                       "degree": 4, "rtol": 1e-8, "label": "16^3", "count": 1,
+                                       "warmup": 0})
+    assert out["kind"] == "oracle" and out["iterations"] > 0 and out["value"] > 0
+    assert out["cores"] == len(os.sched_getaffinity(0))

@@ -184,7 +184,7 @@ struct amgps_ctx {
   int tail_grid = 0;               // co-resident blocks
   void* tail_dev = nullptr;        // CyclePhase<VT, XT>[tail_cap] on the device
   size_t tail_cap = 0;             // bytes
-  unsigned* tail_sync = nullptr;   // barrier words: count, generation
+  unsigned* tail_sync = nullptr;   // barrier word (arrivals)
   double prof_ms[5] = {};
   double prof_bytes[5] = {};
 };
@@ -259,11 +259,11 @@ void leave(amgps_ctx* c) {
   CK(cudaStreamWaitEvent(c->ustream, c->ev_out, 0));
 }
 
-RedWork redwork(amgps_ctx* c, int slot, int64_t work) {
+RedWork redwork(amgps_ctx* c, int slot, int64_t work, int per_sm = 4) {
   RedWork w;
   w.part = c->part;
   w.counter = c->counters + slot;
-  w.grid = reduction_grid(work, c->nsm);
+  w.grid = reduction_grid(work, c->nsm, per_sm);
   return w;
 }
 
@@ -811,7 +811,6 @@ struct Engine {
   static void launch_tail(amgps_ctx* c) {
     CycleSync sy;
     sy.count = c->tail_sync;
-    sy.gen = c->tail_sync + 1;
     CK(cudaMemsetAsync(sy.count, 0, sizeof(unsigned), c->stream));
     const cudaError_t e = launch_cycle<VT, XT>((const CyclePhase<VT, XT>*)c->tail_dev, c->tail_nph,
                                                sy, c->tail_grid, c->dscal + S_ERR, c->stream);
@@ -819,7 +818,7 @@ struct Engine {
   }
 
   // The persistent kernel takes the levels from the first one (>= 1) that
-  // runs no TMA-fed step down to the coarsest, when all of them use the
+  // runs no TMA-fed step and has at most kCycleMaxRows rows down to the coarsest, when all of them use the
   // direct step, one warp per slice, and aggregation transfers.  Its phase
   // list is the kernel sequence vcycle_level would launch there, recorded.
   static void build_tail(amgps_ctx* c) {
@@ -827,7 +826,7 @@ struct Engine {
     const int nl = (int)c->lv.size();
     if (!c->use_cycle || nl < 3) return;
     int lt = 1;
-    while (lt < nl - 1 && level_uses_tma(c, c->lv[lt])) ++lt;
+    while (lt < nl - 1 && (level_uses_tma(c, c->lv[lt]) || c->lv[lt].n > kCycleMaxRows)) ++lt;
     if (lt >= nl - 1) return;  // only the coarsest level left
     for (int l = lt; l < nl - 1; ++l) {
       const Level& L = c->lv[l];
@@ -853,8 +852,8 @@ struct Engine {
       c->tail_cap = bytes;
     }
     if (!c->tail_sync) {
-      CK(cudaMalloc(&c->tail_sync, 2 * sizeof(unsigned)));
-      CK(cudaMemset(c->tail_sync, 0, 2 * sizeof(unsigned)));
+      CK(cudaMalloc(&c->tail_sync, sizeof(unsigned)));
+      CK(cudaMemset(c->tail_sync, 0, sizeof(unsigned)));
     }
     CK(cudaMemcpyAsync(c->tail_dev, ph.data(), bytes, cudaMemcpyHostToDevice, c->stream));
     c->tail_level = lt;
@@ -866,7 +865,6 @@ struct Engine {
     // V-cycle overwrites before reading)
     CycleSync sy;
     sy.count = c->tail_sync;
-    sy.gen = c->tail_sync + 1;
     CK(cudaMemsetAsync(sy.count, 0, sizeof(unsigned), c->stream));
     const cudaError_t e = launch_cycle<VT, XT>((const CyclePhase<VT, XT>*)c->tail_dev, c->tail_nph,
                                                sy, grid, c->dscal + S_ERR, c->stream);
@@ -1021,7 +1019,8 @@ void fcg1_impl(amgps_ctx* c, const double* b, double* x, double rtol, int maxit,
   cudaStream_t s = c->stream;
   const int64_t n = L.n;
   const DevMat<double> A = devmat64(L, c->prec);
-  RedWork rw_dot = redwork(c, 0, n), rw_spmv = redwork(c, 1, n), rw_upd = redwork(c, 2, n);
+  RedWork rw_dot = redwork(c, 0, n, kRedBlocksPerSm), rw_spmv = redwork(c, 1, n),
+          rw_upd = redwork(c, 2, n, kRedBlocksPerSm);
   rw_spmv.grid = reduction_grid(L.nslices * kSlice, c->nsm);
   double *z = c->pz, *w = c->pz2, *p = c->pp, *q = c->pq;
   CK(cudaMemcpyAsync(c->pr, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1084,7 +1083,8 @@ void pcg_impl(amgps_ctx* c, const double* b, double* x, double rtol, int maxit, 
   cudaStream_t s = c->stream;
   const int64_t n = L.n;
   const DevMat<double> A = devmat64(L, c->prec);
-  RedWork rw_dot = redwork(c, 0, n), rw_spmv = redwork(c, 1, n), rw_upd = redwork(c, 2, n);
+  RedWork rw_dot = redwork(c, 0, n, kRedBlocksPerSm), rw_spmv = redwork(c, 1, n),
+          rw_upd = redwork(c, 2, n, kRedBlocksPerSm);
   rw_spmv.grid = reduction_grid(L.nslices * kSlice, c->nsm);
   CK(cudaMemcpyAsync(c->pr, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
@@ -1264,7 +1264,7 @@ amgps_status amgps_create(amgps_ctx** out, int device, void* user_stream) {
     CK(cudaMallocHost(&u->hscal, S_COUNT * sizeof(double)));
     CK(cudaMalloc(&u->ddots, kDotSlots * sizeof(double)));
     CK(cudaMallocHost(&u->hdots, kDotSlots * sizeof(double)));
-    const int maxgrid = u->nsm * 4;
+    const int maxgrid = u->nsm * kRedBlocksPerSm;
     CK(cudaMalloc(&u->part, (size_t)maxgrid * 3 * sizeof(double)));  // grid_sum3: 3 x grid
     CK(cudaMalloc(&u->counters, 8 * sizeof(unsigned)));
     CK(cudaMemset(u->counters, 0, 8 * sizeof(unsigned)));

@@ -15,9 +15,9 @@ std::atomic<int64_t> g_launches{0};
 int64_t launches_enqueued() { return g_launches.load(std::memory_order_relaxed); }
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-int reduction_grid(int64_t work_items, int nsm) {
+int reduction_grid(int64_t work_items, int nsm, int per_sm) {
   int64_t g = (work_items + kBlock - 1) / kBlock;
-  const int64_t cap = (int64_t)nsm * 4;
+  const int64_t cap = (int64_t)nsm * per_sm;
   if (g > cap) g = cap;
   if (g < 1) g = 1;
   return (int)g;

@@ -58,6 +58,10 @@ template <class XT>
 void launch_norm2(int64_t n, const XT* v, const RedWork& rw, double* scal, int slot,
                   cudaStream_t s);
 
-int reduction_grid(int64_t work_items, int nsm);
+// Blocks of a grid-stride reduction over work_items: enough for the items,
+// at most per_sm per SM (kRedBlocksPerSm for the streaming vector kernels,
+// whose registers allow a full SM; 4 for the SpMV-class ones)
+constexpr int kRedBlocksPerSm = 8;
+int reduction_grid(int64_t work_items, int nsm, int per_sm = 4);
 
 }  // namespace amgps

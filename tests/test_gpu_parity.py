@@ -532,3 +532,29 @@ def test_coarse_kernel_equals_launches(torch_cuda, prec):
         it, rel = S.pcg(r, x, rtol=1e-8)
         xs.append((it, rel, x))
     assert xs[0][0] == xs[1][0] and xs[0][1] == xs[1][1] and torch.equal(xs[0][2], xs[1][2])
+
+
+def test_coarse_kernel_option_falls_back_on_general_transfers(torch_cuda):
+    """A smoothed-aggregation hierarchy (general P, stored transfers) is not
+    taken by the persistent kernel: with the option on, the V-cycle keeps its
+    launches and gives the same bits and the same launch count."""
+    from oracle.sa import sa_hierarchy
+    from paper_2407_09848_gb300.amgps import Solver
+    torch = torch_cuda
+    st = pr.poisson(24, 20, 18)
+    A0 = pr.to_csr(st)
+    levels = pr.geometric_aggregates(st.shape, coarse_max=60)
+    As, Ps, _ = sa_hierarchy(A0, [lv[0] for lv in levels], [lv[1] for lv in levels])
+    on, off = Solver().load(As, Ps), Solver().load(As, Ps)
+    on.set_coarse_kernel(True)
+    n = A0.shape[0]
+    r = to_dev(torch, pr.rhs_uniform(n, seed=2))
+    out = []
+    for S in (on, off):
+        z = torch.empty(n, dtype=torch.float64, device="cuda")
+        S.vcycle(r, z)
+        S.profile_read(3, reset=True)
+        S.vcycle(r, z)
+        torch.cuda.synchronize()
+        out.append((z, S.profile_read(3, reset=True)[0]))
+    assert torch.equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]

@@ -214,11 +214,13 @@ struct CyclePhase {
   XT c2 = 0, beta = 0, rhoinv = 1;
 };
 
-// grid-barrier words: arrivals (zeroed before each launch) and generation
+// grid-barrier word: arrivals, zeroed before each launch
 struct CycleSync {
   unsigned* count = nullptr;
-  unsigned* gen = nullptr;
 };
+// the persistent kernel takes levels of at most this many rows (larger ones
+// keep their launches, whose grids hold more warps in flight)
+constexpr int64_t kCycleMaxRows = 65536;
 
 // Blocks of the persistent launch: all co-resident (occupancy x SMs, at most
 // kCycleMaxBlocksPerSm per SM); 0 when the kernel cannot run.

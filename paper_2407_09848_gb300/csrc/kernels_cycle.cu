@@ -22,7 +22,7 @@ namespace {
 
 constexpr int kCycleThreads = 512;
 constexpr int kCycleMaxBlocksPerSm = 1;
-constexpr uint32_t kBarrierSpins = 1u << 22;  // x ~0.1-0.5 us per poll
+constexpr uint32_t kBarrierSpins = 1u << 22;  // L2 polls (~0.5 us each): about two seconds at most
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
@@ -30,26 +30,22 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   return v;
 }
 
-// All blocks of the grid meet; false if this block's wait gave up.
-__device__ bool grid_barrier(const CycleSync& sy, unsigned nblocks) {
+// All blocks of the grid meet for the q-th time (q = 1, 2, ...): one
+// arrival counter that only grows (zeroed before the launch); a block's
+// thread 0 publishes the block's writes (fence, then its arrival) and waits
+// until the counter reaches q x blocks.  False if this block's wait gave up.
+__device__ bool grid_barrier(const CycleSync& sy, unsigned target) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
-    const unsigned g = ld_acquire(sy.gen);  // cannot advance before this block arrives
     __threadfence();
-    if (atomicAdd(sy.count, 1u) == nblocks - 1) {
-      atomicExch(sy.count, 0u);
-      __threadfence();
-      atomicAdd(sy.gen, 1u);
-    } else {
-      uint32_t i = 0;
-      while (ld_acquire(sy.gen) == g) {
-        if (++i > kBarrierSpins) {
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
+    atomicAdd(sy.count, 1u);
+    uint32_t i = 0;
+    while (ld_acquire(sy.count) < target) {
+      if (++i > kBarrierSpins) {
+        ok = 0;
+        break;
       }
     }
     __threadfence();
@@ -158,7 +154,7 @@ __global__ void __launch_bounds__(kCycleThreads, kCycleMaxBlocksPerSm)
         for (int64_t i = gt; i < P.n; i += nt) P.out0[i] = __ldcg(P.in0 + i);
     }
     // the next phase reads what this one wrote (and overwrites P)
-    if (!grid_barrier(sy, gridDim.x)) {
+    if (!grid_barrier(sy, (unsigned)(q + 1) * gridDim.x)) {
       if (threadIdx.x == 0) *err = 1.0;
       return;
     }

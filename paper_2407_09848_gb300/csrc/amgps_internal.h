@@ -96,8 +96,9 @@ constexpr int kMaxSplit = 32;
 // copies keep the TMA unit streaming.  The launch shape depends on the vector
 // type:
 //   FP64: 480-row tiles (15 slices), one CTA per SM of 1 producer warp and two
-//     groups of 15 consumer warps taking alternate tiles (992 threads), with
-//     up to 225 KB of stages -- four in flight, so a tile's copies are issued
+//     groups of 8 consumer warps taking alternate tiles (544 threads; a lane
+//     evaluates two rows of a 7-point tile, slices cw and cw + 8), with up
+//     to 225 KB of stages -- four in flight, so a tile's copies are issued
 //     three tiles ahead of the FP64-bound consumers;
 //   FP32/BF16: 1024-row tiles (32 slices), two CTAs per SM, each 1 producer
 //     warp and one group of 16 consumer warps, up to 112.5 KB of stages.
@@ -112,7 +113,7 @@ struct TmaShape {  // FP32 vectors (FP32 and BF16 levels)
 };
 template <>
 struct TmaShape<double> {
-  static constexpr int kRows = 480, kGroups = 2, kConsumers = 15, kCtasPerSm = 1;
+  static constexpr int kRows = 480, kGroups = 2, kConsumers = 8, kCtasPerSm = 1;
   static constexpr int kSmemBudget = 230400;
   static constexpr int kVecSlots = 2;
 };

@@ -210,9 +210,9 @@ def test_protocol_is_safe(ns, groups):
 
 
 def test_kernel_shapes():
-    # FP64: two groups of 15 warps and four stages; FP32 vectors: one group of
+    # FP64: two groups of 8 warps and four stages; FP32 vectors: one group of
     # 16 warps, two stages; BF16 levels plan five or six
-    for ns, groups, consumers in ((4, 2, 15), (2, 1, 16), (5, 1, 16), (6, 1, 16)):
+    for ns, groups, consumers in ((4, 2, 8), (2, 1, 16), (5, 1, 16), (6, 1, 16)):
         for seed in range(10):
             run_cta(3 * ns + 2, ns, groups, consumers, seed)
 

@@ -315,9 +315,16 @@ amgps_status amgps_synchronize(amgps_ctx* ctx);
  * kernels' work) when they use aggregation transfers and one warp per slice;
  * 0 launches their kernels one by one (inside the CUDA graph of the coarse
  * levels).  Results are identical either way.  A barrier wait that gives up
- * is reported by the next amgps_pcg as AMGPS_E_TIMEOUT. */
+ * is reported by the next amgps_pcg as AMGPS_E_TIMEOUT.
+ * AMGPS_OPT_ALLOC_LIMIT (default 0 = none): the most bytes of device memory
+ * the context may allocate for a hierarchy and its work vectors (the
+ * buffers of amgps_hierarchy_load and of the reverse-mode calls).  A request
+ * that would pass it fails with AMGPS_E_NOMEM before reaching the CUDA
+ * allocator, so a caller can reject a problem that would not fit its memory
+ * share.  Any failed amgps_hierarchy_load leaves no hierarchy loaded and
+ * keeps none of its buffers. */
 enum { AMGPS_OPT_TMA = 1, AMGPS_OPT_FLEXIBLE = 2, AMGPS_OPT_COARSE_SWEEPS = 3,
-       AMGPS_OPT_COARSE_KERNEL = 4 };
+       AMGPS_OPT_COARSE_KERNEL = 4, AMGPS_OPT_ALLOC_LIMIT = 5 };
 amgps_status amgps_set_option(amgps_ctx* ctx, int option, int64_t value);
 
 /* Host-only planning query (no device needed): how the TMA-fed step would

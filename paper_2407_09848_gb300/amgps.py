@@ -25,7 +25,7 @@ STATUS = {0: "AMGPS_OK", 1: "AMGPS_E_ARG", 2: "AMGPS_E_NOT_SPD", 3: "AMGPS_E_NOC
           4: "AMGPS_E_NAN", 5: "AMGPS_E_CUDA", 6: "AMGPS_E_TIMEOUT", 7: "AMGPS_E_STATE",
           8: "AMGPS_E_NOMEM"}
 PROF_STEP, PROF_RESTRICT, PROF_SPMV, PROF_COUNT, PROF_COARSE = 0, 1, 2, 3, 4
-OPT_TMA, OPT_FLEXIBLE, OPT_COARSE_SWEEPS, OPT_COARSE_KERNEL = 1, 2, 3, 4
+OPT_TMA, OPT_FLEXIBLE, OPT_COARSE_SWEEPS, OPT_COARSE_KERNEL, OPT_ALLOC_LIMIT = 1, 2, 3, 4, 5
 
 
 class AmgpsError(RuntimeError):
@@ -512,6 +512,11 @@ class Solver:
         kernel wherever a level's layout allows it)."""
         v = 2 if on == "always" else (1 if on else 0)
         self._check(lib().amgps_set_option(self._h, OPT_TMA, v))
+
+    def set_alloc_limit(self, nbytes):
+        """Most device bytes the context may allocate for a hierarchy (0: no limit);
+        a load that would pass it fails with AMGPS_E_NOMEM and keeps nothing."""
+        self._check(lib().amgps_set_option(self._h, OPT_ALLOC_LIMIT, int(nbytes)))
 
     def set_coarse_kernel(self, on):
         """Coarse levels (below the TMA-fed ones): True one persistent kernel,

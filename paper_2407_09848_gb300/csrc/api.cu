@@ -176,6 +176,8 @@ struct amgps_ctx {
   std::vector<cudaEvent_t> pool;
   int64_t prof_launches[5] = {};  // class 3 (kernel count) is kept apart
   void* noalloc = nullptr;        // device address of the allocation-free scratch array
+  size_t alloc_limit = 0;         // AMGPS_OPT_ALLOC_LIMIT: hierarchy bytes allowed (0: no limit)
+  size_t alloc_bytes = 0;         // hierarchy bytes allocated
   // persistent kernel for the coarse levels (option AMGPS_OPT_COARSE_KERNEL)
   int use_cycle = 0;
   bool tail_ok = false;
@@ -214,6 +216,10 @@ amgps_status guard(amgps_ctx* c, F&& f) {
 
 void* dalloc(amgps_ctx* c, size_t bytes) {
   if (bytes == 0) bytes = 16;
+  if (c->alloc_limit && c->alloc_bytes + bytes > c->alloc_limit)
+    throw Fail{AMGPS_E_NOMEM, "allocation of " + std::to_string(bytes) + " bytes would pass the " +
+                                  "context's limit of " + std::to_string(c->alloc_limit) +
+                                  " bytes (AMGPS_OPT_ALLOC_LIMIT)"};
   void* p = nullptr;
   cudaError_t e = cudaMalloc(&p, bytes);
   if (e != cudaSuccess) {
@@ -222,6 +228,7 @@ void* dalloc(amgps_ctx* c, size_t bytes) {
                                   " bytes failed: " + cudaGetErrorString(e)};
   }
   c->allocs.push_back(p);
+  c->alloc_bytes += bytes;
   return p;
 }
 
@@ -242,6 +249,7 @@ void free_hierarchy(amgps_ctx* c) {
   if (!c->allocs.empty()) cudaStreamSynchronize(c->stream);
   for (void* p : c->allocs) cudaFree(p);
   c->allocs.clear();
+  c->alloc_bytes = 0;
   c->lv.clear();
   c->loaded = false;
   c->bwd_ready = false;
@@ -1228,6 +1236,11 @@ void load_general_transfer(amgps_ctx* c, Level& L, const amgps_csr& P) {
 }  // namespace
 
 
+namespace {
+void load_levels(amgps_ctx* c, int n_levels, const amgps_csr* A, const amgps_csr* P,
+                 amgps_prec prec);
+}  // namespace
+
 extern "C" {
 
 int amgps_version(void) { return 1; }
@@ -1323,150 +1336,168 @@ amgps_status amgps_hierarchy_load(amgps_ctx* c, int n_levels, const amgps_csr* A
     enter(c);
     CK(cudaStreamSynchronize(c->stream));
     free_hierarchy(c);
-    tma_configure();
-    check_launch();
-    c->prec = prec;
-    c->lv.resize(n_levels);
-    const size_t xs = (prec == AMGPS_F64) ? sizeof(double) : sizeof(float);
-    for (int l = 0; l < n_levels; ++l) {
-      Level& L = c->lv[l];
-      L.n = A[l].n_rows;
-      L.nnz = A[l].nnz;
-      L.coarsest = (l == n_levels - 1);
-      L.b = dalloc(c, L.n * xs);
-      L.x = dalloc(c, L.n * xs);
-      if (L.coarsest) {
-        std::vector<double> dense((size_t)L.n * L.n, 0.0);
-        for (int64_t i = 0; i < L.n; ++i)
-          for (int e = A[l].rowptr[i]; e < A[l].rowptr[i + 1]; ++e)
-            dense[(size_t)i * L.n + A[l].col[e]] = A[l].val[e];
-        double* work = dupload(c, dense.data(), dense.size());
-        L.ainv = (double*)dalloc(c, dense.size() * sizeof(double));
-        int* dstat = (int*)dalloc(c, sizeof(int));
-        CK(cudaMemsetAsync(dstat, 0, sizeof(int), c->stream));
-        launch_chol_inverse((int)L.n, work, L.ainv, dstat, c->stream);
-        check_launch();
-        int hstat = 0;
-        CK(cudaMemcpyAsync(&hstat, dstat, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-        REQ(hstat == 0, AMGPS_E_NOT_SPD, "coarsest matrix: Cholesky pivot not positive");
-        // the coarsest level also keeps its SELL form and 1/M: for the PCG
-        // SpMV of a single-level hierarchy and for l1-Jacobi coarse sweeps
-      }
-      HostSell h = build_sell(A[l]);
-      L.split = split_for(h.stored, h.nslices);
-      L.nslices = h.nslices;
-      L.stored = h.stored;
-      L.explicit_entries = h.explicit_entries;
-      L.sd = dupload(c, h.sd.data(), h.sd.size());
-      if (h.off.empty()) h.off.push_back(0);  // every slice explicit: keep a valid pointer
-      L.off = dupload(c, h.off.data(), h.off.size());
-      L.col = h.any_explicit ? dupload(c, h.col.data(), h.col.size()) : nullptr;
-      if (prec == AMGPS_F64) {
-        L.val = dupload(c, h.val.data(), h.val.size());
-      } else if (prec == AMGPS_F32) {
-        std::vector<float> f(h.val.size());
-        for (size_t i = 0; i < f.size(); ++i) f[i] = (float)h.val[i];
-        L.val = dupload(c, f.data(), f.size());
-      } else {
-        std::vector<uint16_t> f(h.val.size());
-        for (size_t i = 0; i < f.size(); ++i) f[i] = dbl_to_bf16(h.val[i]);
-        L.val = dupload(c, f.data(), f.size());
-      }
-      {
-        const size_t vsz = prec == AMGPS_F64 ? 8 : (prec == AMGPS_F32 ? 4 : 2);
-        HostPlan hp = build_tma_plan(h, vsz, xs, tma_smem_budget(xs));
-        L.plan = hp.p;
-        L.ntma = (int)hp.tiles.size();
-        L.ngen = (int64_t)hp.gen.size();
-        if (L.ntma > 0) {
-          L.tma_tiles = dupload(c, hp.tiles.data(), hp.tiles.size());
-          L.tma_grid = std::min<int>(L.ntma, tma_ctas_per_sm(xs) * c->nsm);
-        }
-        if (L.ngen > 0) L.gen_slices = dupload(c, hp.gen.data(), hp.gen.size());
-      }
-      if (l == 0 && prec != AMGPS_F64) {
-        L.sd64 = L.sd;
-        L.off64 = L.off;
-        L.col64 = L.col;
-        L.val64 = dupload(c, h.val.data(), h.val.size());
-      }
-      if ((prec == AMGPS_F64 || prec == AMGPS_F32) && !L.coarsest) {
-        // row-scaled copy a_ij / M_i, M_i = sum_j |a_ij| (the l1 diagonal), in
-        // the level's value type (BF16 levels keep A: a_ij / M_i is rarely exact
-        // in BF16 where a_ij is)
-        std::vector<double> m((size_t)L.n, 0.0);
-        const amgps_csr& Al = A[l];
-        parallel_for(L.n, [&](int64_t i, int) {
-          double acc = 0.0;
-          for (int e = Al.rowptr[i]; e < Al.rowptr[i + 1]; ++e) acc += std::fabs(Al.val[e]);
-          m[i] = acc;
-        });
-        std::vector<double> sv(h.val.size(), 0.0);
-        parallel_for(h.nslices, [&](int64_t sl, int) {
-          const SliceDesc d = h.sd[sl];
-          for (int k = 0; k < d.w; ++k)
-            for (int ln = 0; ln < kSlice; ++ln) {
-              const int64_t row = sl * kSlice + ln;
-              const int64_t e = d.vbase + (int64_t)k * kSlice + ln;
-              if (row < L.n) sv[e] = h.val[e] / m[row];
-            }
-        });
-        if (prec == AMGPS_F64) {
-          L.sval = dupload(c, sv.data(), sv.size());
-        } else {
-          std::vector<float> svf(sv.size());
-          for (size_t i = 0; i < sv.size(); ++i) svf[i] = (float)sv[i];
-          L.sval = dupload(c, svf.data(), svf.size());
-        }
-      }
-      L.dinv = dalloc(c, L.n * xs);
-      L.r = dalloc(c, L.n * xs);
-      L.za = dalloc(c, L.n * xs);
-      L.zb = dalloc(c, L.n * xs);
-      L.xb = dalloc(c, L.n * xs);
-      if (prec == AMGPS_F64) launch_l1diag<double, double>(devmat<double>(L), (double*)L.dinv, c->stream);
-      else if (prec == AMGPS_F32) launch_l1diag<float, float>(devmat<float>(L), (float*)L.dinv, c->stream);
-      else launch_l1diag<__nv_bfloat16, float>(devmat<__nv_bfloat16>(L), (float*)L.dinv, c->stream);
-      check_launch();
-      if (L.coarsest) continue;
-      const amgps_csr& Pl = P[l];
-      const int64_t nc = Pl.n_cols;
-      L.nc = nc;
-      L.spec = Spec{};
-      if (!is_aggregation(Pl)) {
-        load_general_transfer(c, L, Pl);
-        continue;
-      }
-      // aggregation maps: agg[i] and the children lists of every coarse row
-      std::vector<int32_t> agg(L.n), cptr(nc + 1, 0), cidx(L.n);
-      for (int64_t i = 0; i < L.n; ++i) {
-        agg[i] = Pl.col[Pl.rowptr[i]];
-        cptr[agg[i] + 1]++;
-      }
-      for (int64_t I = 0; I < nc; ++I) {
-        REQ(cptr[I + 1] > 0, AMGPS_E_ARG, "P has an empty aggregate (zero column)");
-        cptr[I + 1] += cptr[I];
-      }
-      std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
-      for (int64_t i = 0; i < L.n; ++i) cidx[fill[agg[i]]++] = (int32_t)i;
-      L.agg = dupload(c, agg.data(), agg.size());
-      L.cptr = dupload(c, cptr.data(), cptr.size());
-      L.cidx = dupload(c, cidx.data(), cidx.size());
+    try {
+      load_levels(c, n_levels, A, P, prec);
+    } catch (...) {
+      free_hierarchy(c);  // a failed load keeps no buffers
+      leave(c);
+      throw;
     }
-    const int64_t n0 = c->lv[0].n;
-    c->pr = (double*)dalloc(c, n0 * sizeof(double));
-    c->pp = (double*)dalloc(c, n0 * sizeof(double));
-    c->pq = (double*)dalloc(c, n0 * sizeof(double));
-    c->pz = (double*)dalloc(c, n0 * sizeof(double));
-    c->pz2 = (double*)dalloc(c, n0 * sizeof(double));
-    c->stage_b = (double*)dalloc(c, n0 * sizeof(double));
-    c->stage_x = (double*)dalloc(c, n0 * sizeof(double));
-    CK(cudaStreamSynchronize(c->stream));
-    c->loaded = true;
     leave(c);
   });
 }
+
+}  // extern "C"
+
+namespace {
+// The body of amgps_hierarchy_load after validation: upload and plan every level.
+void load_levels(amgps_ctx* c, int n_levels, const amgps_csr* A, const amgps_csr* P,
+                 amgps_prec prec) {
+  tma_configure();
+  check_launch();
+  c->prec = prec;
+  c->lv.resize(n_levels);
+  const size_t xs = (prec == AMGPS_F64) ? sizeof(double) : sizeof(float);
+  for (int l = 0; l < n_levels; ++l) {
+    Level& L = c->lv[l];
+    L.n = A[l].n_rows;
+    L.nnz = A[l].nnz;
+    L.coarsest = (l == n_levels - 1);
+    L.b = dalloc(c, L.n * xs);
+    L.x = dalloc(c, L.n * xs);
+    if (L.coarsest) {
+      std::vector<double> dense((size_t)L.n * L.n, 0.0);
+      for (int64_t i = 0; i < L.n; ++i)
+        for (int e = A[l].rowptr[i]; e < A[l].rowptr[i + 1]; ++e)
+          dense[(size_t)i * L.n + A[l].col[e]] = A[l].val[e];
+      double* work = dupload(c, dense.data(), dense.size());
+      L.ainv = (double*)dalloc(c, dense.size() * sizeof(double));
+      int* dstat = (int*)dalloc(c, sizeof(int));
+      CK(cudaMemsetAsync(dstat, 0, sizeof(int), c->stream));
+      launch_chol_inverse((int)L.n, work, L.ainv, dstat, c->stream);
+      check_launch();
+      int hstat = 0;
+      CK(cudaMemcpyAsync(&hstat, dstat, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      REQ(hstat == 0, AMGPS_E_NOT_SPD, "coarsest matrix: Cholesky pivot not positive");
+      // the coarsest level also keeps its SELL form and 1/M: for the PCG
+      // SpMV of a single-level hierarchy and for l1-Jacobi coarse sweeps
+    }
+    HostSell h = build_sell(A[l]);
+    L.split = split_for(h.stored, h.nslices);
+    L.nslices = h.nslices;
+    L.stored = h.stored;
+    L.explicit_entries = h.explicit_entries;
+    L.sd = dupload(c, h.sd.data(), h.sd.size());
+    if (h.off.empty()) h.off.push_back(0);  // every slice explicit: keep a valid pointer
+    L.off = dupload(c, h.off.data(), h.off.size());
+    L.col = h.any_explicit ? dupload(c, h.col.data(), h.col.size()) : nullptr;
+    if (prec == AMGPS_F64) {
+      L.val = dupload(c, h.val.data(), h.val.size());
+    } else if (prec == AMGPS_F32) {
+      std::vector<float> f(h.val.size());
+      for (size_t i = 0; i < f.size(); ++i) f[i] = (float)h.val[i];
+      L.val = dupload(c, f.data(), f.size());
+    } else {
+      std::vector<uint16_t> f(h.val.size());
+      for (size_t i = 0; i < f.size(); ++i) f[i] = dbl_to_bf16(h.val[i]);
+      L.val = dupload(c, f.data(), f.size());
+    }
+    {
+      const size_t vsz = prec == AMGPS_F64 ? 8 : (prec == AMGPS_F32 ? 4 : 2);
+      HostPlan hp = build_tma_plan(h, vsz, xs, tma_smem_budget(xs));
+      L.plan = hp.p;
+      L.ntma = (int)hp.tiles.size();
+      L.ngen = (int64_t)hp.gen.size();
+      if (L.ntma > 0) {
+        L.tma_tiles = dupload(c, hp.tiles.data(), hp.tiles.size());
+        L.tma_grid = std::min<int>(L.ntma, tma_ctas_per_sm(xs) * c->nsm);
+      }
+      if (L.ngen > 0) L.gen_slices = dupload(c, hp.gen.data(), hp.gen.size());
+    }
+    if (l == 0 && prec != AMGPS_F64) {
+      L.sd64 = L.sd;
+      L.off64 = L.off;
+      L.col64 = L.col;
+      L.val64 = dupload(c, h.val.data(), h.val.size());
+    }
+    if ((prec == AMGPS_F64 || prec == AMGPS_F32) && !L.coarsest) {
+      // row-scaled copy a_ij / M_i, M_i = sum_j |a_ij| (the l1 diagonal), in
+      // the level's value type (BF16 levels keep A: a_ij / M_i is rarely exact
+      // in BF16 where a_ij is)
+      std::vector<double> m((size_t)L.n, 0.0);
+      const amgps_csr& Al = A[l];
+      parallel_for(L.n, [&](int64_t i, int) {
+        double acc = 0.0;
+        for (int e = Al.rowptr[i]; e < Al.rowptr[i + 1]; ++e) acc += std::fabs(Al.val[e]);
+        m[i] = acc;
+      });
+      std::vector<double> sv(h.val.size(), 0.0);
+      parallel_for(h.nslices, [&](int64_t sl, int) {
+        const SliceDesc d = h.sd[sl];
+        for (int k = 0; k < d.w; ++k)
+          for (int ln = 0; ln < kSlice; ++ln) {
+            const int64_t row = sl * kSlice + ln;
+            const int64_t e = d.vbase + (int64_t)k * kSlice + ln;
+            if (row < L.n) sv[e] = h.val[e] / m[row];
+          }
+      });
+      if (prec == AMGPS_F64) {
+        L.sval = dupload(c, sv.data(), sv.size());
+      } else {
+        std::vector<float> svf(sv.size());
+        for (size_t i = 0; i < sv.size(); ++i) svf[i] = (float)sv[i];
+        L.sval = dupload(c, svf.data(), svf.size());
+      }
+    }
+    L.dinv = dalloc(c, L.n * xs);
+    L.r = dalloc(c, L.n * xs);
+    L.za = dalloc(c, L.n * xs);
+    L.zb = dalloc(c, L.n * xs);
+    L.xb = dalloc(c, L.n * xs);
+    if (prec == AMGPS_F64) launch_l1diag<double, double>(devmat<double>(L), (double*)L.dinv, c->stream);
+    else if (prec == AMGPS_F32) launch_l1diag<float, float>(devmat<float>(L), (float*)L.dinv, c->stream);
+    else launch_l1diag<__nv_bfloat16, float>(devmat<__nv_bfloat16>(L), (float*)L.dinv, c->stream);
+    check_launch();
+    if (L.coarsest) continue;
+    const amgps_csr& Pl = P[l];
+    const int64_t nc = Pl.n_cols;
+    L.nc = nc;
+    L.spec = Spec{};
+    if (!is_aggregation(Pl)) {
+      load_general_transfer(c, L, Pl);
+      continue;
+    }
+    // aggregation maps: agg[i] and the children lists of every coarse row
+    std::vector<int32_t> agg(L.n), cptr(nc + 1, 0), cidx(L.n);
+    for (int64_t i = 0; i < L.n; ++i) {
+      agg[i] = Pl.col[Pl.rowptr[i]];
+      cptr[agg[i] + 1]++;
+    }
+    for (int64_t I = 0; I < nc; ++I) {
+      REQ(cptr[I + 1] > 0, AMGPS_E_ARG, "P has an empty aggregate (zero column)");
+      cptr[I + 1] += cptr[I];
+    }
+    std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
+    for (int64_t i = 0; i < L.n; ++i) cidx[fill[agg[i]]++] = (int32_t)i;
+    L.agg = dupload(c, agg.data(), agg.size());
+    L.cptr = dupload(c, cptr.data(), cptr.size());
+    L.cidx = dupload(c, cidx.data(), cidx.size());
+  }
+  const int64_t n0 = c->lv[0].n;
+  c->pr = (double*)dalloc(c, n0 * sizeof(double));
+  c->pp = (double*)dalloc(c, n0 * sizeof(double));
+  c->pq = (double*)dalloc(c, n0 * sizeof(double));
+  c->pz = (double*)dalloc(c, n0 * sizeof(double));
+  c->pz2 = (double*)dalloc(c, n0 * sizeof(double));
+  c->stage_b = (double*)dalloc(c, n0 * sizeof(double));
+  c->stage_x = (double*)dalloc(c, n0 * sizeof(double));
+  CK(cudaStreamSynchronize(c->stream));
+  c->loaded = true;
+}
+}  // namespace
+
+extern "C" {
 
 amgps_status amgps_level_info(amgps_ctx* c, int level, int64_t* n, int64_t* nnz, int64_t* stored) {
   return guard(c, [&] {
@@ -1867,7 +1898,8 @@ amgps_status amgps_set_option(amgps_ctx* c, int option, int64_t value) {
   return guard(c, [&] {
     REQ(c, AMGPS_E_ARG, "null context");
     REQ(option == AMGPS_OPT_TMA || option == AMGPS_OPT_FLEXIBLE ||
-            option == AMGPS_OPT_COARSE_SWEEPS || option == AMGPS_OPT_COARSE_KERNEL,
+            option == AMGPS_OPT_COARSE_SWEEPS || option == AMGPS_OPT_COARSE_KERNEL ||
+            option == AMGPS_OPT_ALLOC_LIMIT,
         AMGPS_E_ARG, "unknown option");
     if (option == AMGPS_OPT_TMA) {
       REQ(value >= 0 && value <= 2, AMGPS_E_ARG, "AMGPS_OPT_TMA takes 0, 1 or 2");
@@ -1876,6 +1908,9 @@ amgps_status amgps_set_option(amgps_ctx* c, int option, int64_t value) {
     } else if (option == AMGPS_OPT_FLEXIBLE) {
       REQ(value >= 0 && value <= 2, AMGPS_E_ARG, "AMGPS_OPT_FLEXIBLE takes 0, 1 or 2");
       c->flexible = (int)value;
+    } else if (option == AMGPS_OPT_ALLOC_LIMIT) {
+      REQ(value >= 0, AMGPS_E_ARG, "AMGPS_OPT_ALLOC_LIMIT takes a byte count >= 0");
+      c->alloc_limit = (size_t)value;
     } else if (option == AMGPS_OPT_COARSE_KERNEL) {
       REQ(value == 0 || value == 1, AMGPS_E_ARG, "AMGPS_OPT_COARSE_KERNEL takes 0 or 1");
       c->use_cycle = (int)value;

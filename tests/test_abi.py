@@ -91,7 +91,7 @@ def test_tma_plan_covers_and_checks_copies(lib, prec):
             n = lv.A.shape[0]
             tiles, gen, stage, nst = amgps.tma_plan_stats(lv.A, prec)
             nslices = (n + 31) // 32
-            per = (480 if prec == "f64" else 1024) // 32
+            per = (512 if prec == "f64" else 1024) // 32
             assert tiles * per + gen == nslices
             if tiles:
                 budget = 230400 if prec == "f64" else 115200  # one CTA per SM for FP64, two otherwise
@@ -101,7 +101,7 @@ def test_tma_plan_covers_and_checks_copies(lib, prec):
     # qualifies; the exceptions are tiles where the slice pattern changes
     H = pr.build_hierarchy(pr.poisson(64))
     tiles, gen, _, _ = amgps.tma_plan_stats(H.levels[0].A, prec)
-    rows = 480 if prec == "f64" else 1024
+    rows = 512 if prec == "f64" else 1024
     per = rows // 32
     assert tiles * per + gen == 8192 and tiles >= (262144 - 2 * 4096) // rows - 64 // per - 2
 
@@ -223,22 +223,24 @@ def test_binding_constants_match_header():
     for prec, v in amgps.PREC.items():
         assert enum["AMGPS_" + prec.upper()] == v, prec
     assert (enum["AMGPS_OPT_TMA"], enum["AMGPS_OPT_FLEXIBLE"], enum["AMGPS_OPT_COARSE_SWEEPS"],
-            enum["AMGPS_OPT_COARSE_KERNEL"]) == (amgps.OPT_TMA, amgps.OPT_FLEXIBLE,
-                                                 amgps.OPT_COARSE_SWEEPS, amgps.OPT_COARSE_KERNEL)
+            enum["AMGPS_OPT_COARSE_KERNEL"], enum["AMGPS_OPT_ALLOC_LIMIT"]) == (
+        amgps.OPT_TMA, amgps.OPT_FLEXIBLE, amgps.OPT_COARSE_SWEEPS, amgps.OPT_COARSE_KERNEL,
+        amgps.OPT_ALLOC_LIMIT)
 
 
 def test_fp64_stage_count_is_even(lib):
-    # a banded matrix whose seven offsets chain into one 2880-element window
-    # (gaps of at most 544) leaves room for three 57.6 KB FP64 stages (values
-    # 26,880 B, r_in and x_in 7,680 B, window 23,040 B); the planner keeps two,
-    # a multiple of the FP64 shape's two consumer groups
+    # a banded matrix whose seven offsets chain into one window of 2400 + 512
+    # elements (gaps of at most 544) leaves room for three 60.2 KB FP64 stages
+    # of 512-row tiles (values 28,672 B, r_in and x_in 8,192 B, window
+    # 23,296 B); the planner keeps two, a multiple of the FP64 shape's two
+    # consumer groups
     import scipy.sparse as sp
     from paper_2407_09848_gb300 import problems as pr
     offs = [-1200, -656, -112, 0, 112, 656, 1200]
     n = 9600
     A = sp.diags([np.full(n - abs(o), 8.0 if o == 0 else -1.0) for o in offs], offs).tocsr()
     tiles, gen, stage, nst = amgps.tma_plan_stats(A, "f64")
-    assert tiles > 0 and stage == 57600 and nst == 2
+    assert tiles > 0 and stage == 60160 and nst == 2
     tiles, gen, stage, nst = amgps.tma_plan_stats(pr.to_csr(pr.poisson(256, 8, 8)), "f64")
     assert nst == 4
 
@@ -380,17 +382,21 @@ def test_tma_plan_stage_emulation(lib, prec):
 
 
 def test_tma_plan_merges_the_windows_of_512_wide_grids(lib):
-    # host-only: with 480-row tiles the -nx..+nx offsets of a 481..545-wide grid
-    # share one window (the gap it copies along is at most 64 elements), so a
-    # 7-point level has three window groups and, with no 1/M slot in FP64
-    # stages, four stages; one column wider the gap exceeds the slack, five
-    # groups exceed the plan's four and no tile is planned
+    # host-only: with R-row FP64 tiles the -nx..+nx offsets of a grid up to
+    # R + 65 wide share one window (for R < nx the gap the window copies along
+    # is at most 64 elements), so a 7-point level has three window groups and,
+    # with no 1/M slot in FP64 stages, four stages at 512-wide; one column
+    # wider the gap exceeds the slack, five groups exceed the plan's four and
+    # no tile is planned
     from paper_2407_09848_gb300 import problems as pr
-    for nx in (481, 512, 545):
+    rows = amgps.tma_plan(pr.to_csr(pr.poisson(64, 16, 16)), "f64")["rows"]
+    for nx in (rows - 31, 512, rows + 1, rows + 65):
         P = amgps.tma_plan(pr.to_csr(pr.poisson(nx, 16, 16)), "f64")
-        assert P["ngroups"] == 3 and P["nstages"] == 4 and len(P["tiles"]) > 0, nx
-        assert P["g_elems"][1] >= 2 * nx + 480  # rows -nx .. nx + 479 of the tile
-    P = amgps.tma_plan(pr.to_csr(pr.poisson(546, 16, 16)), "f64")
+        assert P["ngroups"] == 3 and len(P["tiles"]) > 0, nx
+        assert P["g_elems"][1] >= 2 * nx + rows  # rows -nx .. nx + rows - 1 of the tile
+        if nx == 512:
+            assert P["nstages"] == 4
+    P = amgps.tma_plan(pr.to_csr(pr.poisson(rows + 66, 16, 16)), "f64")
     assert len(P["tiles"]) == 0
     # 256-wide grids keep their windows and four stages
     P = amgps.tma_plan(pr.to_csr(pr.poisson(256, 16, 16)), "f64")

@@ -558,3 +558,33 @@ def test_coarse_kernel_option_falls_back_on_general_transfers(torch_cuda):
         torch.cuda.synchronize()
         out.append((z, S.profile_read(3, reset=True)[0]))
     assert torch.equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+
+
+def test_allocation_limit_reports_nomem_and_recovers(torch_cuda):
+    """Failure injected on the host: a context limited to 1 MiB of device
+    memory refuses a hierarchy with AMGPS_E_NOMEM before reaching the CUDA
+    allocator, keeps no hierarchy (and none of the partial buffers), and
+    loads and solves once the limit is lifted."""
+    from paper_2407_09848_gb300.amgps import AmgpsError, Solver
+    torch = torch_cuda
+    H = pr.build_hierarchy(pr.poisson(24), coarse_max=100)
+    Solver().load(H.A, H.P).close()   # the load's kernels are on the device now
+    S = Solver()
+    S.set_alloc_limit(1 << 20)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    with pytest.raises(AmgpsError) as e:
+        S.load(H.A, H.P)
+    assert e.value.name == "AMGPS_E_NOMEM" and "AMGPS_OPT_ALLOC_LIMIT" in str(e.value)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free0   # the partial buffers were released
+    with pytest.raises(AmgpsError) as e:
+        S.level_info(0)
+    assert e.value.name == "AMGPS_E_STATE"
+    S.set_alloc_limit(0)
+    S.load(H.A, H.P)
+    n = H.A[0].shape[0]
+    b = to_dev(torch, pr.rhs_uniform(n, seed=0))
+    x = torch.empty_like(b)
+    it, rel = S.pcg(b, x, rtol=1e-8)
+    assert rel <= 1e-8 and it > 0

@@ -95,7 +95,7 @@ constexpr int kMaxSplit = 32;
 // only; a group's warps split each tile's slices between them.  Fewer, larger
 // copies keep the TMA unit streaming.  The launch shape depends on the vector
 // type:
-//   FP64: 480-row tiles (15 slices), one CTA per SM of 1 producer warp and two
+//   FP64: 512-row tiles (16 slices), one CTA per SM of 1 producer warp and two
 //     groups of 8 consumer warps taking alternate tiles (544 threads; a lane
 //     evaluates two rows of a 7-point tile, slices cw and cw + 8), with up
 //     to 225 KB of stages -- four in flight, so a tile's copies are issued
@@ -113,7 +113,7 @@ struct TmaShape {  // FP32 vectors (FP32 and BF16 levels)
 };
 template <>
 struct TmaShape<double> {
-  static constexpr int kRows = 480, kGroups = 2, kConsumers = 8, kCtasPerSm = 1;
+  static constexpr int kRows = 512, kGroups = 2, kConsumers = 8, kCtasPerSm = 1;
   static constexpr int kSmemBudget = 230400;
   static constexpr int kVecSlots = 2;
 };
@@ -132,7 +132,7 @@ inline int tma_vec_slots(size_t xsize) {
 }
 // Two offset groups share one window when the merged window holds at most
 // this many elements more than the two separate ones (the +-nx offsets of a
-// 481..544-wide grid against 480-row tiles).
+// 513..577-wide grid against 512-row tiles).
 constexpr int kTmaMergeSlack = 64;
 // The stage count of a plan is a multiple of the group count: then the
 // previous fill of the stage a group waits on is a tile of the same group,

@@ -17,7 +17,7 @@
 // run the slices outside the plan with direct loads.  The arithmetic and its order are those of k_step,
 // so both paths give the same bits.  Tile height, groups and CTAs per SM come
 // from TmaShape<XT>: for FP64 one CTA per SM with two groups of 8 warps and
-// four 480-row stages in flight (the FP64-bound consumers then never wait for
+// four 512-row stages in flight (the FP64-bound consumers then never wait for
 // a copy), for FP32 vectors two CTAs per SM of 16 consumers on 1024-row tiles.
 //
 // Rows of the 7-point pattern (seven sorted offsets, the row itself in the
@@ -26,8 +26,8 @@
 // pipe a predicated-off DFMA still costs an issue slot), and the centre entry
 // multiplies the z_j value the row already loaded for its c1 term; a lane of
 // that variant evaluates two rows of the tile with their multiply-add chains
-// interleaved (8 consumer warps per group instead of 15 of one row each:
-// 323 -> 319 us per 256^3 step).
+// interleaved (8 consumer warps per group on 512-row tiles instead of 15 of
+// one row each on 480-row tiles: 323 -> 318 us per 256^3 step).
 //
 // Every wait is bounded (kWaitSpins polls).  A wait that gives up sets the
 // solver's error slot and makes all warps leave their loops; the producer

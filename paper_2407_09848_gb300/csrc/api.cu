@@ -826,9 +826,10 @@ struct Engine {
   }
 
   // The persistent kernel takes the levels from the first one (>= 1) that
-  // runs no TMA-fed step and has at most kCycleMaxRows rows down to the coarsest, when all of them use the
-  // direct step, one warp per slice, and aggregation transfers.  Its phase
-  // list is the kernel sequence vcycle_level would launch there, recorded.
+  // runs no TMA-fed step and has at most kCycleMaxRows rows down to the
+  // coarsest, when all of them use the direct step, one warp per slice, and
+  // aggregation transfers.  Its phase list is the kernel sequence
+  // vcycle_level would launch there, recorded.
   static void build_tail(amgps_ctx* c) {
     c->tail_ok = false;
     const int nl = (int)c->lv.size();
@@ -1455,8 +1456,10 @@ void load_levels(amgps_ctx* c, int n_levels, const amgps_csr* A, const amgps_csr
     L.za = dalloc(c, L.n * xs);
     L.zb = dalloc(c, L.n * xs);
     L.xb = dalloc(c, L.n * xs);
-    if (prec == AMGPS_F64) launch_l1diag<double, double>(devmat<double>(L), (double*)L.dinv, c->stream);
-    else if (prec == AMGPS_F32) launch_l1diag<float, float>(devmat<float>(L), (float*)L.dinv, c->stream);
+    if (prec == AMGPS_F64)
+      launch_l1diag<double, double>(devmat<double>(L), (double*)L.dinv, c->stream);
+    else if (prec == AMGPS_F32)
+      launch_l1diag<float, float>(devmat<float>(L), (float*)L.dinv, c->stream);
     else launch_l1diag<__nv_bfloat16, float>(devmat<__nv_bfloat16>(L), (float*)L.dinv, c->stream);
     check_launch();
     if (L.coarsest) continue;

@@ -141,7 +141,8 @@ __global__ void __launch_bounds__(kCycleThreads, kCycleMaxBlocksPerSm)
         }
         break;
       case CY_AGG:
-        for (int64_t I = gt; I < P.n; I += nt) aggregate_row<XT, true>(I, P.i0, P.i1, P.in0, P.out0);
+        for (int64_t I = gt; I < P.n; I += nt)
+          aggregate_row<XT, true>(I, P.i0, P.i1, P.in0, P.out0);
         break;
       case CY_PROLONG:
         for (int64_t i = gt; i < P.n; i += nt) prolong_row<XT, true>(i, P.i0, P.in0, P.out0);

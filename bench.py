@@ -59,6 +59,8 @@ def parse_args(argv=None):
     ap.add_argument("--degree", type=int, default=4)
     ap.add_argument("--prec", default="f64", choices=["f64", "f32", "bf16"])
     ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--step-form", type=int, default=1, choices=[0, 1],
+                    help="FP64 polynomial steps: 1 stored operators (default), 0 recurrence")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -577,7 +579,9 @@ def profiled_pass(S, bd, x, a, torch, smi):
             S.pcg(bd, x, rtol=a.rtol)
         torch.cuda.synchronize()
     S.profile(False)
+    flops = S.profile_flops(PROF_STEP)  # before the reset below
     out = {c: S.profile_read(c, reset=True) for c in classes}
+    out["step_flops"] = flops
     return out, a.steps, clk.summary()
 
 
@@ -623,6 +627,7 @@ def run_ours(a):
     H, b = build_problem(a)
     n = H.levels[0].A.shape[0]
     S = Solver(local).load(H.A, H.P, prec=a.prec)
+    S.set_step_form(a.step_form)
     configure(S, H, a.kind, a.degree, torch)
     bd = torch.from_numpy(b).cuda()
     x = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -663,20 +668,16 @@ def run_ours(a):
     hbm["share_of_solve_time"] = (ms_step / nprof) / ms_per if ms_per else None
     roof = hbm
     if a.prec == "f64" and a.kind in ("cheb4", "cheb4_opt", "weights") and n_step:
-        # FP64 path: the step is bound by the FP64 pipe (ncu: ~85% busy vs
-        # DRAM ~60%).  The 4th-kind steps run on the row-scaled matrix M^{-1}A
-        # with the residual kept scaled.  Flops per launch averaged over a
-        # V-cycle's 2k-1 level-0 steps: every step 2 nnz (the SpMV with the
-        # residual folded in); per row c2 r (1) and, with the c1 z term, one
-        # FMA (2), x += beta z (2), and 1 more where rin is still unscaled (the
-        # first step after the initial one, and the post-smoothing initial
-        # step, which has no c1 term): 2 nnz + 5 n per launch for k >= 2,
-        # 2 nnz + 4 n for k = 1.  Peak: 304 FP64 FMA thread-instructions per
+        # FP64 path: the step is bound by the FP64 pipe.  Flops per launch: the
+        # library's algorithmic count over the profiled level-0 steps
+        # (amgps_profile_flops: a multiply-add 2, a lone multiply 1, 2 per
+        # nonzero for the products), averaged per launch.  In the
+        # stored-operator form a k = 4 cycle's seven level-0 steps total
+        # 14 nnz + 7 n (2 nnz + n per launch); the recurrence form's are
+        # 2 nnz + 5 n per launch.  Peak: 304 FP64 FMA thread-instructions per
         # clock (152 SMs x 2, ncu peak_sustained) x 2 flops x the SM clock
         # sampled during the profiled pass.
-        k = a.degree
-        nnz0 = float(H.levels[0].A.nnz)
-        fl = 2 * nnz0 + (5 * n if k >= 2 else 4 * n)
+        fl = prof["step_flops"] / n_step
         mhz = clk_prof.get("sm_mhz") or 2070.0
         fpeak = 304 * 2 * mhz * 1e6 / 1e12
         fach = fl / (1e-3 * ms_step / n_step) / 1e12
@@ -688,6 +689,8 @@ def run_ours(a):
                 "share_of_solve_time": hbm["share_of_solve_time"], "hbm": hbm}
     roof["measured_in"] = (f"a pass of {nprof} solves after the timed region, CUDA events around "
                            f"each level-0 step launch on the library stream")
+    roof["step_form"] = ("stored operators (Clenshaw steps)" if a.step_form == 1
+                         else "recurrence (z, r, x)")
     roof["clocks"] = clk_prof
 
     # ---- end to end through the host-buffer C-ABI call ----

@@ -322,9 +322,21 @@ amgps_status amgps_synchronize(amgps_ctx* ctx);
  * that would pass it fails with AMGPS_E_NOMEM before reaching the CUDA
  * allocator, so a caller can reject a problem that would not fit its memory
  * share.  Any failed amgps_hierarchy_load leaves no hierarchy loaded and
- * keeps none of its buffers. */
+ * keeps none of its buffers.
+ * AMGPS_OPT_STEP_FORM (default 1): how the polynomial smoothers (both
+ * Chebyshev kinds and AMGPS_WEIGHTS, degree >= 2) run on FP64 levels that
+ * hold at least 4 TMA tiles per SM.  0: the recurrences of Eq. polsmoother /
+ * polsmootheropt and Algorithm 1 step by step.  1: the same polynomial
+ * evaluated backwards (Clenshaw's scheme on its three-term recurrence) with
+ * each step's operator tau_j I - sigma_j M^{-1} A stored in A's layout --
+ * degree - 1 extra arrays of A's stored entries per such level, built by
+ * amgps_hierarchy_load, amgps_set_smoother and this option, and counted
+ * against AMGPS_OPT_ALLOC_LIMIT; a level whose arrays do not fit keeps form
+ * 0.  The two forms agree to rounding (not bit for bit); amgps_smooth uses
+ * form 1 on a level only for the kind, degree, weights and rho set for it by
+ * amgps_set_smoother.  Other values: AMGPS_E_ARG. */
 enum { AMGPS_OPT_TMA = 1, AMGPS_OPT_FLEXIBLE = 2, AMGPS_OPT_COARSE_SWEEPS = 3,
-       AMGPS_OPT_COARSE_KERNEL = 4, AMGPS_OPT_ALLOC_LIMIT = 5 };
+       AMGPS_OPT_COARSE_KERNEL = 4, AMGPS_OPT_ALLOC_LIMIT = 5, AMGPS_OPT_STEP_FORM = 6 };
 amgps_status amgps_set_option(amgps_ctx* ctx, int option, int64_t value);
 
 /* Host-only planning query (no device needed): how the TMA-fed step would
@@ -380,6 +392,17 @@ amgps_status amgps_sell_layout(const amgps_csr* A, int64_t* nslices, int64_t* st
                                int64_t* noff, int64_t* vbase, int32_t* width, int32_t* cref,
                                double* val, int32_t* col, int32_t* off);
 
+/* Host-only query: the steps of one smoother application in the
+ * stored-operator form (AMGPS_OPT_STEP_FORM 1) for a Chebyshev kind or
+ * AMGPS_WEIGHTS (weights as in amgps_set_smoother) and degree k in 2..16.
+ * With B = M^{-1} A and s0 = M^{-1} (b - A x0), step q = 0 .. k-2 forms
+ *   v_q = h[q] s0 + g[q] v_{q-2} + (tau[q] I - sigma[q] B) w_q,
+ *   w_0 = s0, w_q = v_{q-1} (v_{-1} = v_{-2} = 0),
+ * and the application returns x = x0 + v_{k-2}.  Each array receives k - 1
+ * entries (host).  Other kinds or degrees: AMGPS_E_ARG. */
+amgps_status amgps_op_coefs(amgps_kind kind, int degree, const double* weights, double rho,
+                            double* tau, double* sigma, double* h, double* g);
+
 /* The library's tabulated optimal 4th-kind weights beta_{1..degree} for
  * Eq. polsmootheropt (degree 1..16), written to beta_out (host). */
 amgps_status amgps_opt4_weights(int degree, double* beta_out);
@@ -402,6 +425,13 @@ amgps_status amgps_cheb1_astar(int degree, double* a_out);
 amgps_status amgps_profile_enable(amgps_ctx* ctx, int on);
 amgps_status amgps_profile_read(amgps_ctx* ctx, int kernel_class, int reset,
                                 int64_t* launches, double* total_ms, double* bytes);
+
+/* The algorithmic FP64 flops of the launches counted in class 0, 1 or 2
+ * since its last reset (a multiply-add counts 2, a lone multiply or add 1;
+ * the products of a step count 2 per nonzero of A): class 0 has them for
+ * both step forms of AMGPS_OPT_STEP_FORM, classes 1 and 2 report 0.  Read it
+ * before the amgps_profile_read call that resets the class.  Synchronous. */
+amgps_status amgps_profile_flops(amgps_ctx* ctx, int kernel_class, double* flops);
 
 #ifdef __cplusplus
 }

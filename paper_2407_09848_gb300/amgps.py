@@ -26,6 +26,7 @@ STATUS = {0: "AMGPS_OK", 1: "AMGPS_E_ARG", 2: "AMGPS_E_NOT_SPD", 3: "AMGPS_E_NOC
           8: "AMGPS_E_NOMEM"}
 PROF_STEP, PROF_RESTRICT, PROF_SPMV, PROF_COUNT, PROF_COARSE = 0, 1, 2, 3, 4
 OPT_TMA, OPT_FLEXIBLE, OPT_COARSE_SWEEPS, OPT_COARSE_KERNEL, OPT_ALLOC_LIMIT = 1, 2, 3, 4, 5
+OPT_STEP_FORM = 6
 
 
 class AmgpsError(RuntimeError):
@@ -103,6 +104,9 @@ _SIGS = {
                         C.POINTER(CSRBuf), C.POINTER(CSRBuf)], C.c_int),
     "amgps_profile_read": ([C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double),
                             C.POINTER(C.c_double)], C.c_int),
+    "amgps_profile_flops": ([C.c_void_p, C.c_int, C.POINTER(C.c_double)], C.c_int),
+    "amgps_op_coefs": ([C.c_int, C.c_int, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p,
+                        C.c_void_p, C.c_void_p], C.c_int),
 }
 
 
@@ -219,6 +223,19 @@ def step_coefs(kind, degree, weights=None, rho=0.0):
     if stat:
         raise AmgpsError(stat, lib().amgps_last_error(None).decode())
     return c1, c2, beta, ri.value
+
+
+def op_coefs(kind, degree, weights=None, rho=0.0):
+    """Host-only: (tau, sigma, h, g) of the stored-operator steps of one
+    application, arrays of degree - 1 entries (see amgps_op_coefs)."""
+    tau, sigma, h, g = (np.zeros(degree - 1) for _ in range(4))
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    stat = lib().amgps_op_coefs(KIND[kind], int(degree), None if w is None else w.ctypes.data,
+                                float(rho), tau.ctypes.data, sigma.ctypes.data, h.ctypes.data,
+                                g.ctypes.data)
+    if stat:
+        raise AmgpsError(stat, lib().amgps_last_error(None).decode())
+    return tau, sigma, h, g
 
 
 def tma_plan(A, prec="f64"):
@@ -518,6 +535,12 @@ class Solver:
         a load that would pass it fails with AMGPS_E_NOMEM and keeps nothing."""
         self._check(lib().amgps_set_option(self._h, OPT_ALLOC_LIMIT, int(nbytes)))
 
+    def set_step_form(self, form):
+        """Polynomial smoothers on the large FP64 levels: 1 (default) the
+        stored-operator form (Clenshaw steps, one stored operator per step),
+        0 the recurrence form; equal to rounding."""
+        self._check(lib().amgps_set_option(self._h, OPT_STEP_FORM, int(form)))
+
     def set_coarse_kernel(self, on):
         """Coarse levels (below the TMA-fed ones): True one persistent kernel,
         False (default) one launch per kernel; identical results."""
@@ -542,6 +565,13 @@ class Solver:
 
     def profile(self, on=True):
         self._check(lib().amgps_profile_enable(self._h, 1 if on else 0))
+
+    def profile_flops(self, cls):
+        """Algorithmic FP64 flops of the class's timed launches since its last
+        reset (read before profile_read(cls, reset=True))."""
+        f = C.c_double()
+        self._check(lib().amgps_profile_flops(self._h, cls, C.byref(f)))
+        return f.value
 
     def profile_read(self, cls, reset=False):
         n, ms, by = C.c_int64(), C.c_double(), C.c_double()

@@ -53,10 +53,30 @@ struct DevMat {
 // the accumulation starts from (1/M) rin.
 // FAM_CHEB1S / FAM_CHEB1SR do the same for the 1st-kind steps, keeping the
 // residual as rho M^{-1} r (the 1/rho goes into the coefficient of r).
+// FAM_OP / FAM_OPT are the steps of the stored-operator form of a polynomial
+// smoother on FP64 levels (the same polynomial evaluated backwards, Clenshaw's
+// scheme, with each step's operator tau I - sigma M^{-1} A stored in A's
+// layout; api.cu derives the coefficients):
+//   FAM_OP:  out = [q | c2 s] + [c1 p] + sum_k m_ik u_k   (A = the step's operator)
+//            rin = the slot-0 vector (q or s): read when INIT, added with
+//            coefficient 1 when WR, else times c2; xin = the slot-1 vector p,
+//            read (times c1) when ZOWN.
+//   FAM_OPT: out = q - sum_k (a_ik / M_i) u_k              (A = the row-scaled values)
+//            rin = q; when WR also rout = u_row + beta out.
 enum Family { FAM_CHEB4 = 0, FAM_CHEB1 = 1, FAM_JAC = 2, FAM_RES = 3, FAM_CHEB4S = 4,
-              FAM_CHEB4SR = 5, FAM_CHEB1S = 6, FAM_CHEB1SR = 7 };
+              FAM_CHEB4SR = 5, FAM_CHEB1S = 6, FAM_CHEB1SR = 7, FAM_OP = 8, FAM_OPT = 9 };
 __host__ __device__ constexpr bool is_cheb4(int fam) {
   return fam == FAM_CHEB4 || fam == FAM_CHEB4S || fam == FAM_CHEB4SR;
+}
+__host__ __device__ constexpr bool is_op(int fam) { return fam == FAM_OP || fam == FAM_OPT; }
+// per-row vectors of a step: slot 0 (rin) and slot 1 (xin)
+template <int FAM, bool INIT>
+__host__ __device__ constexpr bool reads_slot0() {
+  return !is_op(FAM) || FAM == FAM_OPT || INIT;
+}
+template <int FAM, bool ZOWN>
+__host__ __device__ constexpr bool reads_slot1() {
+  return is_op(FAM) ? (FAM == FAM_OP && ZOWN) : FAM != FAM_RES;
 }
 
 // Arguments of one fused smoother step (see kernels_smooth.cu).
@@ -219,6 +239,11 @@ struct CyclePhase {
 struct CycleSync {
   unsigned* count = nullptr;
 };
+// Operator values of a stored-operator step: out = tau I - sigma B over B's
+// layout (B = a level's row-scaled values), in FP64.
+void launch_build_op(const DevMat<double>& B, double tau, double sigma, double* out,
+                     cudaStream_t s);
+
 // the persistent kernel takes levels of at most this many rows (larger ones
 // keep their launches, whose grids hold more warps in flight)
 constexpr int64_t kCycleMaxRows = 65536;

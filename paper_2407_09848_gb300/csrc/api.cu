@@ -90,6 +90,90 @@ Coefs make_coefs(int kind, int k, const double* w, double rho) {
   return c;
 }
 
+// ---- stored-operator form of the polynomial smoothers (FP64 levels) ----
+// Both polynomial families are, with s_j = M^{-1} r_j and B = M^{-1} A,
+//   z_1 = c_1 s_0,  z_j = a_j z_{j-1} + c_j s_{j-1},  s_j = s_{j-1} - B z_j,
+//   x = x_0 + sum_j beta_j z_j
+// (4th kind, Eq. polsmoother / polsmootheropt: a_j = (2j-3)/(2j+1),
+// c_j = (8j-4)/(2j+1)/rho; 1st kind, Algorithm 1: z_{j+1} = d^(j), c_1 =
+// 1/(theta rho), a_{j+1} = rho_j rho_{j-1}, c_{j+1} = 2 rho_j/(delta rho),
+// beta = 1).  Eliminating s gives the three-term recurrence
+//   z_{j+1} = (al_j I - mu_j B) z_j - ga_j z_{j-1},
+//   al_j = a_{j+1} + c_{j+1}/c_j,  mu_j = c_{j+1},  ga_j = c_{j+1} a_j / c_j,
+// and Clenshaw's backward scheme evaluates the weighted sum with one product
+// per step: u_{k+1} = u_{k+2} = 0,
+//   u_j = beta_j s_0 + (al_j I - mu_j B) u_{j+1} - ga_{j+1} u_{j+2},
+//   x = x_0 + c_1 u_1
+// (the same polynomial in B applied to s_0, so the same result up to
+// rounding).  Step q (q = 0 .. k-2) produces u_j, j = k-1-q, as
+//   u_j = h s_0 + g u_{j+2} + (tau I - sigma B) u_{j+1}
+// with u_k = beta_k s_0 folded in; the operator tau I - sigma B of each step
+// is stored in A's layout, so a row costs one multiply-add per stored entry
+// plus one per vector term: 7 to 9 FP64 operations on a 7-point row instead
+// of the recurrence's 10, and two or three vector streams instead of five.
+struct OpStep {
+  double tau = 0, sigma = 0, h = 0, g = 0;
+};
+
+// The steps for the coefficients of one smoother application (polynomial
+// families, k >= 2); returns k - 1.
+int op_plan(const Coefs& cf, OpStep* st) {
+  const int k = cf.k;
+  double a[kMaxDegree + 2] = {}, cc[kMaxDegree + 2] = {}, be[kMaxDegree + 2] = {};
+  for (int j = 1; j <= k; ++j) be[j] = 1.0;
+  if (cf.fam == FAM_CHEB4) {
+    for (int j = 1; j <= k; ++j) {
+      a[j] = cf.c1[j];
+      cc[j] = cf.c2[j];
+      be[j] = cf.beta[j];
+    }
+  } else {
+    cc[1] = cf.c2[0] * cf.rhoinv;
+    for (int j = 1; j < k; ++j) {
+      a[j + 1] = cf.c1[j];
+      cc[j + 1] = cf.c2[j] * cf.rhoinv;
+    }
+  }
+  double al[kMaxDegree + 2] = {}, mu[kMaxDegree + 2] = {}, ga[kMaxDegree + 2] = {};
+  for (int j = 1; j < k; ++j) {
+    al[j] = a[j + 1] + cc[j + 1] / cc[j];
+    mu[j] = cc[j + 1];
+    ga[j] = j >= 2 ? cc[j + 1] * a[j] / cc[j] : 0.0;  // z_0 = 0
+  }
+  for (int q = 0; q < k - 1; ++q) {
+    const int j = k - 1 - q;
+    OpStep o;
+    if (j == k - 1) {  // u_{k-1} = beta_{k-1} s + (al I - mu B)(beta_k s): the product is of s
+      o.tau = be[k - 1] + be[k] * al[k - 1];
+      o.sigma = be[k] * mu[k - 1];
+    } else if (j == k - 2) {  // the u_{j+2} = u_k = beta_k s term joins h
+      o.tau = al[j];
+      o.sigma = mu[j];
+      o.h = be[j] - ga[j + 1] * be[k];
+    } else {
+      o.tau = al[j];
+      o.sigma = mu[j];
+      o.h = be[j];
+      o.g = -ga[j + 1];
+    }
+    if (j == 1) {  // x = x_0 + c_1 u_1
+      o.tau *= cc[1];
+      o.sigma *= cc[1];
+      o.h *= cc[1];
+      o.g *= cc[1];
+    }
+    st[q] = o;
+  }
+  return k - 1;
+}
+
+bool same_coefs(const Coefs& x, const Coefs& y) {
+  if (x.fam != y.fam || x.k != y.k || x.rhoinv != y.rhoinv) return false;
+  for (int j = 0; j <= x.k; ++j)
+    if (x.c1[j] != y.c1[j] || x.c2[j] != y.c2[j] || x.beta[j] != y.beta[j]) return false;
+  return true;
+}
+
 struct Level {
   int64_t n = 0, nnz = 0, stored = 0, nslices = 0, explicit_entries = 0;
   SliceDesc* sd = nullptr;
@@ -130,6 +214,11 @@ struct Level {
   // reverse-mode buffers (allocated on the first backward call)
   void *bx2 = nullptr, *bgx = nullptr, *bgb = nullptr, *bt1 = nullptr, *bt2 = nullptr,
        *bt3 = nullptr;
+  // stored-operator form: one operator per step (stored entries each), built
+  // for the coefficients ops_cf; ops_ok when they match the level's spec
+  std::vector<double*> ops;
+  Coefs ops_cf;
+  bool ops_ok = false;
 };
 
 }  // namespace
@@ -164,13 +253,14 @@ struct amgps_ctx {
   int use_tma = 1;             // TMA-fed step kernels (option AMGPS_OPT_TMA: 0 off, 1 auto, 2 always)
   int flexible = 0;            // AMGPS_OPT_FLEXIBLE: 0 standard, 1 Polak-Ribiere, 2 one-reduction
   int coarse_sweeps = 0;       // AMGPS_OPT_COARSE_SWEEPS: 0 dense Cholesky, m l1-Jacobi sweeps
+  int step_form = 1;           // AMGPS_OPT_STEP_FORM: 0 recurrence, 1 stored operators where built
   int64_t launch_adjust = 0;   // captured (not run) launches removed, replays added
   int64_t launch_base = 0;     // reset point of the launch counter
   bool prof = false;
   struct Pair {
     cudaEvent_t a, b;
     int cls;
-    double bytes;
+    double bytes, flops;
   };
   std::vector<Pair> pending;
   std::vector<cudaEvent_t> pool;
@@ -189,6 +279,7 @@ struct amgps_ctx {
   unsigned* tail_sync = nullptr;   // barrier word (arrivals)
   double prof_ms[5] = {};
   double prof_bytes[5] = {};
+  double prof_flops[5] = {};
 };
 
 namespace {
@@ -295,6 +386,7 @@ void harvest(amgps_ctx* c) {
     c->prof_launches[p.cls] += 1;
     c->prof_ms[p.cls] += ms;
     c->prof_bytes[p.cls] += p.bytes;
+    c->prof_flops[p.cls] += p.flops;
     c->pool.push_back(p.a);
     c->pool.push_back(p.b);
   }
@@ -306,9 +398,9 @@ struct ProfScope {
   bool on;
   cudaEvent_t a{}, b{};
   int cls;
-  double bytes;
-  ProfScope(amgps_ctx* c_, bool want, int cls_, double bytes_) : c(c_), on(want && c_->prof),
-                                                                  cls(cls_), bytes(bytes_) {
+  double bytes, flops;
+  ProfScope(amgps_ctx* c_, bool want, int cls_, double bytes_, double flops_ = 0.0)
+      : c(c_), on(want && c_->prof), cls(cls_), bytes(bytes_), flops(flops_) {
     if (on) {
       a = take_event(c);
       b = take_event(c);
@@ -318,7 +410,7 @@ struct ProfScope {
   void done() {
     if (on) {
       CK(cudaEventRecord(b, c->stream));
-      c->pending.push_back({a, b, cls, bytes});
+      c->pending.push_back({a, b, cls, bytes, flops});
       on = false;
     }
   }
@@ -354,6 +446,28 @@ template <class VT, class XT>
 double step_bytes(const Level& L, int nvec) {
   return (double)L.nnz * sizeof(VT) + (double)L.explicit_entries * 4.0 +
          (double)L.n * sizeof(XT) * nvec;
+}
+
+// Algorithmic FP64 flops of one step (a multiply-add 2, a lone multiply or
+// add 1; nnz products per launch).  Recurrence form (row-scaled FP64
+// families): the SpMV with the residual folded in, c2 r, the c1 z term when
+// present, the x update, and (1/M) rin where rin is still unscaled.
+double step_flops(const Level& L, int fam, bool zown, bool raw) {
+  const double nnz2 = 2.0 * (double)L.nnz, n = (double)L.n;
+  if (fam == FAM_JAC) return nnz2 + 2.0 * n;
+  double per = (fam == FAM_CHEB4 ? 2.0 : 1.0) + 1.0 + (zown ? 2.0 : 0.0);
+  if (!L.sval || raw) per += 1.0;
+  return nnz2 + per * n;
+}
+// Stored-operator step: the products (the first one a lone multiply when no
+// vector term starts the sum), c2 s0 (a multiply) or q (nothing), c1 p, and
+// for FAM_OPT the side output u + beta out.
+double op_flops(const Level& L, int fam, bool s0, bool s0add, bool s1, bool wt) {
+  const double nnz2 = 2.0 * (double)L.nnz, n = (double)L.n;
+  if (fam == FAM_OPT) return nnz2 + (wt ? 2.0 * n : 0.0);
+  double f = nnz2 + (s0 ? (s0add ? 0.0 : n) : -n);
+  if (s1) f += 2.0 * n;
+  return f;
 }
 
 // ---------------------------------------------------------------------------
@@ -487,9 +601,88 @@ struct Engine {
     return L.ntma > 0 && (c->use_tma == 2 || (c->use_tma == 1 && L.ntma >= 4 * c->nsm));
   }
 
-  // One smoother application on level l: x <- S(b, x) (x = 0 when xzero).
-  static void smooth(amgps_ctx* c, int l, const Coefs& cf, const XT* b, XT* x, bool xzero) {
+  // Whether this application on level L runs in the stored-operator form.
+  static bool use_ops(const amgps_ctx* c, const Level& L, const Coefs& cf) {
+    if constexpr (std::is_same<VT, double>::value && std::is_same<XT, double>::value)
+      return c->step_form == 1 && L.ops_ok && !rec() && same_coefs(L.ops_cf, cf);
+    else
+      return false;
+  }
+
+  // One application in the stored-operator form (see op_plan).  Buffers: za
+  // holds c = M^{-1} b (formed here unless c_ready: an application from zero
+  // on the same b left it there), then s_0 = M^{-1}(b - A x_0) in place; the
+  // u_j alternate between zb and xb (u_j overwrites u_{j+2}, which only its
+  // own row reads); r holds x_0 + h s_0 for the last step when k >= 3.
+  static void smooth_ops(amgps_ctx* c, int l, const Coefs& cf, const XT* b, XT* x, bool xzero,
+                         bool c_ready) {
     Level& L = c->lv[l];
+    cudaStream_t s = c->stream;
+    OpStep st[kMaxDegree];
+    const int ns = op_plan(cf, st);
+    const int k = cf.k;
+    XT* cv = (XT*)L.za;
+    XT* U[2] = {(XT*)L.zb, (XT*)L.xb};
+    XT* t = (XT*)L.r;
+    const bool profl = (l == 0);
+    if (!c_ready)
+      do_first(FAM_JAC, L.n, b, (const XT*)L.dinv, nullptr, nullptr, cv, XT(0), XT(0), XT(1), s);
+    const DevMat<VT> A = devmat<VT>(L);
+    if (!xzero) {
+      StepArgs<VT, XT> a;
+      a.A = A;
+      a.A.val = (const VT*)L.sval;
+      a.u = x;
+      a.rin = cv;
+      a.zout = cv;
+      a.fam = FAM_OPT;
+      a.write_r = k >= 3;
+      a.rout = t;
+      a.beta = XT(st[ns - 1].h);
+      ProfScope ps(c, profl, 0, step_bytes<VT, XT>(L, a.write_r ? 4 : 3),
+                   op_flops(L, FAM_OPT, true, true, false, a.write_r));
+      run_step(c, L, a, s);
+      ps.done();
+    }
+    for (int q = 0; q < ns; ++q) {
+      const int j = k - 1 - q;
+      StepArgs<VT, XT> a;
+      a.A = A;
+      a.A.val = (const VT*)L.ops[q];
+      a.fam = FAM_OP;
+      a.u = q == 0 ? cv : U[(q - 1) & 1];
+      a.zout = j == 1 ? x : U[q & 1];
+      if (j == 1 && !xzero) {
+        a.rin = k >= 3 ? t : x;  // x_0 (+ h s_0), added with coefficient 1
+        a.write_r = true;
+      } else if (j <= k - 2) {
+        a.rin = cv;
+        a.c2 = XT(st[q].h);
+      }
+      if (j <= k - 3) {
+        a.xin = U[q & 1];  // u_{j+2}
+        a.c1 = XT(st[q].g);
+      }
+      const int nvec = 2 + (a.rin ? 1 : 0) + (a.xin ? 1 : 0);
+      ProfScope ps(c, profl, 0, step_bytes<VT, XT>(L, nvec),
+                   op_flops(L, FAM_OP, a.rin != nullptr, a.write_r, a.xin != nullptr, false));
+      run_step(c, L, a, s);
+      ps.done();
+    }
+    check_launch();
+  }
+
+  // One smoother application on level l: x <- S(b, x) (x = 0 when xzero).
+  // Returns true when it ran in the stored-operator form (then, from zero,
+  // the level's za holds M^{-1} b for a following application with x given:
+  // pass c_ready there).
+  static bool smooth(amgps_ctx* c, int l, const Coefs& cf, const XT* b, XT* x, bool xzero,
+                     bool c_ready = false) {
+    Level& L = c->lv[l];
+    if (use_ops(c, L, cf)) {
+      smooth_ops(c, l, cf, b, x, xzero, c_ready);
+      return true;
+    }
     cudaStream_t s = c->stream;
     const DevMat<VT> A = devmat<VT>(L);
     const XT* md = (const XT*)L.dinv;
@@ -517,14 +710,14 @@ struct Engine {
         a.dinv = md;
         a.fam = FAM_JAC;
         a.init = true;
-        ProfScope ps(c, profl, 0, step_bytes<VT, XT>(L, 4));
+        ProfScope ps(c, profl, 0, step_bytes<VT, XT>(L, 4), step_flops(L, FAM_JAC, false, false));
         run_step(c, L, a, s);
         ps.done();
         std::swap(cur, oth);
       }
       if (cur != x) do_copy(x, cur, L.n, s);
       check_launch();
-      return;
+      return false;
     }
     const XT* rin_next;
     XT* xcur = x;
@@ -553,7 +746,8 @@ struct Engine {
       a.rhoinv = XT(cf.rhoinv);
       a.fam = cf.fam;
       a.init = true;
-      ProfScope ps(c, profl, 0, step_bytes<VT, XT>(L, a.write_r ? 6 : 5));
+      ProfScope ps(c, profl, 0, step_bytes<VT, XT>(L, a.write_r ? 6 : 5),
+                   step_flops(L, cf.fam, false, true));
       run_step(c, L, a, s);
       ps.done();
       xcur = xb;
@@ -585,7 +779,8 @@ struct Engine {
       a.rin_raw = (rin_next == b);  // first step after k_first: r_0 = b
       // streams: z_j, r in(/out), z_{j+1}, x in/out, and 1/M unless scaled
       const bool no_dinv = L.sval && ((cf.fam == FAM_CHEB4 && !a.rin_raw) || cf.fam == FAM_CHEB1);
-      ProfScope ps(c, profl, 0, step_bytes<VT, XT>(L, (a.write_r ? 7 : 6) - (no_dinv ? 1 : 0)));
+      ProfScope ps(c, profl, 0, step_bytes<VT, XT>(L, (a.write_r ? 7 : 6) - (no_dinv ? 1 : 0)),
+                   step_flops(L, cf.fam, true, a.rin_raw && cf.fam == FAM_CHEB4));
       run_step(c, L, a, s);
       ps.done();
       xcur = x;
@@ -594,6 +789,7 @@ struct Engine {
     }
     if (xcur != x) do_copy(x, xcur, L.n, s);
     check_launch();
+    return false;
   }
 
   // Coarsest level: x = A_c^{-1} b (dense inverse), or with the coarse-sweeps
@@ -626,7 +822,7 @@ struct Engine {
       return;
     }
     const Coefs cf = make_coefs(L.spec.kind, L.spec.k, L.spec.w, L.spec.rho);
-    smooth(c, l, cf, b, x, true);
+    const bool c_kept = smooth(c, l, cf, b, x, true);  // stored-operator form: za = M^{-1} b
     Level& C = c->lv[l + 1];
     {
       // b_{l+1} = P^T (b - A x): the true residual (into the level's r buffer,
@@ -661,7 +857,7 @@ struct Engine {
     if (L.xfer_general) launch_xfer<XT>(L.Pm, (const XT*)C.x, x, 1, L.psplit, s);
     else do_prolong(L, (const XT*)C.x, x, s);
     if (record) CK(cudaMemcpyAsync(L.bx2, x, L.n * sizeof(XT), cudaMemcpyDeviceToDevice, s));
-    smooth(c, l, cf, b, x, false);
+    smooth(c, l, cf, b, x, false, c_kept);
     check_launch();
   }
 
@@ -1012,6 +1208,49 @@ void check_kind_degree(int kind, int degree) {
   REQ(degree >= 1 && degree <= kMaxDegree, AMGPS_E_ARG, "degree must be in 1..16");
 }
 
+// Levels that take the stored-operator form: FP64 values with the row-scaled
+// copy, one warp per slice, and enough TMA tiles for the pipelined kernel
+// (the levels whose steps the FP64 pipe bounds; the small levels below are
+// launch-bound and keep the recurrence).
+bool op_level(const amgps_ctx* c, const Level& L) {
+  return c->prec == AMGPS_F64 && L.sval && !L.coarsest && L.split == 1 &&
+         L.ntma >= 4 * c->nsm;
+}
+
+// Builds, on the library stream, the stored operators of every such level
+// for its current smoother (polynomial kinds, degree >= 2), unless they are
+// already built for it.  A level whose operators would not fit the device or
+// the context's allocation limit keeps the recurrence form; so does every
+// level while the library stream is being captured.
+void prepare_ops(amgps_ctx* c) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(c->stream, &cap));
+  for (size_t l = 0; l + 1 < c->lv.size(); ++l) {
+    Level& L = c->lv[l];
+    const Coefs cf = make_coefs(L.spec.kind, L.spec.k, L.spec.w, L.spec.rho);
+    if (L.ops_ok && same_coefs(L.ops_cf, cf)) continue;
+    L.ops_ok = false;
+    if (c->step_form != 1 || cap != cudaStreamCaptureStatusNone || !op_level(c, L)) continue;
+    if ((cf.fam != FAM_CHEB4 && cf.fam != FAM_CHEB1) || cf.k < 2) continue;
+    const int ns = cf.k - 1;
+    try {
+      while ((int)L.ops.size() < ns)
+        L.ops.push_back((double*)dalloc(c, (size_t)L.stored * sizeof(double)));
+    } catch (const Fail& f) {
+      if (f.st != AMGPS_E_NOMEM) throw;
+      continue;
+    }
+    OpStep st[kMaxDegree];
+    op_plan(cf, st);
+    DevMat<double> B = devmat<double>(L);
+    B.val = (const double*)L.sval;
+    for (int q = 0; q < ns; ++q) launch_build_op(B, st[q].tau, st[q].sigma, L.ops[q], c->stream);
+    check_launch();
+    L.ops_cf = cf;
+    L.ops_ok = true;
+  }
+}
+
 // Outer PCG (Sec. 4): one application of the preconditioner (a V-cycle unless
 // `precond` is given) per iteration; beta = r.z / r_old.z_old, or with the
 // flexible option the Polak-Ribiere beta = r.(z - z_old) / r_old.z_old.
@@ -1339,6 +1578,7 @@ amgps_status amgps_hierarchy_load(amgps_ctx* c, int n_levels, const amgps_csr* A
     free_hierarchy(c);
     try {
       load_levels(c, n_levels, A, P, prec);
+      prepare_ops(c);
     } catch (...) {
       free_hierarchy(c);  // a failed load keeps no buffers
       leave(c);
@@ -1535,6 +1775,9 @@ amgps_status amgps_set_smoother(amgps_ctx* c, int level, amgps_kind kind, int de
       if (weights) std::copy(weights, weights + degree, s.w);
     }
     c->graph_ok = false;
+    enter(c);
+    prepare_ops(c);
+    leave(c);
   });
 }
 
@@ -1902,9 +2145,18 @@ amgps_status amgps_set_option(amgps_ctx* c, int option, int64_t value) {
     REQ(c, AMGPS_E_ARG, "null context");
     REQ(option == AMGPS_OPT_TMA || option == AMGPS_OPT_FLEXIBLE ||
             option == AMGPS_OPT_COARSE_SWEEPS || option == AMGPS_OPT_COARSE_KERNEL ||
-            option == AMGPS_OPT_ALLOC_LIMIT,
+            option == AMGPS_OPT_ALLOC_LIMIT || option == AMGPS_OPT_STEP_FORM,
         AMGPS_E_ARG, "unknown option");
-    if (option == AMGPS_OPT_TMA) {
+    if (option == AMGPS_OPT_STEP_FORM) {
+      REQ(value == 0 || value == 1, AMGPS_E_ARG, "AMGPS_OPT_STEP_FORM takes 0 or 1");
+      c->step_form = (int)value;
+      c->graph_ok = false;
+      if (c->loaded) {
+        enter(c);
+        prepare_ops(c);
+        leave(c);
+      }
+    } else if (option == AMGPS_OPT_TMA) {
       REQ(value >= 0 && value <= 2, AMGPS_E_ARG, "AMGPS_OPT_TMA takes 0, 1 or 2");
       c->use_tma = (int)value;
       c->graph_ok = false;
@@ -1968,6 +2220,27 @@ amgps_status amgps_step_coefs(amgps_kind kind, int degree, const double* weights
       beta[j] = cf.beta[j];
     }
     *rhoinv = cf.rhoinv;
+  });
+}
+
+amgps_status amgps_op_coefs(amgps_kind kind, int degree, const double* weights, double rho,
+                            double* tau, double* sigma, double* h, double* g) {
+  return guard(nullptr, [&] {
+    check_kind_degree(kind, degree);
+    REQ(kind != AMGPS_L1JACOBI && degree >= 2, AMGPS_E_ARG,
+        "the stored-operator form takes the polynomial kinds of degree >= 2");
+    REQ(tau && sigma && h && g, AMGPS_E_ARG, "null argument");
+    REQ(kind != AMGPS_WEIGHTS || weights, AMGPS_E_ARG, "AMGPS_WEIGHTS needs weights");
+    REQ(std::isfinite(rho), AMGPS_E_ARG, "non-finite rho");
+    const Coefs cf = make_coefs(kind, degree, weights, rho);
+    OpStep st[kMaxDegree];
+    const int ns = op_plan(cf, st);
+    for (int q = 0; q < ns; ++q) {
+      tau[q] = st[q].tau;
+      sigma[q] = st[q].sigma;
+      h[q] = st[q].h;
+      g[q] = st[q].g;
+    }
   });
 }
 
@@ -2072,7 +2345,19 @@ amgps_status amgps_profile_read(amgps_ctx* c, int cls, int reset, int64_t* launc
       c->prof_launches[cls] = 0;
       c->prof_ms[cls] = 0.0;
       c->prof_bytes[cls] = 0.0;
+      c->prof_flops[cls] = 0.0;
     }
+  });
+}
+
+amgps_status amgps_profile_flops(amgps_ctx* c, int cls, double* flops) {
+  return guard(c, [&] {
+    REQ(c && flops, AMGPS_E_ARG, "null argument");
+    REQ(cls >= 0 && cls <= 4, AMGPS_E_ARG, "kernel class out of range");
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    harvest(c);
+    *flops = c->prof_flops[cls];
   });
 }
 

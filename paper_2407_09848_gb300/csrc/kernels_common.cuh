@@ -106,17 +106,38 @@ __device__ __forceinline__ XT row_spmv(const DevMat<VT>& A, int64_t s, int lane,
 // r_j = r_{j-1} - A z_j directly for the 4th kind, the 1st-kind initial step
 // and Jacobi (init = r_in, SIGN = -1); the plain product t = A d for the
 // other 1st-kind steps (init = 0, SIGN = +1).
+// The stored-operator steps add their operator's products to the vector terms
+// (FAM_OP) or subtract the row-scaled products from q (FAM_OPT).
 template <int FAM, bool INIT>
 struct StepForm {
   static constexpr bool kResidual = !(FAM == FAM_CHEB1 && !INIT);
-  static constexpr int kSign = kResidual ? -1 : 1;
+  static constexpr int kSign = FAM == FAM_OP ? 1 : (kResidual ? -1 : 1);
 };
 
-// Whether a step reads 1/M: every step but the residual and the scaled
-// 4th-kind step with scaled rin.
+// Whether a step reads 1/M: every step but the residual, the scaled
+// 4th-kind step with scaled rin and the stored-operator steps.
 template <int FAM>
 __device__ __forceinline__ constexpr bool step_needs_dinv() {
-  return FAM != FAM_RES && FAM != FAM_CHEB4S && FAM != FAM_CHEB1S;
+  return FAM != FAM_RES && FAM != FAM_CHEB4S && FAM != FAM_CHEB1S && !is_op(FAM);
+}
+
+// Stored-operator steps: the vector terms the accumulation starts from
+// (s0 = slot-0 entry of the row, s1 = slot-1 entry), then the stores.
+template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN>
+__device__ __forceinline__ XT op_init(const StepArgs<VT, XT>& a, XT s0, XT s1) {
+  XT acc = XT(0);
+  if constexpr (FAM == FAM_OPT) {
+    acc = s0;
+  } else {
+    if constexpr (INIT) acc = WR ? s0 : a.c2 * s0;
+    if constexpr (ZOWN) acc = INIT ? fma(a.c1, s1, acc) : a.c1 * s1;
+  }
+  return acc;
+}
+template <class VT, class XT, int FAM, bool WR>
+__device__ __forceinline__ void op_finish(const StepArgs<VT, XT>& a, int64_t row, XT acc, XT ucen) {
+  a.zout[row] = acc;
+  if constexpr (FAM == FAM_OPT && WR) a.rout[row] = fma(a.beta, acc, ucen);
 }
 
 // Starting value of the accumulation: rin for the residual forms ((1/M) rin
@@ -171,6 +192,19 @@ template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN, bool CG = 
 __device__ __forceinline__ void step_slice(const StepArgs<VT, XT>& a, int64_t s, int lane) {
   const int64_t row = s * kSlice + lane;
   const bool live = row < a.A.n;
+  if constexpr (is_op(FAM)) {
+    XT s0 = XT(0), s1 = XT(0), uc = XT(0);
+    if (live) {
+      if (reads_slot0<FAM, INIT>()) s0 = ldv<CG>(a.rin + row);
+      if (reads_slot1<FAM, ZOWN>()) s1 = ldv<CG>(a.xin + row);
+      if (FAM == FAM_OPT && WR) uc = ldv<CG>(a.u + row);
+    }
+    constexpr int kSign = StepForm<FAM, INIT>::kSign;
+    const XT acc = row_spmv<kSign, VT, XT, CG>(a.A, s, lane, row, a.u,
+                                               op_init<VT, XT, FAM, INIT, WR, ZOWN>(a, s0, s1));
+    if (live) op_finish<VT, XT, FAM, WR>(a, row, acc, uc);
+    return;
+  }
   XT rin = XT(0), xin = XT(0), zo = XT(0), di = XT(0);
   if (live) {
     rin = ldv<CG>(a.rin + row);

@@ -24,6 +24,8 @@
 // their latency overlaps it.  z ping-pongs between two buffers because
 // neighbouring rows gather z_j in the same launch that writes z_{j+1}.  Levels
 // with wide rows use the split form (several warps per slice).
+#include <type_traits>
+
 #include "kernels_common.cuh"
 
 namespace amgps {
@@ -96,10 +98,37 @@ static void dispatch_wr(const StepArgs<VT, XT>& a, int64_t work, cudaStream_t s)
   }
 }
 
+// Stored-operator steps (FP64 levels, one warp per slice): the flags of
+// FAM_OP / FAM_OPT from the arguments.
+template <class VT, class XT>
+static void dispatch_op(const StepArgs<VT, XT>& a, int64_t work, cudaStream_t s) {
+  if constexpr (std::is_same<VT, double>::value && std::is_same<XT, double>::value) {
+    const unsigned g = (unsigned)((work + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    const bool s0 = a.rin != nullptr, s1 = a.xin != nullptr, wr = a.write_r;
+    if (a.fam == FAM_OPT) {
+      if (wr) k_step<VT, XT, FAM_OPT, true, true, false><<<g, kBlock, 0, s>>>(a);
+      else k_step<VT, XT, FAM_OPT, true, false, false><<<g, kBlock, 0, s>>>(a);
+    } else if (!s0) {
+      k_step<VT, XT, FAM_OP, false, false, false><<<g, kBlock, 0, s>>>(a);
+    } else if (!s1) {
+      if (wr) k_step<VT, XT, FAM_OP, true, true, false><<<g, kBlock, 0, s>>>(a);
+      else k_step<VT, XT, FAM_OP, true, false, false><<<g, kBlock, 0, s>>>(a);
+    } else {
+      if (wr) k_step<VT, XT, FAM_OP, true, true, true><<<g, kBlock, 0, s>>>(a);
+      else k_step<VT, XT, FAM_OP, true, false, true><<<g, kBlock, 0, s>>>(a);
+    }
+    count_launch();
+  }
+}
+
 template <class VT, class XT>
 void launch_step(const StepArgs<VT, XT>& a, cudaStream_t s) {
   const int64_t work = a.slices ? a.nlist : a.A.nslices;
   if (work == 0) return;
+  if (is_op(a.fam)) {
+    dispatch_op<VT, XT>(a, work, s);
+    return;
+  }
   switch (a.fam) {
     case FAM_CHEB4:
       if (a.init) dispatch_wr<VT, XT, FAM_CHEB4, true>(a, work, s);
@@ -237,6 +266,40 @@ void launch_l1diag(const DevMat<VT>& A, XT* dinv, cudaStream_t s) {
   if (A.nslices == 0) return;
   dim3 g((unsigned)((A.nslices + kWarpsPerBlock - 1) / kWarpsPerBlock));
   k_l1diag<VT, XT><<<g, kBlock, 0, s>>>(A, dinv);
+  count_launch();
+}
+
+// Operator values of one stored-operator step, m = tau I - sigma B, entry by
+// entry of B's layout.  The row's diagonal slot: offset 0 of a uniform slice,
+// else the first stored column equal to the row (explicit rows are sorted by
+// column and padded after their entries).  Rows past n keep zeros.
+__global__ void __launch_bounds__(kBlock) k_build_op(const DevMat<double> B, double tau,
+                                                     double sigma, double* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (s >= B.nslices) return;
+  const int64_t row = s * kSlice + lane;
+  const SliceDesc d = B.sd[s];
+  bool seen = false;
+  for (int k = 0; k < d.w; ++k) {
+    const int64_t e = d.vbase + (int64_t)k * kSlice + lane;
+    bool dg;
+    if (d.cref >= 0) {
+      dg = B.off[d.cref + k] == 0;
+    } else {
+      dg = !seen && B.col[e] == row;
+      seen = seen || dg;
+    }
+    const double v = B.val[e];
+    out[e] = row < B.n ? (dg ? fma(-sigma, v, tau) : -sigma * v) : 0.0;
+  }
+}
+
+void launch_build_op(const DevMat<double>& B, double tau, double sigma, double* out,
+                     cudaStream_t s) {
+  if (B.nslices == 0) return;
+  dim3 g((unsigned)((B.nslices + kWarpsPerBlock - 1) / kWarpsPerBlock));
+  k_build_op<<<g, kBlock, 0, s>>>(B, tau, sigma, out);
   count_launch();
 }
 

@@ -150,13 +150,15 @@ __global__ void __launch_bounds__((tma_warps<XT>() + 1) * 32, TmaShape<XT>::kCta
             stage_r0[st] = rq;
             // the residual needs no x_in or 1/M; a scaled step with scaled rin no
             // 1/M; FP64 stages hold no 1/M slot (read from global memory)
+            // (a stored-operator step copies the slots it reads)
             constexpr bool wdi = step_needs_dinv<FAM>() && TmaShape<XT>::kVecSlots == 3;
-            constexpr int nvec = FAM == FAM_RES ? 1 : (wdi ? 3 : 2);
+            constexpr bool c0 = reads_slot0<FAM, INIT>(), c1 = reads_slot1<FAM, ZOWN>();
+            constexpr int nvec = (c0 ? 1 : 0) + (c1 ? 1 : 0) + (wdi ? 1 : 0);
             mbar_expect_tx(&full[st], (uint32_t)(p.vals_bytes + nvec * p.vec_bytes + p.win_bytes));
             bulk_g2s(base, a.A.val + vq, (uint32_t)p.vals_bytes, &full[st]);
             XT* sv = reinterpret_cast<XT*>(base + p.vals_bytes);
-            bulk_g2s(sv, a.rin + r0, (uint32_t)p.vec_bytes, &full[st]);
-            if (FAM != FAM_RES) bulk_g2s(sv + p.rows, a.xin + r0, (uint32_t)p.vec_bytes, &full[st]);
+            if (c0) bulk_g2s(sv, a.rin + r0, (uint32_t)p.vec_bytes, &full[st]);
+            if (c1) bulk_g2s(sv + p.rows, a.xin + r0, (uint32_t)p.vec_bytes, &full[st]);
             if (wdi) bulk_g2s(sv + 2 * p.rows, a.dinv + r0, (uint32_t)p.vec_bytes, &full[st]);
             XT* sw = sv + TmaShape<XT>::kVecSlots * p.rows;
             for (int g = 0; g < p.ngroups; ++g)
@@ -210,7 +212,52 @@ __global__ void __launch_bounds__((tma_warps<XT>() + 1) * 32, TmaShape<XT>::kCta
     const XT* sv = reinterpret_cast<const XT*>(base + p.vals_bytes);
     const XT* sw = sv + TmaShape<XT>::kVecSlots * p.rows;
     const int64_t r0 = stage_r0[st];
-    if constexpr (W > 0 && std::is_same<XT, double>::value) {
+    if constexpr (is_op(FAM)) {
+      // stored-operator step: vector terms, then the row's products; with W
+      // fixed a lane takes two rows (slices cs and cs + kCons) interleaved, and
+      // the row's own u entry is the centre product's operand
+      constexpr int kSign = F::kSign;
+      constexpr bool c0 = reads_slot0<FAM, INIT>(), c1 = reads_slot1<FAM, ZOWN>();
+      constexpr int kStep = W > 0 ? 2 * kCons : kCons;
+      for (int cs = cw; cs < spt; cs += kStep) {
+        const int cs2 = cs + kCons;
+        const bool two = W > 0 && cs2 < spt;
+        const int r1 = cs * kSlice + lane, r2 = (two ? cs2 : cs) * kSlice + lane;
+        const VT* v1 = reinterpret_cast<const VT*>(base) + (size_t)cs * p.w * kSlice + lane;
+        const VT* v2 =
+            reinterpret_cast<const VT*>(base) + (size_t)(two ? cs2 : cs) * p.w * kSlice + lane;
+        XT acc1 = op_init<VT, XT, FAM, INIT, WR, ZOWN>(a, c0 ? sv[r1] : XT(0),
+                                                       c1 ? sv[p.rows + r1] : XT(0));
+        XT uc1 = XT(0), uc2 = XT(0);
+        if constexpr (W > 0) {
+          XT acc2 = op_init<VT, XT, FAM, INIT, WR, ZOWN>(a, c0 ? sv[r2] : XT(0),
+                                                         c1 ? sv[p.rows + r2] : XT(0));
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            const XT a1 = widen<XT>(v1[k * kSlice]), a2 = widen<XT>(v2[k * kSlice]);
+            const XT u1 = sw[p.d[k] + r1], u2 = sw[p.d[k] + r2];
+            if (k == W / 2) {
+              uc1 = u1;
+              uc2 = u2;
+            }
+            acc1 = fma(kSign > 0 ? a1 : -a1, u1, acc1);
+            acc2 = fma(kSign > 0 ? a2 : -a2, u2, acc2);
+          }
+          op_finish<VT, XT, FAM, WR>(a, r0 + r1, acc1, uc1);
+          if (two) op_finish<VT, XT, FAM, WR>(a, r0 + r2, acc2, uc2);
+        } else {
+#pragma unroll
+          for (int k = 0; k < kTmaMaxW; ++k) {
+            if (k < p.w) {
+              const XT av = widen<XT>(v1[k * kSlice]);
+              acc1 = fma(kSign > 0 ? av : -av, sw[p.d[k] + r1], acc1);
+            }
+          }
+          if (FAM == FAM_OPT && WR) uc1 = sw[p.d0 + r1];
+          op_finish<VT, XT, FAM, WR>(a, r0 + r1, acc1, uc1);
+        }
+      }
+    } else if constexpr (W > 0 && std::is_same<XT, double>::value) {
       // FP64 rows of fixed width: a lane evaluates two rows of the tile,
       // slices cs and cs + kCons, with their multiply-add chains interleaved
       // (a slot past the tile repeats slice cs and is not stored); each row's
@@ -304,6 +351,27 @@ void launch_wr(const StepArgs<VT, XT>& a, const TmaPlan& p, const TmaTile* tiles
   }
 }
 
+// stored-operator steps (FP64 levels): the flags from the arguments
+template <class VT, class XT, int W>
+void launch_op(const StepArgs<VT, XT>& a, const TmaPlan& p, const TmaTile* tiles, int ntiles,
+               int grid, double* err, cudaStream_t s) {
+  if constexpr (std::is_same<VT, double>::value && std::is_same<XT, double>::value) {
+    const bool s0 = a.rin != nullptr, s1 = a.xin != nullptr, wr = a.write_r;
+    if (a.fam == FAM_OPT) {
+      if (wr) launch_inst<VT, XT, FAM_OPT, true, true, false, W>(a, p, tiles, ntiles, grid, err, s);
+      else launch_inst<VT, XT, FAM_OPT, true, false, false, W>(a, p, tiles, ntiles, grid, err, s);
+    } else if (!s0) {
+      launch_inst<VT, XT, FAM_OP, false, false, false, W>(a, p, tiles, ntiles, grid, err, s);
+    } else if (!s1) {
+      if (wr) launch_inst<VT, XT, FAM_OP, true, true, false, W>(a, p, tiles, ntiles, grid, err, s);
+      else launch_inst<VT, XT, FAM_OP, true, false, false, W>(a, p, tiles, ntiles, grid, err, s);
+    } else {
+      if (wr) launch_inst<VT, XT, FAM_OP, true, true, true, W>(a, p, tiles, ntiles, grid, err, s);
+      else launch_inst<VT, XT, FAM_OP, true, false, true, W>(a, p, tiles, ntiles, grid, err, s);
+    }
+  }
+}
+
 template <class VT, class XT, int FAM, bool INIT, bool WR, bool ZOWN, int W>
 void set_smem_attr(int bytes) {
   cudaFuncSetAttribute(k_step_tma<VT, XT, FAM, INIT, WR, ZOWN, W>,
@@ -331,12 +399,25 @@ void configure_all(int bytes) {
   configure_wr<VT, XT, FAM_CHEB1SR, true, W>(bytes);
   set_smem_attr<VT, XT, FAM_JAC, true, false, false, W>(bytes);
   set_smem_attr<VT, XT, FAM_RES, true, false, false, W>(bytes);
+  if constexpr (std::is_same<VT, double>::value && std::is_same<XT, double>::value) {
+    set_smem_attr<VT, XT, FAM_OPT, true, true, false, W>(bytes);
+    set_smem_attr<VT, XT, FAM_OPT, true, false, false, W>(bytes);
+    set_smem_attr<VT, XT, FAM_OP, false, false, false, W>(bytes);
+    set_smem_attr<VT, XT, FAM_OP, true, true, false, W>(bytes);
+    set_smem_attr<VT, XT, FAM_OP, true, false, false, W>(bytes);
+    set_smem_attr<VT, XT, FAM_OP, true, true, true, W>(bytes);
+    set_smem_attr<VT, XT, FAM_OP, true, false, true, W>(bytes);
+  }
 }
 
 // the family / INIT dispatch for one width variant
 template <class VT, class XT, int W>
 void launch_fam(const StepArgs<VT, XT>& a, const TmaPlan& p, const TmaTile* tiles, int ntiles,
                 int grid, double* err, cudaStream_t s) {
+  if (is_op(a.fam)) {
+    launch_op<VT, XT, W>(a, p, tiles, ntiles, grid, err, s);
+    return;
+  }
   switch (a.fam) {
     case FAM_CHEB4:
       if (a.init) launch_wr<VT, XT, FAM_CHEB4, true, W>(a, p, tiles, ntiles, grid, err, s);
@@ -385,6 +466,8 @@ bool launch_step_tma(const StepArgs<VT, XT>& a, const TmaPlan& p, const TmaTile*
   if (!aligned16(a.A.val) || !aligned16(a.u) || !aligned16(a.rin)) return false;
   if (a.fam != FAM_RES && (!aligned16(a.xin) || !aligned16(a.dinv))) return false;
   if (a.zown && a.zown != a.u) return false;  // z_j at the row is read from u's window
+  if (is_op(a.fam) && !(std::is_same<VT, double>::value && std::is_same<XT, double>::value))
+    return false;  // stored-operator steps exist for FP64 levels only
   // FP64 rows of the 7-point pattern: the fixed-width variant (its centre
   // entry, index 3, is the row itself)
   if constexpr (std::is_same<XT, double>::value) {

@@ -1,0 +1,88 @@
+"""Host logic of the stored-operator form of the polynomial smoothers (no GPU).
+
+The library evaluates each Chebyshev smoother backwards (Clenshaw's scheme on
+the three-term recurrence of its z_j, Sec. 2.1 Eq. polsmoother /
+polsmootheropt, Sec. 2.2 Algorithm 1), one stored operator
+tau I - sigma M^{-1} A per step.  Here the step coefficients that
+amgps_op_coefs returns are applied in numpy exactly as the header documents
+them, and one application must equal the oracle's forward recurrence to
+rounding, for every kind, degree 2..16, rho and starting vector.  A wrong
+sign, index or coefficient anywhere in the derivation changes the polynomial
+and fails by orders of magnitude."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle.smoother import SmootherSpec, l1_diag, smooth
+from paper_2407_09848_gb300 import amgps, build
+from paper_2407_09848_gb300 import problems as pr
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return amgps.lib()
+
+
+@pytest.fixture(scope="module")
+def system():
+    A = pr.to_csr(pr.varcoef(10, sigma=1.0, ell=3.0, seed=3)).tocsr()
+    rng = np.random.default_rng(11)
+    n = A.shape[0]
+    return A, l1_diag(A), rng.standard_normal(n), rng.standard_normal(n)
+
+
+def op_apply(A, M, b, x0, coefs):
+    """x = x0 + v_{k-2}: v_q = h s0 + g v_{q-2} + (tau I - sigma B) w_q."""
+    tau, sigma, h, g = coefs
+    B = sp.diags(1.0 / M) @ A
+    s0 = (b - (A @ x0 if x0 is not None else 0.0)) / M
+    v = []
+    for q in range(len(tau)):
+        w = s0 if q == 0 else v[q - 1]
+        out = tau[q] * w - sigma[q] * (B @ w) + h[q] * s0
+        if q >= 2:
+            out = out + g[q] * v[q - 2]
+        v.append(out)
+    return (x0 if x0 is not None else 0.0) + v[-1]
+
+
+CASES = [(kind, k, rho) for k in range(2, 17)
+         for kind, rho in (("cheb4", 1.0), ("cheb4", 0.9), ("cheb4_opt", 1.0), ("cheb4_opt", 0.9),
+                           ("weights", 0.95), ("cheb1", 1.0), ("cheb1", 0.9), ("cheb1_opt", 1.0))]
+
+
+@pytest.mark.parametrize("kind,k,rho", CASES, ids=lambda v: str(v))
+def test_op_form_equals_oracle_recurrence(lib, system, kind, k, rho):
+    A, M, b, x0 = system
+    w = None
+    beta = None
+    if kind == "weights":
+        w = 1.0 + 0.4 * np.sin(np.arange(1, k + 1))
+        beta = w
+    elif kind == "cheb4_opt":
+        beta = amgps.opt4_weights(k)  # the library's table (pinned against the paper elsewhere)
+    coefs = amgps.op_coefs(kind, k, w, rho)
+    for start in (None, x0):
+        spec = SmootherSpec(kind, k, beta=beta, rho=rho)
+        ref = smooth(A, b, start, spec, M=M)
+        got = op_apply(A, M, b, start, coefs)
+        err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+        assert err <= 1e-13, (kind, k, rho, start is None, err)
+
+
+def test_op_coefs_shape_of_the_steps(lib):
+    # the first step multiplies s0 alone; the second adds s0; from the third
+    # on a step also takes v_{q-2}
+    tau, sigma, h, g = amgps.op_coefs("cheb4_opt", 6)
+    assert len(tau) == 5
+    assert h[0] == 0.0 and g[0] == 0.0 and g[1] == 0.0
+    assert np.all(g[2:] != 0.0) and np.all(h[1:] != 0.0)
+    assert np.all(sigma > 0.0)
+
+
+def test_op_coefs_rejects_jacobi_and_degree_one(lib):
+    with pytest.raises(amgps.AmgpsError):
+        amgps.op_coefs("l1jacobi", 4)
+    with pytest.raises(amgps.AmgpsError):
+        amgps.op_coefs("cheb4_opt", 1)

@@ -595,9 +595,10 @@ def step_hbm_roofline(n_step, ms_step, by_step, traffic=None, kernel=None):
             "bytes_per_launch": by_step / max(n_step, 1), "peak_source": peak_src}
 
 
-def committed_traffic(workload, prec):
+def committed_traffic(workload, prec, step_form=1):
     """ncu DRAM bytes per launch of the level-0 step from the committed capture,
-    when it was taken on the current sources of the step kernels."""
+    when it was taken on the current sources of the step kernels in the same
+    step form."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
     with open(TRAFFIC_FILE) as f:
@@ -605,7 +606,7 @@ def committed_traffic(workload, prec):
     entries = tr if isinstance(tr, list) else [tr]
     for e in entries:
         if (e.get("source_sha256") == step_source_hash() and e.get("workload") == workload
-                and e.get("prec", "f64") == prec):
+                and e.get("prec", "f64") == prec and e.get("step_form", 0) == step_form):
             return e.get("dram_bytes_per_launch")
     return None
 
@@ -663,7 +664,7 @@ def run_ours(a):
     prof, nprof, clk_prof = profiled_pass(S, bd, x, a, torch, smi)
     n_step, ms_step, by_step = prof[PROF_STEP]
     ms_rr, ms_sp, ms_coarse = prof[PROF_RESTRICT][1], prof[PROF_SPMV][1], prof[PROF_COARSE][1]
-    traffic = committed_traffic(workload_name(a), a.prec)
+    traffic = committed_traffic(workload_name(a), a.prec, a.step_form)
     hbm = step_hbm_roofline(n_step, ms_step, by_step, traffic)
     hbm["share_of_solve_time"] = (ms_step / nprof) / ms_per if ms_per else None
     roof = hbm

@@ -323,10 +323,10 @@ amgps_status amgps_synchronize(amgps_ctx* ctx);
  * allocator, so a caller can reject a problem that would not fit its memory
  * share.  Any failed amgps_hierarchy_load leaves no hierarchy loaded and
  * keeps none of its buffers.
- * AMGPS_OPT_STEP_FORM (default 1): how the polynomial smoothers (both
- * Chebyshev kinds and AMGPS_WEIGHTS, degree >= 2) run on FP64 levels that
- * hold at least 4 TMA tiles per SM.  0: the recurrences of Eq. polsmoother /
- * polsmootheropt and Algorithm 1 step by step.  1: the same polynomial
+ * AMGPS_OPT_STEP_FORM (default 1): how the smoothers of degree >= 2 (every
+ * kind) run on FP64 levels that hold at least 4 TMA tiles per SM.  0: the
+ * recurrences of Eq. polsmoother / polsmootheropt, Algorithm 1 and
+ * Eq. l1smooth step by step.  1: the same polynomial
  * evaluated backwards (Clenshaw's scheme on its three-term recurrence) with
  * each step's operator tau_j I - sigma_j M^{-1} A stored in A's layout --
  * degree - 1 extra arrays of A's stored entries per such level, built by
@@ -393,8 +393,8 @@ amgps_status amgps_sell_layout(const amgps_csr* A, int64_t* nslices, int64_t* st
                                double* val, int32_t* col, int32_t* off);
 
 /* Host-only query: the steps of one smoother application in the
- * stored-operator form (AMGPS_OPT_STEP_FORM 1) for a Chebyshev kind or
- * AMGPS_WEIGHTS (weights as in amgps_set_smoother) and degree k in 2..16.
+ * stored-operator form (AMGPS_OPT_STEP_FORM 1) for any kind (AMGPS_WEIGHTS:
+ * weights as in amgps_set_smoother) and degree k in 2..16.
  * With B = M^{-1} A and s0 = M^{-1} (b - A x0), step q = 0 .. k-2 forms
  *   v_q = h[q] s0 + g[q] v_{q-2} + (tau[q] I - sigma[q] B) w_q,
  *   w_0 = s0, w_q = v_{q-1} (v_{-1} = v_{-2} = 0),

@@ -91,13 +91,15 @@ Coefs make_coefs(int kind, int k, const double* w, double rho) {
 }
 
 // ---- stored-operator form of the polynomial smoothers (FP64 levels) ----
-// Both polynomial families are, with s_j = M^{-1} r_j and B = M^{-1} A,
+// Both polynomial families and l1-Jacobi are, with s_j = M^{-1} r_j and
+// B = M^{-1} A,
 //   z_1 = c_1 s_0,  z_j = a_j z_{j-1} + c_j s_{j-1},  s_j = s_{j-1} - B z_j,
 //   x = x_0 + sum_j beta_j z_j
 // (4th kind, Eq. polsmoother / polsmootheropt: a_j = (2j-3)/(2j+1),
 // c_j = (8j-4)/(2j+1)/rho; 1st kind, Algorithm 1: z_{j+1} = d^(j), c_1 =
 // 1/(theta rho), a_{j+1} = rho_j rho_{j-1}, c_{j+1} = 2 rho_j/(delta rho),
-// beta = 1).  Eliminating s gives the three-term recurrence
+// beta = 1; l1-Jacobi, Eq. l1smooth: a_j = 0, c_j = 1, beta = 1).
+// Eliminating s gives the three-term recurrence
 //   z_{j+1} = (al_j I - mu_j B) z_j - ga_j z_{j-1},
 //   al_j = a_{j+1} + c_{j+1}/c_j,  mu_j = c_{j+1},  ga_j = c_{j+1} a_j / c_j,
 // and Clenshaw's backward scheme evaluates the weighted sum with one product
@@ -115,8 +117,8 @@ struct OpStep {
   double tau = 0, sigma = 0, h = 0, g = 0;
 };
 
-// The steps for the coefficients of one smoother application (polynomial
-// families, k >= 2); returns k - 1.
+// The steps for the coefficients of one smoother application (k >= 2);
+// returns k - 1.
 int op_plan(const Coefs& cf, OpStep* st) {
   const int k = cf.k;
   double a[kMaxDegree + 2] = {}, cc[kMaxDegree + 2] = {}, be[kMaxDegree + 2] = {};
@@ -127,6 +129,8 @@ int op_plan(const Coefs& cf, OpStep* st) {
       cc[j] = cf.c2[j];
       be[j] = cf.beta[j];
     }
+  } else if (cf.fam == FAM_JAC) {  // x_j = x_{j-1} + M^{-1} r_{j-1}: z_j = s_{j-1}
+    for (int j = 1; j <= k; ++j) cc[j] = 1.0;
   } else {
     cc[1] = cf.c2[0] * cf.rhoinv;
     for (int j = 1; j < k; ++j) {
@@ -808,8 +812,10 @@ struct Engine {
     }
   }
 
-  // record: keep each level's post-smoother input (for the reverse pass)
-  static void vcycle_level(amgps_ctx* c, int l, const XT* b, XT* x, bool record = false) {
+  // record: keep each level's post-smoother input (for the reverse pass);
+  // c_ready: the level's za already holds M^{-1} b (written by the PCG update)
+  static void vcycle_level(amgps_ctx* c, int l, const XT* b, XT* x, bool record = false,
+                           bool c_ready = false) {
     Level& L = c->lv[l];
     cudaStream_t s = c->stream;
     if (!record && !rec() && c->tail_ok && l == c->tail_level && b == (const XT*)L.b &&
@@ -822,7 +828,8 @@ struct Engine {
       return;
     }
     const Coefs cf = make_coefs(L.spec.kind, L.spec.k, L.spec.w, L.spec.rho);
-    const bool c_kept = smooth(c, l, cf, b, x, true);  // stored-operator form: za = M^{-1} b
+    // stored-operator form: za = M^{-1} b afterwards, for the post-smoother
+    const bool c_kept = smooth(c, l, cf, b, x, true, c_ready);
     Level& C = c->lv[l + 1];
     {
       // b_{l+1} = P^T (b - A x): the true residual (into the level's r buffer,
@@ -1132,12 +1139,13 @@ struct Engine {
     c->graph_ok = true;
   }
 
-  // z = B r on level 0 with FP64 vectors at the boundary.
-  static void vcycle(amgps_ctx* c, const double* r, double* z) {
+  // z = B r on level 0 with FP64 vectors at the boundary (c_ready: level 0's
+  // za already holds M^{-1} r, see pcg_impl).
+  static void vcycle(amgps_ctx* c, const double* r, double* z, bool c_ready = false) {
     build_graph(c);
     Level& L = c->lv[0];
     if constexpr (std::is_same<XT, double>::value) {
-      vcycle_level(c, 0, r, z);
+      vcycle_level(c, 0, r, z, false, c_ready);
     } else {
       launch_convert<double, XT>(L.n, r, (XT*)L.b, c->stream);
       vcycle_level(c, 0, (const XT*)L.b, (XT*)L.x);
@@ -1218,7 +1226,7 @@ bool op_level(const amgps_ctx* c, const Level& L) {
 }
 
 // Builds, on the library stream, the stored operators of every such level
-// for its current smoother (polynomial kinds, degree >= 2), unless they are
+// for its current smoother (degree >= 2), unless they are
 // already built for it.  A level whose operators would not fit the device or
 // the context's allocation limit keeps the recurrence form; so does every
 // level while the library stream is being captured.
@@ -1231,7 +1239,7 @@ void prepare_ops(amgps_ctx* c) {
     if (L.ops_ok && same_coefs(L.ops_cf, cf)) continue;
     L.ops_ok = false;
     if (c->step_form != 1 || cap != cudaStreamCaptureStatusNone || !op_level(c, L)) continue;
-    if ((cf.fam != FAM_CHEB4 && cf.fam != FAM_CHEB1) || cf.k < 2) continue;
+    if (cf.k < 2) continue;
     const int ns = cf.k - 1;
     try {
       while ((int)L.ops.size() < ns)
@@ -1328,6 +1336,12 @@ void pcg_impl(amgps_ctx* c, const double* b, double* x, double rtol, int maxit, 
     return;
   }
   Level& L = c->lv[0];
+  // The V-cycle's level-0 smoother starts from c = M^{-1} r in the
+  // stored-operator form: the r update writes it (one stream less than a
+  // pass of its own), and the V-cycle skips its c pass.
+  const bool fuse_c = !precond && c->prec == AMGPS_F64 && c->step_form == 1 && !L.coarsest &&
+                      L.ops_ok &&
+                      same_coefs(L.ops_cf, make_coefs(L.spec.kind, L.spec.k, L.spec.w, L.spec.rho));
   cudaStream_t s = c->stream;
   const int64_t n = L.n;
   const DevMat<double> A = devmat64(L, c->prec);
@@ -1363,7 +1377,10 @@ void pcg_impl(amgps_ctx* c, const double* b, double* x, double rtol, int maxit, 
       ps.done();
     }
     // r -= alpha q now; x += alpha p is deferred to the direction update
-    launch_r_update(n, c->pq, c->pr, rw_upd, c->dscal, s);
+    if (fuse_c)
+      launch_r_update(n, c->pq, c->pr, rw_upd, c->dscal, s, (const double*)L.dinv, (double*)L.za);
+    else
+      launch_r_update(n, c->pq, c->pr, rw_upd, c->dscal, s);
     check_launch();
     CK(cudaMemcpyAsync(c->hscal, c->dscal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaEventRecord(c->ev_sync, s));
@@ -1383,7 +1400,10 @@ void pcg_impl(amgps_ctx* c, const double* b, double* x, double rtol, int maxit, 
       break;
     }
     std::swap(z, zo);
-    M(c->pr, z);
+    if (fuse_c)
+      Engine<double, double>::vcycle(c, c->pr, z, true);
+    else
+      M(c->pr, z);
     if (c->flexible == 1) launch_dot(n, c->pr, zo, rw_dot, c->dscal, S_RZP, 0, s);
     launch_dot(n, c->pr, z, rw_dot, c->dscal, S_RZ, c->flexible == 1 ? 2 : 1, s);
     launch_xpay_x(n, z, c->pp, x, c->dscal, 1, s);  // x += alpha p; p = z + beta p
@@ -2227,8 +2247,7 @@ amgps_status amgps_op_coefs(amgps_kind kind, int degree, const double* weights, 
                             double* tau, double* sigma, double* h, double* g) {
   return guard(nullptr, [&] {
     check_kind_degree(kind, degree);
-    REQ(kind != AMGPS_L1JACOBI && degree >= 2, AMGPS_E_ARG,
-        "the stored-operator form takes the polynomial kinds of degree >= 2");
+    REQ(degree >= 2, AMGPS_E_ARG, "the stored-operator form takes degrees >= 2");
     REQ(tau && sigma && h && g, AMGPS_E_ARG, "null argument");
     REQ(kind != AMGPS_WEIGHTS || weights, AMGPS_E_ARG, "AMGPS_WEIGHTS needs weights");
     REQ(std::isfinite(rho), AMGPS_E_ARG, "non-finite rho");

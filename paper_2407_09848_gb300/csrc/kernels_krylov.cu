@@ -167,24 +167,32 @@ void launch_fcg_update(int64_t n, const double* z, const double* w, double* p, d
 }
 
 // r -= alpha q ; r.r (S_RR).  The x update of the same iteration is deferred
-// to k_xpay_x, which reads p anyway.
+// to k_xpay_x, which reads p anyway.  WC: also c = M^{-1} r (the product the
+// stored-operator smoother of the next V-cycle starts from, same operation
+// as its own c pass).
+template <bool WC>
 __global__ void __launch_bounds__(kBlock) k_r_update(int64_t n, const double* __restrict__ q,
                                                      double* __restrict__ r, const RedWork w,
-                                                     double* scal) {
+                                                     double* scal, const double* __restrict__ dinv,
+                                                     double* __restrict__ cout) {
   const double alpha = scal[S_ALPHA];
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * kBlock) {
     const double ri = fma(-alpha, q[i], r[i]);
     r[i] = ri;
+    if constexpr (WC) cout[i] = ri * dinv[i];
     acc = fma(ri, ri, acc);
   }
   grid_sum(acc, w, [&](double tot) { scal[S_RR] = tot; });
 }
 
 void launch_r_update(int64_t n, const double* q, double* r, const RedWork& w, double* scal,
-                     cudaStream_t s) {
-  k_r_update<<<w.grid, kBlock, 0, s>>>(n, q, r, w, scal);
+                     cudaStream_t s, const double* dinv, double* cout) {
+  if (cout)
+    k_r_update<true><<<w.grid, kBlock, 0, s>>>(n, q, r, w, scal, dinv, cout);
+  else
+    k_r_update<false><<<w.grid, kBlock, 0, s>>>(n, q, r, w, scal, nullptr, nullptr);
   count_launch();
 }
 

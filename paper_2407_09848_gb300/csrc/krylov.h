@@ -34,10 +34,11 @@ void launch_spmv_dot3(const DevMat<double>& A, const double* z, double* w, const
 void launch_fcg_update(int64_t n, const double* z, const double* w, double* p, double* q,
                        double* x, double* r, int first, const RedWork& rw, double* scal,
                        cudaStream_t s);
-// standard PCG with the x update deferred: r -= alpha q and r.r; later
-// x += alpha p together with p = z + beta p (with_p = 0: x only)
+// standard PCG with the x update deferred: r -= alpha q and r.r (with cout:
+// also cout = dinv .* r); later x += alpha p together with p = z + beta p
+// (with_p = 0: x only)
 void launch_r_update(int64_t n, const double* q, double* r, const RedWork& w, double* scal,
-                     cudaStream_t s);
+                     cudaStream_t s, const double* dinv = nullptr, double* cout = nullptr);
 void launch_xpay_x(int64_t n, const double* z, double* p, double* x, const double* scal,
                    int with_p, cudaStream_t s);
 // rz_mode 0: scal[out_slot] = a.b.  1: scal[S_RZOLD] <- scal[S_RZ], scal[S_RZ] = a.b,

@@ -53,7 +53,7 @@ def dev(torch, v):
 
 SPECS = [("cheb4_opt", 2), ("cheb4_opt", 3), ("cheb4_opt", 4), ("cheb4_opt", 6),
          ("cheb4_opt", 16), ("cheb4", 3), ("weights", 4), ("cheb1", 2), ("cheb1", 4),
-         ("cheb1_opt", 3)]
+         ("cheb1_opt", 3), ("l1jacobi", 2), ("l1jacobi", 5)]
 
 
 def set_spec(S, kind, k):

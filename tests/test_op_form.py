@@ -1,8 +1,8 @@
-"""Host logic of the stored-operator form of the polynomial smoothers (no GPU).
+"""Host logic of the stored-operator form of the smoothers (no GPU).
 
-The library evaluates each Chebyshev smoother backwards (Clenshaw's scheme on
-the three-term recurrence of its z_j, Sec. 2.1 Eq. polsmoother /
-polsmootheropt, Sec. 2.2 Algorithm 1), one stored operator
+The library evaluates each smoother backwards (Clenshaw's scheme on the
+three-term recurrence of its z_j: Sec. 2.1 Eq. polsmoother / polsmootheropt,
+Sec. 2.2 Algorithm 1, and l1-Jacobi, Eq. l1smooth), one stored operator
 tau I - sigma M^{-1} A per step.  Here the step coefficients that
 amgps_op_coefs returns are applied in numpy exactly as the header documents
 them, and one application must equal the oracle's forward recurrence to
@@ -49,7 +49,8 @@ def op_apply(A, M, b, x0, coefs):
 
 CASES = [(kind, k, rho) for k in range(2, 17)
          for kind, rho in (("cheb4", 1.0), ("cheb4", 0.9), ("cheb4_opt", 1.0), ("cheb4_opt", 0.9),
-                           ("weights", 0.95), ("cheb1", 1.0), ("cheb1", 0.9), ("cheb1_opt", 1.0))]
+                           ("weights", 0.95), ("cheb1", 1.0), ("cheb1", 0.9), ("cheb1_opt", 1.0),
+                           ("l1jacobi", 1.0))]
 
 
 @pytest.mark.parametrize("kind,k,rho", CASES, ids=lambda v: str(v))
@@ -81,8 +82,16 @@ def test_op_coefs_shape_of_the_steps(lib):
     assert np.all(sigma > 0.0)
 
 
-def test_op_coefs_rejects_jacobi_and_degree_one(lib):
-    with pytest.raises(amgps.AmgpsError):
-        amgps.op_coefs("l1jacobi", 4)
+def test_op_coefs_l1jacobi_steps(lib):
+    # l1-Jacobi (a_j = 0, c_j = 1): u_{k-1} = (2 I - B) s0, then
+    # u_j = s0 + (I - B) u_{j+1}, with no u_{j+2} term
+    tau, sigma, h, g = amgps.op_coefs("l1jacobi", 5)
+    assert np.array_equal(tau, [2.0, 1.0, 1.0, 1.0]) and np.all(sigma == 1.0)
+    assert np.array_equal(h, [0.0, 1.0, 1.0, 1.0]) and np.all(g == 0.0)
+
+
+def test_op_coefs_rejects_degree_one(lib):
     with pytest.raises(amgps.AmgpsError):
         amgps.op_coefs("cheb4_opt", 1)
+    with pytest.raises(amgps.AmgpsError):
+        amgps.op_coefs("l1jacobi", 1)

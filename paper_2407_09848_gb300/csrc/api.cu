@@ -1217,12 +1217,12 @@ void check_kind_degree(int kind, int degree) {
 }
 
 // Levels that take the stored-operator form: FP64 values with the row-scaled
-// copy, one warp per slice, and enough TMA tiles for the pipelined kernel
-// (the levels whose steps the FP64 pipe bounds; the small levels below are
-// launch-bound and keep the recurrence).
+// copy, one warp per slice, and at least kOpMinRows rows (whichever step
+// kernel runs them; the smaller levels are launch-bound, and their operators
+// would only take memory).
+constexpr int64_t kOpMinRows = 1 << 17;
 bool op_level(const amgps_ctx* c, const Level& L) {
-  return c->prec == AMGPS_F64 && L.sval && !L.coarsest && L.split == 1 &&
-         L.ntma >= 4 * c->nsm;
+  return c->prec == AMGPS_F64 && L.sval && !L.coarsest && L.split == 1 && L.n >= kOpMinRows;
 }
 
 // Builds, on the library stream, the stored operators of every such level

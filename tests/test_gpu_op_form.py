@@ -1,14 +1,15 @@
 """GPU parity of the stored-operator form of the polynomial smoothers.
 
-On FP64 levels with at least 4 TMA tiles per SM the library evaluates each
+On FP64 levels of at least 131,072 rows the library evaluates each
 polynomial smoother backwards (Clenshaw's scheme, one stored operator
 tau I - sigma M^{-1} A per step).  It is the same polynomial as the forward
 recurrences of Sec. 2.1 (Eq. polsmoother, Eq. polsmootheropt) and Sec. 2.2
 (Algorithm 1), so it must meet the oracle at the FP64 tolerance of every
 smoother application (relative 2-norm and largest element <= 1e-12), give
 identical PCG iteration counts, and run the same bits through the TMA-fed and
-the direct kernels.  The levels here just pass the 608-tile threshold, with
-a ragged last slice and a 512-wide grid whose +-nx offsets share one window.
+the direct kernels.  Two levels just pass the 608-tile threshold of the
+TMA-fed kernel (a ragged last slice; a 512-wide grid whose +-nx offsets share
+one window); a third (64^3) takes the form through the direct kernel only.
 """
 import numpy as np
 import pytest
@@ -25,6 +26,8 @@ GRIDS = {
     "varcoef81": lambda: pr.varcoef(81, 1.0, 4.0, seed=5, ny=72, nz=63),
     # 512 x 24 x 28 = 344,064 rows: 672 tiles, merged +-nx window
     "poisson512": lambda: pr.poisson(512, 24, 28),
+    # 64^3 = 262,144 rows: 512 tiles, below the TMA threshold (direct kernel)
+    "varcoef64": lambda: pr.varcoef(64, 1.0, 4.0, seed=9),
 }
 
 
@@ -42,7 +45,8 @@ def torch_cuda():
 def case(request, torch_cuda):
     from paper_2407_09848_gb300.amgps import Solver, tma_plan_stats
     H = pr.build_hierarchy(GRIDS[request.param](), coarse_max=512)
-    assert tma_plan_stats(H.levels[0].A, "f64")[0] >= 4 * 152
+    tiles = tma_plan_stats(H.levels[0].A, "f64")[0]
+    assert (tiles < 4 * 152) == (request.param == "varcoef64")
     S = Solver().load(H.A, H.P)
     return request.param, H, S
 

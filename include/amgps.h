@@ -40,7 +40,8 @@ extern "C" {
 
 typedef enum {
   AMGPS_OK = 0,
-  AMGPS_E_ARG = 1,      /* bad argument: null pointer, malformed CSR, size mismatch, bad kind/degree */
+  AMGPS_E_ARG = 1,      /* bad argument: null pointer, malformed CSR, size mismatch,
+                           bad kind/degree */
   AMGPS_E_NOT_SPD = 2,  /* non-positive diagonal, Cholesky pivot <= 0, or p^T A p <= 0 in PCG */
   AMGPS_E_NOCONV = 3,   /* PCG reached maxit without meeting rtol (x holds the last iterate) */
   AMGPS_E_NAN = 4,      /* a NaN/Inf appeared in a PCG scalar */

@@ -226,7 +226,8 @@ struct CyclePhase {
   StepArgs<VT, XT> a;    // CY_STEP (direct form, every slice of the level)
   const int32_t* i0 = nullptr;  // CY_AGG: cptr; CY_PROLONG: agg
   const int32_t* i1 = nullptr;  // CY_AGG: cidx
-  const XT* in0 = nullptr;      // CY_FIRST: b; CY_AGG: res; CY_PROLONG: e_c; CY_GEMV: b; CY_COPY: src
+  // CY_FIRST: b; CY_AGG: res; CY_PROLONG: e_c; CY_GEMV: b; CY_COPY: src
+  const XT* in0 = nullptr;
   const XT* in1 = nullptr;      // CY_FIRST: 1/M
   XT* out0 = nullptr;           // CY_FIRST: r; CY_AGG: b_c; CY_PROLONG, CY_GEMV: x; CY_COPY: dst
   XT* out1 = nullptr;           // CY_FIRST: z

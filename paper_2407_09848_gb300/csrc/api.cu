@@ -78,7 +78,8 @@ Coefs make_coefs(int kind, int k, const double* w, double rho) {
     c.rhoinv = (kind == AMGPS_CHEB1_OPT) ? 1.0 : 1.0 / rho;
     return c;
   }
-  // Eq. polsmoother / polsmootheropt: z_j = (2j-3)/(2j+1) z_{j-1} + (8j-4)/(2j+1)/rho M^{-1} r_{j-1}
+  // Eq. polsmoother / polsmootheropt:
+  //   z_j = (2j-3)/(2j+1) z_{j-1} + (8j-4)/(2j+1)/rho M^{-1} r_{j-1}
   c.fam = FAM_CHEB4;
   for (int j = 1; j <= k; ++j) {
     c.c1[j] = double(2 * j - 3) / double(2 * j + 1);
@@ -254,7 +255,7 @@ struct amgps_ctx {
   cudaGraphExec_t gexec = nullptr;
   bool graph_ok = false;
   int64_t graph_kernels = 0;   // kernel nodes in gexec
-  int use_tma = 1;             // TMA-fed step kernels (option AMGPS_OPT_TMA: 0 off, 1 auto, 2 always)
+  int use_tma = 1;             // AMGPS_OPT_TMA: TMA-fed step kernels 0 off, 1 auto, 2 always
   int flexible = 0;            // AMGPS_OPT_FLEXIBLE: 0 standard, 1 Polak-Ribiere, 2 one-reduction
   int coarse_sweeps = 0;       // AMGPS_OPT_COARSE_SWEEPS: 0 dense Cholesky, m l1-Jacobi sweeps
   int step_form = 1;           // AMGPS_OPT_STEP_FORM: 0 recurrence, 1 stored operators where built
@@ -977,7 +978,8 @@ struct Engine {
     else launch_aggregate<XT>(L.cptr, L.cidx, L.nc, t2, (XT*)C.bgx, s);
     vcycle_bwd(c, l + 1, (const XT*)C.b, (const XT*)C.bgx, (XT*)C.bgb);
     CK(cudaMemsetAsync(t3, 0, L.n * sizeof(XT), s));
-    if (L.xfer_general) launch_xfer<XT>(L.Pm, (const XT*)C.bgb, t3, 1, L.psplit, s);  // dL/dres = P dL/db_c
+    // dL/dres = P dL/db_c
+    if (L.xfer_general) launch_xfer<XT>(L.Pm, (const XT*)C.bgb, t3, 1, L.psplit, s);
     else launch_prolong<XT>(L.n, L.agg, (const XT*)C.bgb, t3, s);
     launch_add<XT>(L.n, t1, t3, gbout, s);
     {
@@ -1828,7 +1830,9 @@ amgps_status amgps_smooth(amgps_ctx* c, int level, amgps_kind kind, int degree, 
         "AMGPS_WEIGHTS: set the level's weights of this degree first");
     const Coefs cf = make_coefs(kind, degree, sp.w, sp.rho);
     enter(c);
-    with_engine(c, [&](auto eng) { decltype(eng)::smooth_public(c, level, cf, b, x, x_is_zero != 0); });
+    with_engine(c, [&](auto eng) {
+      decltype(eng)::smooth_public(c, level, cf, b, x, x_is_zero != 0);
+    });
     leave(c);
   });
 }

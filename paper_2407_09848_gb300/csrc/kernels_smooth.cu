@@ -203,7 +203,8 @@ template <class XT>
 void launch_aggregate(const int32_t* cptr, const int32_t* cidx, int64_t nc, const XT* res, XT* bc,
                       cudaStream_t s) {
   if (nc == 0) return;
-  k_aggregate<XT><<<(unsigned)((nc + kBlock - 1) / kBlock), kBlock, 0, s>>>(cptr, cidx, nc, res, bc);
+  const unsigned g = (unsigned)((nc + kBlock - 1) / kBlock);
+  k_aggregate<XT><<<g, kBlock, 0, s>>>(cptr, cidx, nc, res, bc);
   count_launch();
 }
 

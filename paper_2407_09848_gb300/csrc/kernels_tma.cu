@@ -14,11 +14,15 @@
 // on "full", evaluate the rows from shared memory, store r/z/x to global
 // memory, and arrive on the stage's "empty" mbarrier so the producer may
 // refill it.  Before the tiles, while the first copies land, all consumers
-// run the slices outside the plan with direct loads.  The arithmetic and its order are those of k_step,
-// so both paths give the same bits.  Tile height, groups and CTAs per SM come
-// from TmaShape<XT>: for FP64 one CTA per SM with two groups of 8 warps and
-// four 512-row stages in flight (the FP64-bound consumers then never wait for
-// a copy), for FP32 vectors two CTAs per SM of 16 consumers on 1024-row tiles.
+// run the slices outside the plan with direct loads.  The arithmetic and its
+// order are those of k_step, so both paths give the same bits.  The same
+// pipeline runs the recurrence steps and the stored-operator steps (FAM_OP,
+// FAM_OPT), whose values are the step's own operator and whose per-row
+// vectors are copied only when the step reads them.  Tile height, groups and
+// CTAs per SM come from TmaShape<XT>: for FP64 one CTA per SM with two groups
+// of 8 warps and four 512-row stages in flight (copies issued three tiles
+// ahead of the FP64-bound consumers), for FP32 vectors two CTAs per SM of 16
+// consumers on 1024-row tiles.
 //
 // Rows of the 7-point pattern (seven sorted offsets, the row itself in the
 // middle) take a variant with the width fixed at compile time: exactly seven

@@ -325,8 +325,9 @@ amgps_status amgps_synchronize(amgps_ctx* ctx);
  * share.  Any failed amgps_hierarchy_load leaves no hierarchy loaded and
  * keeps none of its buffers.
  * AMGPS_OPT_STEP_FORM (default 1): how the smoothers of degree >= 2 (every
- * kind) run on FP64 levels of at least 131,072 rows whose rows average
- * fewer than 24 stored entries (one warp per slice).  0: the
+ * kind) run on FP64 levels of at least 131,072 rows that the step kernel
+ * evaluates one warp per 32-row slice (every level whose rows average fewer
+ * than 24 stored entries, and wider ones with enough slices).  0: the
  * recurrences of Eq. polsmoother / polsmootheropt, Algorithm 1 and
  * Eq. l1smooth step by step.  1: the same polynomial
  * evaluated backwards (Clenshaw's scheme on its three-term recurrence) with

@@ -580,8 +580,10 @@ def profiled_pass(S, bd, x, a, torch, smi):
         torch.cuda.synchronize()
     S.profile(False)
     flops = S.profile_flops(PROF_STEP)  # before the reset below
+    inst = S.profile_fp64_inst(PROF_STEP)
     out = {c: S.profile_read(c, reset=True) for c in classes}
     out["step_flops"] = flops
+    out["step_fp64_inst"] = inst
     return out, a.steps, clk.summary()
 
 
@@ -682,9 +684,15 @@ def run_ours(a):
         mhz = clk_prof.get("sm_mhz") or 2070.0
         fpeak = 304 * 2 * mhz * 1e6 / 1e12
         fach = fl / (1e-3 * ms_step / n_step) / 1e12
+        # FP64 issue: thread instructions per launch (one per stored entry and
+        # per vector term) against 304 per clock; a lone multiply is one flop
+        # but a whole issue slot, so this is the pipe's utilisation
+        inst = prof["step_fp64_inst"] / n_step
+        issue = inst / (1e-3 * ms_step / n_step) / (304 * mhz * 1e6)
         roof = {"bound": "alu", "achieved": fach, "peak": fpeak, "unit": "TFLOP/s",
                 "frac": fach / fpeak, "traffic": traffic, "kernel": hbm["kernel"],
-                "flops_per_launch": fl,
+                "flops_per_launch": fl, "fp64_inst_per_launch": inst,
+                "fp64_issue_frac": issue,
                 "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2 flops x sampled SM clock",
                 "launches": n_step, "avg_launch_us": hbm["avg_launch_us"],
                 "share_of_solve_time": hbm["share_of_solve_time"], "hbm": hbm}

@@ -436,6 +436,14 @@ amgps_status amgps_profile_read(amgps_ctx* ctx, int kernel_class, int reset,
  * before the amgps_profile_read call that resets the class.  Synchronous. */
 amgps_status amgps_profile_flops(amgps_ctx* ctx, int kernel_class, double* flops);
 
+/* The FP64 thread instructions the same launches issue (class 0; others 0):
+ * one multiply-add per stored matrix entry, zeros of the SELL padding
+ * included, plus one per vector term of a row.  Against the FP64 issue rate
+ * (2 per clock per SM on GB300) it gives the pipe's utilisation, which the
+ * flop count understates where a lone multiply takes a whole issue slot.
+ * Read it before the resetting amgps_profile_read.  Synchronous. */
+amgps_status amgps_profile_fp64_inst(amgps_ctx* ctx, int kernel_class, double* inst);
+
 #ifdef __cplusplus
 }
 #endif

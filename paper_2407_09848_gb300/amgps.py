@@ -105,6 +105,7 @@ _SIGS = {
     "amgps_profile_read": ([C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double),
                             C.POINTER(C.c_double)], C.c_int),
     "amgps_profile_flops": ([C.c_void_p, C.c_int, C.POINTER(C.c_double)], C.c_int),
+    "amgps_profile_fp64_inst": ([C.c_void_p, C.c_int, C.POINTER(C.c_double)], C.c_int),
     "amgps_op_coefs": ([C.c_int, C.c_int, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p,
                         C.c_void_p, C.c_void_p], C.c_int),
 }
@@ -571,6 +572,13 @@ class Solver:
         reset (read before profile_read(cls, reset=True))."""
         f = C.c_double()
         self._check(lib().amgps_profile_flops(self._h, cls, C.byref(f)))
+        return f.value
+
+    def profile_fp64_inst(self, cls):
+        """FP64 thread instructions of the class's timed launches since its
+        last reset (read before profile_read(cls, reset=True))."""
+        f = C.c_double()
+        self._check(lib().amgps_profile_fp64_inst(self._h, cls, C.byref(f)))
         return f.value
 
     def profile_read(self, cls, reset=False):

@@ -265,7 +265,7 @@ struct amgps_ctx {
   struct Pair {
     cudaEvent_t a, b;
     int cls;
-    double bytes, flops;
+    double bytes, flops, inst;
   };
   std::vector<Pair> pending;
   std::vector<cudaEvent_t> pool;
@@ -285,6 +285,7 @@ struct amgps_ctx {
   double prof_ms[5] = {};
   double prof_bytes[5] = {};
   double prof_flops[5] = {};
+  double prof_inst[5] = {};
 };
 
 namespace {
@@ -392,6 +393,7 @@ void harvest(amgps_ctx* c) {
     c->prof_ms[p.cls] += ms;
     c->prof_bytes[p.cls] += p.bytes;
     c->prof_flops[p.cls] += p.flops;
+    c->prof_inst[p.cls] += p.inst;
     c->pool.push_back(p.a);
     c->pool.push_back(p.b);
   }
@@ -403,9 +405,11 @@ struct ProfScope {
   bool on;
   cudaEvent_t a{}, b{};
   int cls;
-  double bytes, flops;
-  ProfScope(amgps_ctx* c_, bool want, int cls_, double bytes_, double flops_ = 0.0)
-      : c(c_), on(want && c_->prof), cls(cls_), bytes(bytes_), flops(flops_) {
+  double bytes, flops, inst;
+  // flops / inst: the launch's algorithmic FP64 flops and FP64 thread instructions
+  ProfScope(amgps_ctx* c_, bool want, int cls_, double bytes_, double flops_ = 0.0,
+            double inst_ = 0.0)
+      : c(c_), on(want && c_->prof), cls(cls_), bytes(bytes_), flops(flops_), inst(inst_) {
     if (on) {
       a = take_event(c);
       b = take_event(c);
@@ -415,7 +419,7 @@ struct ProfScope {
   void done() {
     if (on) {
       CK(cudaEventRecord(b, c->stream));
-      c->pending.push_back({a, b, cls, bytes, flops});
+      c->pending.push_back({a, b, cls, bytes, flops, inst});
       on = false;
     }
   }
@@ -473,6 +477,21 @@ double op_flops(const Level& L, int fam, bool s0, bool s0add, bool s1, bool wt) 
   double f = nnz2 + (s0 ? (s0add ? 0.0 : n) : -n);
   if (s1) f += 2.0 * n;
   return f;
+}
+
+// FP64 thread instructions the step kernels issue for one step: one
+// multiply-add per stored entry (zeros included) and one per vector term of
+// the row.  Recurrence form: c2 r, the c1 z term, the x update, and (1/M) rin
+// where rin is unscaled (Jacobi: the x update only).
+double step_inst(const Level& L, int fam, bool zown, bool raw) {
+  const double n = (double)L.n;
+  if (fam == FAM_JAC) return (double)L.stored + n;
+  return (double)L.stored + n * (2.0 + (zown ? 1.0 : 0.0) + (raw ? 1.0 : 0.0));
+}
+double op_inst(const Level& L, int fam, bool s0, bool s0add, bool s1, bool wt) {
+  const double n = (double)L.n;
+  if (fam == FAM_OPT) return (double)L.stored + (wt ? n : 0.0);
+  return (double)L.stored + n * ((s0 && !s0add ? 1.0 : 0.0) + (s1 ? 1.0 : 0.0));
 }
 
 // ---------------------------------------------------------------------------
@@ -645,7 +664,8 @@ struct Engine {
       a.rout = t;
       a.beta = XT(st[ns - 1].h);
       ProfScope ps(c, profl, 0, step_bytes<VT, XT>(L, a.write_r ? 4 : 3),
-                   op_flops(L, FAM_OPT, true, true, false, a.write_r));
+                   op_flops(L, FAM_OPT, true, true, false, a.write_r),
+                   op_inst(L, FAM_OPT, true, true, false, a.write_r));
       run_step(c, L, a, s);
       ps.done();
     }
@@ -669,8 +689,10 @@ struct Engine {
         a.c1 = XT(st[q].g);
       }
       const int nvec = 2 + (a.rin ? 1 : 0) + (a.xin ? 1 : 0);
+      const bool s0 = a.rin != nullptr, s1 = a.xin != nullptr;
       ProfScope ps(c, profl, 0, step_bytes<VT, XT>(L, nvec),
-                   op_flops(L, FAM_OP, a.rin != nullptr, a.write_r, a.xin != nullptr, false));
+                   op_flops(L, FAM_OP, s0, a.write_r, s1, false),
+                   op_inst(L, FAM_OP, s0, a.write_r, s1, false));
       run_step(c, L, a, s);
       ps.done();
     }
@@ -715,7 +737,8 @@ struct Engine {
         a.dinv = md;
         a.fam = FAM_JAC;
         a.init = true;
-        ProfScope ps(c, profl, 0, step_bytes<VT, XT>(L, 4), step_flops(L, FAM_JAC, false, false));
+        ProfScope ps(c, profl, 0, step_bytes<VT, XT>(L, 4), step_flops(L, FAM_JAC, false, false),
+                     step_inst(L, FAM_JAC, false, false));
         run_step(c, L, a, s);
         ps.done();
         std::swap(cur, oth);
@@ -752,7 +775,7 @@ struct Engine {
       a.fam = cf.fam;
       a.init = true;
       ProfScope ps(c, profl, 0, step_bytes<VT, XT>(L, a.write_r ? 6 : 5),
-                   step_flops(L, cf.fam, false, true));
+                   step_flops(L, cf.fam, false, true), step_inst(L, cf.fam, false, true));
       run_step(c, L, a, s);
       ps.done();
       xcur = xb;
@@ -784,8 +807,9 @@ struct Engine {
       a.rin_raw = (rin_next == b);  // first step after k_first: r_0 = b
       // streams: z_j, r in(/out), z_{j+1}, x in/out, and 1/M unless scaled
       const bool no_dinv = L.sval && ((cf.fam == FAM_CHEB4 && !a.rin_raw) || cf.fam == FAM_CHEB1);
+      const bool raw = a.rin_raw && cf.fam == FAM_CHEB4;
       ProfScope ps(c, profl, 0, step_bytes<VT, XT>(L, (a.write_r ? 7 : 6) - (no_dinv ? 1 : 0)),
-                   step_flops(L, cf.fam, true, a.rin_raw && cf.fam == FAM_CHEB4));
+                   step_flops(L, cf.fam, true, raw), step_inst(L, cf.fam, true, raw));
       run_step(c, L, a, s);
       ps.done();
       xcur = x;
@@ -2369,6 +2393,7 @@ amgps_status amgps_profile_read(amgps_ctx* c, int cls, int reset, int64_t* launc
       c->prof_ms[cls] = 0.0;
       c->prof_bytes[cls] = 0.0;
       c->prof_flops[cls] = 0.0;
+      c->prof_inst[cls] = 0.0;
     }
   });
 }
@@ -2381,6 +2406,17 @@ amgps_status amgps_profile_flops(amgps_ctx* c, int cls, double* flops) {
     CK(cudaStreamSynchronize(c->stream));
     harvest(c);
     *flops = c->prof_flops[cls];
+  });
+}
+
+amgps_status amgps_profile_fp64_inst(amgps_ctx* c, int cls, double* inst) {
+  return guard(c, [&] {
+    REQ(c && inst, AMGPS_E_ARG, "null argument");
+    REQ(cls >= 0 && cls <= 4, AMGPS_E_ARG, "kernel class out of range");
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    harvest(c);
+    *inst = c->prof_inst[cls];
   });
 }
 

@@ -154,13 +154,17 @@ def test_op_form_vcycle_and_pcg(torch_cuda, case):
     S.vcycle(dev(torch, r), z)
     S.synchronize()
     flops = S.profile_flops(0)
+    inst = S.profile_fp64_inst(0)
     launches, _, _ = S.profile_read(0, reset=True)
     S.profile(False)
     assert_parity(z.cpu().numpy(), ora.vcycle(r), TOL, (name, "vcycle"))
     # a k = 4 cycle on level 0: three steps from zero, the s0 step and three
-    # more after the prolongation; flops 14 nnz + 7 n (see amgps_profile_flops)
+    # more after the prolongation; flops 14 nnz + 7 n (see amgps_profile_flops),
+    # FP64 instructions 7 x stored entries + 6 n (vector terms 0, 1, 2 from
+    # zero; 1, 0, 1, 1 after the prolongation)
     assert launches == 7
     assert flops == 14.0 * A.nnz + 7.0 * n
+    assert inst == 7.0 * S.level_info(0)[2] + 6.0 * n
     b = rng.uniform(-1, 1, n)
     x = torch.empty(n, dtype=torch.float64, device="cuda")
     it1, rel1 = S.pcg(dev(torch, b), x, rtol=1e-8)

@@ -204,3 +204,13 @@ def test_op_form_falls_back_when_operators_do_not_fit(torch_cuda, case):
         assert nc == 8 and not torch.equal(xc, xb)
     finally:
         S.close()
+
+
+def test_step_form_option_values(torch_cuda, case):
+    from paper_2407_09848_gb300.amgps import AmgpsError
+    _, _, S = case
+    for bad in (-1, 2):
+        with pytest.raises(AmgpsError) as e:
+            S.set_step_form(bad)
+        assert e.value.name == "AMGPS_E_ARG"
+    S.set_step_form(1)

@@ -214,3 +214,46 @@ def test_step_form_option_values(torch_cuda, case):
             S.set_step_form(bad)
         assert e.value.name == "AMGPS_E_ARG"
     S.set_step_form(1)
+
+
+def test_op_form_on_explicit_slices(torch_cuda):
+    # a non-stencil SPD matrix large enough for the stored-operator form:
+    # random symmetric pattern (explicit SELL slices, the operators' diagonal
+    # found by column), one warp per slice (direct kernel), two levels
+    import scipy.sparse as sp
+    from paper_2407_09848_gb300.amgps import Solver
+    torch = torch_cuda
+    rng = np.random.default_rng(31)
+    n = 1 << 18
+    m = 4 * n  # random off-diagonal entries (duplicates and the diagonal merge below)
+    R = sp.coo_matrix((rng.uniform(0.0, 1.0, m), (rng.integers(0, n, m), rng.integers(0, n, m))),
+                      shape=(n, n)).tocsr()
+    R.setdiag(0.0)
+    R.eliminate_zeros()
+    R = R + R.T
+    R.data = -np.abs(R.data)
+    d = np.asarray(abs(R).sum(axis=1)).ravel() + rng.uniform(0.1, 1.0, n)
+    A0 = (R + sp.diags(d)).tocsr()
+    A0.sort_indices()
+    agg = (rng.permutation(n) // 256).astype(np.int32)  # 1024 aggregates
+    P0 = sp.csr_matrix((np.ones(n), agg, np.arange(n + 1)), shape=(n, 1024))
+    A1 = (P0.T @ A0 @ P0).tocsr()
+    A1.sort_indices()
+    S = Solver().load([A0, A1], [P0])
+    M = l1_diag(A0)
+    b, x0 = rng.uniform(-1, 1, n), rng.uniform(-1, 1, n)
+    try:
+        for kind, k in (("cheb4_opt", 4), ("cheb1_opt", 3), ("l1jacobi", 3)):
+            spec = set_spec(S, kind, k)
+            for zero in (True, False):
+                ref = smooth(A0, b, None if zero else x0, spec, M=M)
+                x1, _, n1 = run_smooth(torch, S, kind, k, dev(torch, b), dev(torch, x0), zero, 1)
+                x0f, _, _ = run_smooth(torch, S, kind, k, dev(torch, b), dev(torch, x0), zero, 0)
+                assert_parity(x1.cpu().numpy(), ref, TOL, ("explicit", kind, k, zero))
+                assert n1 == (k - 1 if zero else k) and not torch.equal(x1, x0f)
+            ora = OracleAMG([A0, A1], [P0], spec)
+            z = torch.empty(n, dtype=torch.float64, device="cuda")
+            S.vcycle(dev(torch, b), z)
+            assert_parity(z.cpu().numpy(), ora.vcycle(b), TOL, ("explicit vcycle", kind, k))
+    finally:
+        S.close()

@@ -95,3 +95,30 @@ def test_op_coefs_rejects_degree_one(lib):
         amgps.op_coefs("cheb4_opt", 1)
     with pytest.raises(amgps.AmgpsError):
         amgps.op_coefs("l1jacobi", 1)
+
+
+@pytest.mark.parametrize("mistake", ["g_sign", "h_dropped", "tau_sigma_swapped", "sigma_sign",
+                                     "steps_shifted", "last_c1_missing"])
+def test_planted_coefficient_mistakes_are_caught(lib, system, mistake):
+    # each plausible slip in the derivation (a sign, a dropped term, a swapped
+    # or shifted coefficient, the c_1 scaling of the last step) moves the
+    # result far outside the rounding-level agreement the test above demands
+    A, M, b, x0 = system
+    k = 5
+    tau, sigma, h, g = (c.copy() for c in amgps.op_coefs("cheb4_opt", k))
+    if mistake == "g_sign":
+        g = -g
+    elif mistake == "h_dropped":
+        h[1] = 0.0
+    elif mistake == "tau_sigma_swapped":
+        tau[1], sigma[1] = sigma[1], tau[1]
+    elif mistake == "sigma_sign":
+        sigma[2] = -sigma[2]
+    elif mistake == "steps_shifted":
+        tau, sigma = np.roll(tau, 1), np.roll(sigma, 1)
+    else:
+        c1 = 4.0 / 3.0  # c_1 = (8 - 4) / (2 + 1) at rho = 1
+        tau[-1], sigma[-1], h[-1], g[-1] = tau[-1] / c1, sigma[-1] / c1, h[-1] / c1, g[-1] / c1
+    ref = smooth(A, b, x0, SmootherSpec("cheb4_opt", k, beta=amgps.opt4_weights(k)), M=M)
+    got = op_apply(A, M, b, x0, (tau, sigma, h, g))
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) > 1e-6

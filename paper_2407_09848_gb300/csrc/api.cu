@@ -635,7 +635,8 @@ struct Engine {
 
   // One application in the stored-operator form (see op_plan).  Buffers: za
   // holds c = M^{-1} b (formed here unless c_ready: an application from zero
-  // on the same b left it there), then s_0 = M^{-1}(b - A x_0) in place; the
+  // on the same b, or on level 0 the PCG r update, left it there), then
+  // s_0 = M^{-1}(b - A x_0) in place; the
   // u_j alternate between zb and xb (u_j overwrites u_{j+2}, which only its
   // own row reads); r holds x_0 + h s_0 for the last step when k >= 3.
   static void smooth_ops(amgps_ctx* c, int l, const Coefs& cf, const XT* b, XT* x, bool xzero,
